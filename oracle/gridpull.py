@@ -231,9 +231,13 @@ def nearest_point(q: np.ndarray, points: np.ndarray, chunk: int = 512) -> np.nda
 
 def knn_sigma(points: np.ndarray, k: int = 50, idx=None, chunk: int = 256) -> np.ndarray:
     """Distance from each point (or from points[idx]) to its k-th nearest other
-    point; the point itself is excluded by index, duplicates count."""
+    point; the point itself is excluded by index, duplicates count.  A cloud
+    with fewer than k + 1 points uses k = J - 1 (sigma = 0 for a single point)."""
     idx = np.arange(len(points)) if idx is None else np.asarray(idx)
-    out = np.empty(len(idx), dtype=np.float64)
+    k = min(k, len(points) - 1)
+    out = np.zeros(len(idx), dtype=np.float64)
+    if k <= 0:
+        return out
     for a in range(0, len(idx), chunk):
         sel = idx[a:a + chunk]
         d = sq_dist64(points[sel], points)
@@ -243,58 +247,52 @@ def knn_sigma(points: np.ndarray, k: int = 50, idx=None, chunk: int = 256) -> np
 
 
 # ------------------------------------------------ counter-based sampling
-_M0, _M1 = 0xD2E7470EE14C6C93, 0xCA5A826395121157
-_W0, _W1 = 0x9E3779B97F4A7C15, 0xBB67AE8584CAA73B
-_MASK64 = (1 << 64) - 1
+_PHILOX_M0, _PHILOX_M1 = 0xD2511F53, 0xCD9E8D57
+_PHILOX_W0, _PHILOX_W1 = 0x9E3779B9, 0xBB67AE85
+_MASK32 = 0xFFFFFFFF
 
 
-def philox4x64(ctr, key):
-    """Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11) on one counter.
+def philox4x32(ctr, key):
+    """Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) on one counter.
 
-    ctr: four uint64, key: two uint64.  Ten rounds of two 64x64->128 products;
-    the key is bumped by the Weyl constants between rounds."""
-    c = [int(x) & _MASK64 for x in ctr]
-    k = [int(x) & _MASK64 for x in key]
+    ctr: four uint32 words, key: two uint32 words.  Each of the ten rounds
+    multiplies words 0 and 2 by the round multipliers (32x32 -> 64 bits), mixes
+    the high halves with the other words and the key, and the key is bumped by
+    the Weyl constants between rounds."""
+    c = [int(x) & _MASK32 for x in ctr]
+    k = [int(x) & _MASK32 for x in key]
     for _ in range(10):
-        p0 = _M0 * c[0]
-        p1 = _M1 * c[2]
-        c = [(p1 >> 64) ^ c[1] ^ k[0], p1 & _MASK64, (p0 >> 64) ^ c[3] ^ k[1], p0 & _MASK64]
-        k = [(k[0] + _W0) & _MASK64, (k[1] + _W1) & _MASK64]
+        p0 = _PHILOX_M0 * c[0]
+        p1 = _PHILOX_M1 * c[2]
+        c = [(p1 >> 32) ^ c[1] ^ k[0], p1 & _MASK32, (p0 >> 32) ^ c[3] ^ k[1], p0 & _MASK32]
+        k = [(k[0] + _PHILOX_W0) & _MASK32, (k[1] + _PHILOX_W1) & _MASK32]
     return c
 
 
-def philox4x64_vec(c0: np.ndarray, c1, c2, c3, k0: int, k1: int):
-    """Vectorised Philox4x64-10 over an array of first counter words."""
-    c0 = np.asarray(c0, dtype=np.uint64)
-    n = len(c0)
-    c = [c0.copy(), np.full(n, c1, np.uint64), np.full(n, c2, np.uint64), np.full(n, c3, np.uint64)]
-    k = [np.uint64(k0 & _MASK64), np.uint64(k1 & _MASK64)]
-
-    def mulhilo(a: int, b: np.ndarray):
-        lo_mask = np.uint64(0xFFFFFFFF)
-        a_lo, a_hi = np.uint64(a & 0xFFFFFFFF), np.uint64(a >> 32)
-        b_lo, b_hi = b & lo_mask, b >> np.uint64(32)
-        ll = a_lo * b_lo
-        lh = a_lo * b_hi
-        hl = a_hi * b_lo
-        hh = a_hi * b_hi
-        mid = (ll >> np.uint64(32)) + (lh & lo_mask) + (hl & lo_mask)
-        hi = hh + (lh >> np.uint64(32)) + (hl >> np.uint64(32)) + (mid >> np.uint64(32))
-        lo = np.uint64(a) * b  # wraps mod 2^64
-        return hi, lo
-
-    with np.errstate(over="ignore"):
-        for _ in range(10):
-            hi0, lo0 = mulhilo(_M0, c[0])
-            hi1, lo1 = mulhilo(_M1, c[2])
-            c = [hi1 ^ c[1] ^ k[0], lo1, hi0 ^ c[3] ^ k[1], lo0]
-            k = [k[0] + np.uint64(_W0), k[1] + np.uint64(_W1)]
+def philox4x32_vec(c0, c1, c2, c3, k0: int, k1: int):
+    """Vectorised Philox4x32-10: each counter word may be an array or a scalar."""
+    c0 = np.asarray(c0, dtype=np.uint64) & np.uint64(_MASK32)
+    n = c0.shape
+    c = [c0] + [np.broadcast_to(np.asarray(x, dtype=np.uint64) & np.uint64(_MASK32), n).copy()
+                for x in (c1, c2, c3)]
+    k = [k0 & _MASK32, k1 & _MASK32]
+    m32 = np.uint64(_MASK32)
+    sh = np.uint64(32)
+    for _ in range(10):
+        p0 = np.uint64(_PHILOX_M0) * c[0]          # < 2^64: no wrap
+        p1 = np.uint64(_PHILOX_M1) * c[2]
+        c = [(p1 >> sh) ^ c[1] ^ np.uint64(k[0]), p1 & m32, (p0 >> sh) ^ c[3] ^ np.uint64(k[1]), p0 & m32]
+        k = [(k[0] + _PHILOX_W0) & _MASK32, (k[1] + _PHILOX_W1) & _MASK32]
     return c
+
+
+def _seed_key(seed: int):
+    return int(seed) & _MASK32, (int(seed) >> 32) & _MASK32
 
 
 def _u24(x: np.ndarray, plus_one: bool) -> np.ndarray:
-    """Top 24 bits of a uint64 word as a float in (0,1] (plus_one) or [0,1)."""
-    top = (x >> np.uint64(40)).astype(np.float64)
+    """Top 24 bits of a 32-bit word as a float in (0,1] (plus_one) or [0,1)."""
+    top = (np.asarray(x, np.uint64) >> np.uint64(8)).astype(np.float64)
     return (top + (1.0 if plus_one else 0.0)) * 2.0 ** -24
 
 
@@ -319,8 +317,8 @@ def point_permutation(J: int, seed: int, epoch: int, positions=None) -> np.ndarr
     """Pi_e(p): the random order in which epoch ``epoch`` visits the points.
 
     A 4-round balanced Feistel network on m bits (m even, 2^m >= J) whose round
-    function is word 0 of Philox4x64-10 at counter (value, round, epoch, 1) and
-    key (seed, 0), made a bijection of [0, J) by cycle walking."""
+    function is word 0 of Philox4x32-10 at counter (value, round, epoch, 1) and
+    key (seed low, seed high), made a bijection of [0, J) by cycle walking."""
     m = feistel_bits(J)
     half = m // 2
     mask = (1 << half) - 1
@@ -330,7 +328,7 @@ def point_permutation(J: int, seed: int, epoch: int, positions=None) -> np.ndarr
         left = x >> np.uint64(half)
         right = x & np.uint64(mask)
         for rnd in range(4):
-            f = philox4x64_vec(right, rnd, epoch, 1, seed, 0)[0] & np.uint64(mask)
+            f = philox4x32_vec(right, rnd, epoch, 1, *_seed_key(seed))[0] & np.uint64(mask)
             left, right = right, left ^ f
         return (left << np.uint64(half)) | right
 
@@ -348,24 +346,27 @@ def sample_queries(points: np.ndarray, sigma: np.ndarray, seed: int, epoch: int,
     """Queries at pool positions ``positions`` of epoch ``epoch`` (Sec. 3:
     Gaussian queries around randomly visited surface points, drawn anew each
     epoch).  Position k visits point j = Pi_e(k mod J) and draws
-    z ~ N(0, I) from Philox4x64-10 at counter (k, epoch, 0, 0), key (seed, 0);
+    z ~ N(0, I) from Philox4x32-10 at counter (k, epoch, 0, 0), key (seed low,
+    seed high);
     q = s_j + sigma_j * z.  Returns (q float64 (n,3), j int64 (n,))."""
     J = len(points)
     positions = np.asarray(positions, dtype=np.int64)
     j = point_permutation(J, seed, epoch, positions % J)
-    z = box_muller3(philox4x64_vec(positions.astype(np.uint64), epoch, 0, 0, seed, 0))
+    z = box_muller3(philox4x32_vec(positions.astype(np.uint64), epoch, 0, 0, *_seed_key(seed)))
     s = np.asarray(points, np.float32).astype(np.float64)[j]
     return s + np.asarray(sigma, np.float64)[j][:, None] * z, j
 
 
 def sphere_init(vkeys: np.ndarray, R: int, center, radius: float, noise_std: float, seed: int):
     """Geometric initialisation (Sec. 3): |v - c| - radius at each vertex, plus
-    noise_std * N(0,1) from Philox4x64-10 at counter (vertex key, 0, 0, 2)."""
+    noise_std * N(0,1) (the first Box-Muller normal) from Philox4x32-10 at
+    counter (vertex key low, vertex key high, 0, 2), key (seed low, seed high)."""
     h = grid_spacing(R)
     v = -1.0 + h * key_to_vertex(np.asarray(vkeys, np.int64), R).astype(np.float64)
     d = np.sqrt(np.sum((v - np.asarray(center, np.float64)) ** 2, axis=1)) - radius
     if noise_std != 0:
-        w = philox4x64_vec(np.asarray(vkeys, np.uint64), 0, 0, 2, seed, 0)
+        kk = np.asarray(vkeys, np.uint64)
+        w = philox4x32_vec(kk & np.uint64(_MASK32), kk >> np.uint64(32), 0, 2, *_seed_key(seed))
         d = d + noise_std * box_muller3(w)[:, 0]
     return d
 
