@@ -1,0 +1,394 @@
+"""Benchmark of the GridPull fitting step on GB300.
+
+One step = one pass of the whole hot path over one batch of the epoch's query
+pool: gp_sample (Gaussian queries around points in the epoch's random order)
+-> gp_nn (exact nearest surface point) -> gp_step (Eq. 8 forward and
+hand-written backward, L_TV included) -> gp_update (Adam on the trainable
+vertices).  Band construction and sigma are once-per-cloud set-up, untimed.
+
+Default workload: the single synthetic object (3 random ellipsoids and a
+torus, 100,000 points with N(0, 0.001^2) noise), 256^3 grid with a band of
+cells within 2 voxels of the points stored as 8^3 float32 bricks, a pool of
+2,000,000 queries per epoch and batches of 262,144 queries.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
+on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "pull-step queries/sec (fwd+bwd+Adam)"
+UNIT = "queries/s"
+
+WORKLOADS = {
+    "object": dict(desc="single object: 3 random ellipsoids + torus (R=0.3, r=0.08), 100,000 points + "
+                        "N(0,0.001^2) noise; 256^3 grid, band = cells within 2 voxels of a point, 8^3 float32 "
+                        "bricks; pool 2,000,000 queries/epoch (q = s_j + sigma_j N(0,I), sigma_j = 50th-NN "
+                        "distance); batch 262,144",
+                   cloud=lambda: __import__("paper_2308_13175_gb300.synth", fromlist=["x"]).object_cloud(100_000, seed=1),
+                   R=256, M1=2, M2=2, Q=2_000_000, B=262_144, lr=1e-3),
+    "sphere": dict(desc="single sphere: 5,000 points on a radius-0.5 sphere; dense 64^3 grid; 50,000 queries "
+                        "(10 per point), full batch",
+                   cloud=lambda: __import__("paper_2308_13175_gb300.synth", fromlist=["x"]).sphere_cloud(5000, 0.5, 0),
+                   R=64, M1=-1, M2=-1, Q=50_000, B=50_000, lr=1e-3),
+}
+
+# Algorithmic bytes per launch of each kernel ("Kernels and
+# their rooflines").  n = queries in the launch, J = points, Vs = stored
+# slots, Vt = trainable vertices.
+def alg_bytes(name, n, J, Vs, Vt):
+    return {
+        "k_sample": 32 * n,
+        "k_perm": 4 * J,
+        "k_nn": 36 * n + 16 * J,
+        "k_count_valid": 24 * n,
+        "k_tv": 8 * Vs,
+        "k_query": 24 * n + 8 * Vt,
+        "k_finalize": 0,
+        "k_adam": 28 * Vt,
+    }.get(name, 0)
+
+
+KERNEL_BOUND = {"k_nn": "hbm", "k_tv": "hbm", "k_query": "hbm", "k_adam": "hbm", "k_sample": "hbm"}
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# -------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [r.split(",") for r in self.file.read().strip().splitlines() if r.strip()]
+        self.file.close()
+        os.unlink(self.file.name)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+                for k, nm in enumerate(names):
+                    if r[5 + k].strip().lower() == "active":
+                        reasons.add(nm)
+            except Exception:
+                continue
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- helpers
+def dist_setup():
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def reduce_max(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_sum(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# -------------------------------------------------- oracle CPU baseline
+def oracle_rate(pts, wl, sample_q: int, seed: int = 0, repeats: int = 1):
+    """Queries/s of the FP64 oracle on a bounded sample of the workload.
+
+    Timed per step: the sampler, brute-force NN and the query terms with their
+    gradient for ``sample_q`` queries, plus the vertex work (L_TV over the TV
+    set and Adam over the trainable set) once.  The rate is extrapolated to a
+    full batch B: B / (t_query * B / sample_q + t_vertex).  Band sets, sigma of
+    the visited points and the dense value array are set-up (untimed)."""
+    from oracle import gridpull as o
+    R = wl["R"]
+    sets = o.band_sets(pts, R, wl["M1"], wl["M2"])
+    keys = np.arange((R + 1) ** 3) if R <= 128 else None
+    D = np.zeros((R + 1) ** 3)
+    h = 2.0 / R
+    c = 0.5 * (pts.min(0) + pts.max(0))
+    need = sets["required"] if keys is None else keys
+    v = -1.0 + h * o.key_to_vertex(need, R)
+    D[need] = np.linalg.norm(v - c, axis=1) - 2 * h
+    J = len(pts)
+    pos = np.arange(sample_q, dtype=np.int64) + 12345
+    j = o.point_permutation(J, seed, 0, pos % J)
+    sig = np.zeros(J)
+    uj = np.unique(j)
+    sig[uj] = o.knn_sigma(pts, 50, idx=uj)
+    m = np.zeros(len(sets["trainable"]))
+    vv = np.zeros(len(sets["trainable"]))
+    tq_all, tv_all = [], []
+    for r in range(repeats):
+        t0 = time.perf_counter()
+        q, _ = o.sample_queries(pts, sig, seed, 0, pos)
+        q = q.astype(np.float32)
+        nn = o.nearest_point(q, pts)
+        qt = o.query_terms(D, R, sets["pull_cells"], q, pts[nn], 1.0, 0.005)
+        t1 = time.perf_counter()
+        _, tvg, _ = o.tv_term(D, R, sets["tv"])
+        g = qt["grad"][sets["trainable"]] + tvg[sets["trainable"]]
+        o.adam(D[sets["trainable"]], g, m, vv, r + 1, wl["lr"])
+        t2 = time.perf_counter()
+        tq_all.append(t1 - t0)
+        tv_all.append(t2 - t1)
+    tq, tv = float(np.median(tq_all)), float(np.median(tv_all))
+    B = wl["B"]
+    per_step = tq * B / sample_q + tv
+    return B / per_step, {"t_query_s": tq, "t_vertex_s": tv, "sample_q": sample_q}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    wl = WORKLOADS[args.workload]
+    pts = wl["cloud"]()
+    sample_q = args.ref_sample
+    t_start = time.perf_counter()
+    oracle_rate(pts, wl, sample_q, repeats=max(1, args.warmup))
+    rate, info = oracle_rate(pts, wl, sample_q, repeats=max(1, args.steps))
+    elapsed = time.perf_counter() - t_start
+    sample = (f"each step: sampler + brute-force NN + query terms for {sample_q} queries and the full vertex "
+              f"work (L_TV + Adam) once; rate extrapolated to a {wl['B']}-query batch")
+    out = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wl["B"] / rate,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": wl["desc"], "host_seconds": round(elapsed, 1)},
+           "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# ------------------------------------------------------------- our arm
+def run_ours(args, world, rank, local):
+    import torch
+    from paper_2308_13175_gb300 import binding as gb
+    from paper_2308_13175_gb300 import build as gbuild
+    from paper_2308_13175_gb300.fit import FitStep, PAPER_WEIGHTS
+
+    if not os.path.exists(gb.lib_path()):
+        gbuild.build()
+    torch.cuda.set_device(local)
+    wl = WORKLOADS[args.workload]
+    pts = wl["cloud"]()
+    R = wl["R"]
+    ctx = gb.gp_create(local)
+    band = gb.gp_build_band(ctx, torch.from_numpy(pts).cuda(), R, wl["M1"], wl["M2"], 50)
+    c = 0.5 * (pts.min(0) + pts.max(0))
+    gb.gp_band_init_sphere(band, c, 2.0 * 2.0 / R, 0.0, seed=0)
+    fit = FitStep(band, wl["Q"], wl["B"], seed=rank, weights=PAPER_WEIGHTS, lr=wl["lr"])
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    info = band.info
+
+    def timed_steps(first_t, K, profile=False):
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+        queries = 0
+        for k in range(K):
+            t = first_t + k
+            flush.fill_(float(k))          # L2 flush outside the timed events
+            starts[k].record(stream)
+            fit.run(t)
+            ends[k].record(stream)
+            queries += fit.batch_of(t)[2]
+        torch.cuda.synchronize()
+        ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+        return ms, queries
+
+    for t in range(args.warmup):
+        fit.run(t)
+    torch.cuda.synchronize()
+    t0 = args.warmup
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = gb.gp_launch_count(ctx)
+    ms, queries = timed_steps(t0, args.steps)
+    launches = gb.gp_launch_count(ctx) - launches0
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    t_ms = sum(ms)
+    t_max = reduce_max(t_ms, world)
+    q_total = reduce_sum(float(queries), world)
+    value = q_total / (t_max / 1e3)
+
+    # Per-kernel durations: the same steps again with the library's CUDA-event
+    # tracing on (events on the launching stream).
+    gb.gp_profile(ctx, True)
+    ms_prof, q_prof = timed_steps(t0 + args.steps, args.steps)
+    gb.gp_profile(ctx, False)
+    kern = gb.gp_profile_read(ctx)
+    peak, peak_kind = peaks()
+    J, Vs, Vt = info["J"], info["V_stored"], info["V_trainable"]
+    per_kernel = {}
+    for name, (cnt, tot) in kern.items():
+        per_step_n = q_prof / args.steps
+        by = alg_bytes(name, per_step_n, J, Vs, Vt)
+        avg_ms = tot / cnt
+        per_kernel[name] = {"launches": cnt, "avg_us": round(1e3 * avg_ms, 2),
+                            "share": round(tot / max(sum(v[1] for v in kern.values()), 1e-12), 4),
+                            "alg_bytes": int(by), "gbs": round(by / (avg_ms / 1e3) / 1e9, 1) if by else None}
+    dom = max(kern.items(), key=lambda kv: kv[1][1])[0]
+    dk = per_kernel[dom]
+    achieved = dk["gbs"] or 0.0
+    roofline = {"bound": KERNEL_BOUND.get(dom, "hbm"), "kernel": dom, "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
+                "peak_kind": peak_kind}
+
+    # End to end through the public API: host queries (pinned) -> device,
+    # NN + step + update, loss back to the host, every step.
+    B = wl["B"]
+    K = args.steps
+    rng = np.random.default_rng(rank + 7)
+    jj = rng.integers(0, len(pts), size=(K, B))
+    sig = gb.gp_band_sigma(band).cpu().numpy()
+    hq = torch.empty((K, B, 3), dtype=torch.float32).pin_memory()
+    hq.copy_(torch.from_numpy((pts[jj] + sig[jj][..., None] * rng.normal(size=(K, B, 3))).astype(np.float32)))
+    hloss = torch.empty((K, 8), dtype=torch.float32).pin_memory()
+    dq = torch.empty((B, 3), dtype=torch.float32, device="cuda")
+    barrier(world)
+    torch.cuda.synchronize()
+    e_start = torch.cuda.Event(enable_timing=True)
+    e_end = torch.cuda.Event(enable_timing=True)
+    e2e_ms = 0.0
+    step_t = t0 + 2 * args.steps
+    for k in range(K):
+        flush.fill_(float(k))
+        e_start.record(stream)
+        dq.copy_(hq[k], non_blocking=True)
+        gb.gp_nn(band, dq, None, fit.rec)
+        gb.gp_step(band, fit.rec, B, fit.grad, fit.loss, PAPER_WEIGHTS)
+        gb.gp_update(band, fit.grad, wl["lr"], step_t + k + 1)
+        hloss[k].copy_(fit.loss, non_blocking=True)
+        e_end.record(stream)
+        e_end.synchronize()
+        e2e_ms += e_start.elapsed_time(e_end)
+    e2e_ms = reduce_max(e2e_ms, world)
+    e2e_value = reduce_sum(float(K * B), world) / (e2e_ms / 1e3)
+    loss_final = float(hloss[K - 1][gb.GP_LOSS_TOTAL])
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, cinfo = oracle_rate(pts, wl, args.cpu_sample)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{args.cpu_sample} queries (sampler + brute-force NN + query terms) and the full vertex "
+                         f"work once, extrapolated to a {B}-query batch; t_query={cinfo['t_query_s']:.2f}s "
+                         f"t_vertex={cinfo['t_vertex_s']:.2f}s"}
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+               "config": {"workload": wl["desc"], "parallelism": f"replicas x{world}",
+                          "l2": "flushed between timed steps (256 MB write outside the step events)",
+                          "V_stored": Vs, "V_trainable": Vt, "V_tv": info["V_tv"], "J": J},
+               "roofline": roofline, "cpu_baseline": cpu,
+               "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 12 * B, "d2h_bytes_per_step": 32},
+               "gpu_launches": int(launches), "clocks": clk, "kernels": per_kernel,
+               "loss_last": loss_final}
+        print(json.dumps(out), flush=True)
+    gb.gp_band_check(band)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="object", choices=sorted(WORKLOADS))
+    ap.add_argument("--cpu-sample", type=int, default=4096)
+    ap.add_argument("--ref-sample", type=int, default=1024)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

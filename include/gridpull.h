@@ -1,0 +1,272 @@
+/*
+ * gridpull.h - C ABI of the GB300 GridPull step library (libgridpull.so).
+ *
+ * GridPull (Chen, Liu, Han, ICCV 2023) fits a discrete signed distance field
+ * D = {d_i} held on the vertices of a uniform grid to a point cloud S by
+ * minimising, over D, the loss of Eq. 8 on sampled queries q (Sec. 3).  This
+ * library runs one optimisation step of that fit on one GPU:
+ *
+ *   gp_build_band  uniform grid + near-surface brick table (Sec. 3 "Discrete
+ *                  Grids", the M1 / M2 bandwidths) and the per-point sampling
+ *                  sigma;
+ *   gp_sample      Gaussian queries around randomly visited points (Sec. 3);
+ *   gp_nn          NN(q), the nearest surface point of each query (Eq. 4);
+ *   gp_step        the loss of Eq. 8 (Eq. 3-7 inside) and its gradient dL/dD,
+ *                  forward and hand-written backward in one pass;
+ *   gp_update      Adam on the trainable vertices (Sec. 4 "Details").
+ *
+ * Conventions shared by every call:
+ *   - Geometry.  The domain is [-1,1]^3 split into R^3 cells (R a power of two),
+ *     h = 2/R, vertex (i,j,k) at (-1,-1,-1) + h*(i,j,k), i,j,k in [0,R].  The
+ *     cell of a point x is floor((x+1)/h) per axis, taken exactly on the
+ *     float32 input; surface points are clamped to [0,R-1]; a query outside the
+ *     domain, or whose cell or whose NN's cell is outside the pull band, is
+ *     masked (weight 0, not counted in B_v).
+ *   - Storage.  Grid values live in bricks of 8x8x8 vertices.  Brick b covers
+ *     vertices [8*bx, 8*bx+7] x ...; the value of vertex (i,j,k) is at slot
+ *     index  s*512 + ((k&7)*8 + (j&7))*8 + (i&7)  where s is the brick's slot.
+ *     "V_stored" = 512 * n_bricks; slots whose coordinate exceeds R are padding.
+ *   - Memory.  Pointers named *_dev are device pointers on the context's device
+ *     owned by the caller; the library never frees them and never keeps them
+ *     after the call returns.  The library owns the band (brick table, D, Adam
+ *     moments, point cell list, scratch) and frees it in gp_band_destroy.
+ *   - Streams.  Every call is asynchronous on the context's stream, except
+ *     gp_build_band and the gp_band_* queries that return host values, which
+ *     synchronise that stream.  gp_sample, gp_nn, gp_step and gp_update never
+ *     allocate memory.
+ *   - Errors.  Every call returns a gp_status; on failure gp_last_error(ctx)
+ *     holds a one-line message.  No C++ exception crosses this interface.
+ *     Invalid arguments are reported before anything is launched.
+ */
+#ifndef GRIDPULL_H
+#define GRIDPULL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum gp_status {
+  GP_OK = 0,
+  GP_ERR_ARG = 1,     /* invalid argument: null pointer, bad size or descriptor  */
+  GP_ERR_OOM = 2,     /* a device allocation failed                              */
+  GP_ERR_CUDA = 3,    /* a CUDA runtime call or a kernel launch failed           */
+  GP_ERR_TIMEOUT = 4, /* a bounded device-side wait gave up                      */
+  GP_ERR_STATE = 5,   /* the call is not valid in the object's current state     */
+  GP_ERR_NUMERIC = 6  /* a device-side numeric or range check fired              */
+} gp_status;
+
+typedef struct gp_ctx gp_ctx;
+typedef struct gp_band gp_band;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on CUDA device `device` whose calls run on `stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  *out receives the
+ * context; destroy it with gp_destroy after every band made from it. */
+gp_status gp_create(gp_ctx** out, int device, void* stream);
+
+/* Change the stream later calls run on (e.g. torch's current stream). */
+gp_status gp_set_stream(gp_ctx* ctx, void* stream);
+
+/* Free the context (NULL is ignored). */
+void gp_destroy(gp_ctx* ctx);
+
+/* Message of the last failing call on this context ("" if none).  The string
+ * is owned by the context and valid until its next call. */
+const char* gp_last_error(const gp_ctx* ctx);
+
+/* Library version string, e.g. "gridpull-gb300 0.1". */
+const char* gp_version(void);
+
+/* ---------------------------------------------------------------- tracing */
+
+/* Start (enable != 0) or stop recording a pair of CUDA events around every
+ * kernel this context launches, on its stream.  Off by default; recording adds
+ * two event records per launch and no synchronisation. */
+gp_status gp_profile(gp_ctx* ctx, int enable);
+
+/* Aggregate the recorded launches by kernel name and clear the record
+ * (synchronises the stream).  Up to max_kernels entries are written: names as
+ * 32-byte NUL-terminated strings (names + 32*k), total_ms[k] the summed event
+ * durations, launches[k] the launch count; *n_kernels receives the number of
+ * distinct kernels seen (may exceed max_kernels). */
+gp_status gp_profile_read(gp_ctx* ctx, char* names, double* total_ms, int64_t* launches, int32_t max_kernels,
+                          int32_t* n_kernels);
+
+/* Kernels launched through this context since its creation (always counted;
+ * -1 for a NULL context). */
+int64_t gp_launch_count(const gp_ctx* ctx);
+
+/* ------------------------------------------------------------------- band */
+
+/* Band flags (gp_grid_desc.flags). */
+#define GP_BAND_DETERMINISTIC 1u /* also allocate the fixed-point gradient
+                                    accumulator used by GP_STEP_DETERMINISTIC  */
+
+typedef struct gp_grid_desc {
+  int32_t R;       /* cells per axis: a power of two in [8, 2048]                */
+  int32_t M1;      /* pull bandwidth (Sec. 3): Chebyshev dilation, in cells, of
+                      the cells holding points; < 0 = every cell                 */
+  int32_t M2;      /* TV bandwidth (Sec. 3 "Continuous Distance Fields"): L_TV is
+                      imposed on the corners of the M2 dilation; < 0 = all      */
+  int32_t knn_k;   /* sigma_j = distance from s_j to its knn_k-th nearest other
+                      point (0 = do not compute; gp_sample then fails)           */
+  int32_t nn_grid; /* cells per axis of the point cell list used by gp_nn
+                      (0 = chosen from J)                                        */
+  uint32_t flags;  /* GP_BAND_* flags                                            */
+} gp_grid_desc;
+
+typedef struct gp_band_info {
+  int32_t R;                 /* cells per axis                                  */
+  int32_t nb;                /* bricks per axis of the virtual brick grid       */
+  int64_t n_bricks;          /* stored bricks                                   */
+  int64_t n_active_bricks;   /* bricks holding at least one trainable vertex    */
+  int64_t V_stored;          /* 512 * n_bricks value slots                      */
+  int64_t V_trainable;       /* corners of the max(M1,M2) band                  */
+  int64_t V_tv;              /* |T|: corners of the M2 band                     */
+  int64_t n_pull_cells;      /* cells of the M1 band                            */
+  int64_t n_occupied_cells;  /* cells holding at least one point                */
+  int64_t J;                 /* points in the cloud                             */
+  int32_t nn_grid;           /* cells per axis of the point cell list           */
+  int32_t knn_k;             /* k used for sigma (0 if not computed)            */
+} gp_band_info;
+
+/* Build the band for the cloud `pts_dev` (J x 3 float32, xyz interleaved, in
+ * [-1,1]^3; points outside are clamped to the boundary cells).  Computes the
+ * occupied cells, the M1 pull band, the TV vertex set, the trainable set,
+ * allocates the bricks that hold them plus the one-vertex apron L_TV reads, and
+ * initialises every stored value to 0 and the Adam state to zero.  Also builds
+ * the point cell list for gp_nn and sigma_j (knn_k > 0).  Synchronises the
+ * stream.  Errors: GP_ERR_ARG (R not a power of two in range, J < 1 or
+ * J >= 2^31, null pointer), GP_ERR_OOM, GP_ERR_CUDA. */
+gp_status gp_build_band(gp_ctx* ctx, const float* pts_dev, int64_t J,
+                        const gp_grid_desc* desc, gp_band** out);
+
+/* Free the band and everything it owns (NULL is ignored). */
+void gp_band_destroy(gp_band* band);
+
+/* Sizes of the band (host struct).  Does not synchronise. */
+gp_status gp_band_get_info(const gp_band* band, gp_band_info* out);
+
+/* Geometric initialisation (Sec. 3): every stored value (trainable or not) is
+ * set to |v - c| - radius + noise_std * z, z ~ N(0,1) the first Box-Muller
+ * normal of Philox4x32-10 at counter (key_lo, key_hi, 0, 2) and key (seed_lo,
+ * seed_hi), key = i + (R+1)*(j + (R+1)*k).  Padding slots are set to 0. */
+gp_status gp_band_init_sphere(gp_band* band, float cx, float cy, float cz, float radius,
+                              float noise_std, uint64_t seed);
+
+/* Overwrite all V_stored values from `d_dev` (V_stored floats, storage order). */
+gp_status gp_band_set_values(gp_band* band, const float* d_dev);
+
+/* Export the stored vertices in storage order.  Any output may be NULL.
+ * ijk_dev: V_stored x 3 int32 vertex coordinates (padding slots have a
+ * coordinate > R); d_dev: V_stored current values; flags_dev: V_stored bytes,
+ * bit0 = in the TV set T, bit1 = trainable, bit2 = inside [0,R]^3,
+ * bit3 = lowest corner of a pull-band cell. */
+gp_status gp_band_export(const gp_band* band, int32_t* ijk_dev, float* d_dev, uint8_t* flags_dev);
+
+/* Zero-copy device pointers of the band's values and Adam moments (each
+ * V_stored floats, storage order).  Any output may be NULL.  The pointers stay
+ * valid until gp_band_destroy. */
+gp_status gp_band_values(gp_band* band, float** d_dev, float** m_dev, float** v_dev);
+
+/* Copy sigma_j (J floats, original point order) to `sigma_dev`. */
+gp_status gp_band_sigma(const gp_band* band, float* sigma_dev);
+
+/* Zero the Adam moments (the step counter is the caller's). */
+gp_status gp_band_reset_adam(gp_band* band);
+
+/* Read and clear the band's device-side error flag (synchronises the stream).
+ * Returns GP_OK, GP_ERR_NUMERIC (a fixed-point accumulator overflowed or a
+ * non-finite value reached a deterministic sum) or GP_ERR_TIMEOUT. */
+gp_status gp_band_check(gp_band* band);
+
+/* --------------------------------------------------------------- sampling */
+
+/* Queries of the epoch-`epoch` pool of Q queries, pool positions
+ * [first, first + count), written to q_dev (count x 3 float32).  Sec. 3: each
+ * epoch visits the points in a fresh random order and draws a Gaussian query
+ * around each visited point.  Position k visits point j = Pi_e(k mod J), where
+ * Pi_e is a 4-round Feistel bijection of [0, J) keyed by (seed, epoch), and
+ * q = s_j + sigma_j * z with z ~ N(0, I) from Philox4x32-10 at counter
+ * (k, epoch, 0, 0), key (seed_lo, seed_hi), via Box-Muller.  Requires
+ * knn_k > 0 at build.  Errors: GP_ERR_ARG (Q > 2^31-1, first + count > Q,
+ * null q_dev with count > 0), GP_ERR_STATE (no sigma). */
+gp_status gp_sample(gp_band* band, uint64_t seed, uint32_t epoch, int64_t Q, int64_t first,
+                    int64_t count, float* q_dev);
+
+/* ---------------------------------------------------------- nearest point */
+
+/* NN(q) of Eq. 4 for n queries q_dev (n x 3 float32): nn_dev[i] receives the
+ * index (original order) of the cloud point minimising
+ * ((qx-sx)^2 + (qy-sy)^2) + (qz-sz)^2 evaluated in float64 from the float32
+ * coordinates, ties to the lowest index.  If rec_dev is not NULL it receives
+ * the step record (qx,qy,qz,sx,sy,sz) per query (n x 6 float32).  nn_dev may
+ * be NULL when rec_dev is given.  Exact: a float32 screen with a proven error
+ * margin keeps every candidate that could be the float64 minimum.  A query
+ * with a NaN or infinite coordinate gets index -1 and NaN for s. */
+gp_status gp_nn(gp_band* band, const float* q_dev, int64_t n, int32_t* nn_dev, float* rec_dev);
+
+/* ------------------------------------------------------------------- step */
+
+typedef struct gp_loss_w {
+  float alpha;  /* weight of L_TV      (Eq. 8; paper: 1, or 2 for noisy input) */
+  float beta;   /* weight of L_Surface (Eq. 8; paper: 1)                        */
+  float gamma;  /* weight of L_grad    (Eq. 8; paper: 0.005)                    */
+} gp_loss_w;
+
+#define GP_STEP_DETERMINISTIC 1u /* fixed-point gradient sums: bitwise equal
+                                    results run to run (band needs
+                                    GP_BAND_DETERMINISTIC)                      */
+#define GP_STEP_NO_TV 2u         /* leave out the L_TV term and its gradient   */
+#define GP_STEP_LOSS_ONLY 4u     /* compute the loss only; grad_dev untouched  */
+
+/* Loss slots written to loss_dev (8 floats). */
+#define GP_LOSS_TOTAL 0 /* L = L_Pull + alpha L_TV + beta L_Surface + gamma L_grad */
+#define GP_LOSS_PULL 1  /* mean over valid queries of |p - NN(q)|  (Eq. 4)         */
+#define GP_LOSS_GRAD 2  /* mean of 1 - cos(grad f(q), grad f(NN(q))) (Eq. 7)       */
+#define GP_LOSS_SURF 3  /* mean of |f(NN(q))|                         (Eq. 6)       */
+#define GP_LOSS_TV 4    /* mean over T of sqrt(sum of 6 squared differences) (Eq. 5) */
+#define GP_LOSS_BV 5    /* B_v, the number of valid queries (as float)             */
+#define GP_LOSS_T 6     /* |T| (as float)                                          */
+
+/* One forward + hand-written backward pass of Eq. 8 over B step records
+ * rec_dev (B x 6 float32: q then NN(q), e.g. from gp_nn).  Query terms are
+ * averaged over the B_v valid queries, L_TV over T.  Writes the loss slots to
+ * loss_dev (8 floats) and, unless GP_STEP_LOSS_ONLY, overwrites grad_dev
+ * (V_stored floats, storage order) with dL/dD at every stored slot (0 at
+ * padding).  If nvalid_dev is not NULL, only the first *nvalid_dev records are
+ * read and B_v is taken from it (records must then all be valid); otherwise all
+ * B records are read and B_v is counted.  If d_dev is not NULL the values are
+ * read from it (V_stored floats) instead of the band's own.  Errors:
+ * GP_ERR_ARG (B < 0, null rec/loss, B >= 2^31, rec_dev not 8-byte aligned),
+ * GP_ERR_STATE (deterministic
+ * flag on a band built without GP_BAND_DETERMINISTIC). */
+gp_status gp_step(gp_band* band, const float* rec_dev, int64_t B, const int32_t* nvalid_dev,
+                  const float* d_dev, const gp_loss_w* w, float* grad_dev, float* loss_dev,
+                  uint32_t flags);
+
+/* ----------------------------------------------------------------- update */
+
+typedef struct gp_adam {
+  float lr;     /* learning rate (world units per step)                 */
+  float beta1;  /* 0.9   */
+  float beta2;  /* 0.999 */
+  float eps;    /* 1e-8  */
+} gp_adam;
+
+/* Adam (Kingma and Ba) at step `step` >= 1 on every trainable vertex:
+ * m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
+ * d -= lr * (m / (1-b1^step)) / (sqrt(v / (1-b2^step)) + eps),
+ * with g = grad_dev (V_stored floats, storage order).  Vertices outside the
+ * trainable set are left untouched (Sec. 3: only variables in the bandwidth are
+ * optimised).  Errors: GP_ERR_ARG (step < 1, null pointers). */
+gp_status gp_update(gp_band* band, const float* grad_dev, const gp_adam* hp, int64_t step);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GRIDPULL_H */

@@ -309,7 +309,8 @@ def box_muller3(words) -> np.ndarray:
 
 
 def feistel_bits(J: int) -> int:
-    m = max(2, int(math.ceil(math.log2(max(J, 2)))))
+    """Even bit width m >= 2 with 2^m >= J."""
+    m = max(2, (int(J) - 1).bit_length())
     return m + (m & 1)
 
 

@@ -1,0 +1,271 @@
+// Internal declarations of libgridpull: the context and band objects, error
+// plumbing, launch helpers and the small device functions every kernel shares
+// (exact cell lookup, brick addressing, Philox4x32-10, Box-Muller, Feistel).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "gridpull.h"
+
+// ------------------------------------------------------------------ objects
+struct gp_prof_rec {
+  const char* name;
+  cudaEvent_t start, stop;
+};
+
+struct gp_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int num_sms = 0;
+  std::string err;
+  // Tracing: launch counter (always on) and, while profiling, one pair of
+  // CUDA events around every kernel launch on the context's stream.
+  int64_t launches = 0;
+  bool profiling = false;
+  std::vector<gp_prof_rec> prof;
+  std::vector<cudaEvent_t> event_pool;
+};
+
+// Record the start event of the next launch (profiling only).
+void gp_prof_pre(gp_ctx* ctx);
+// Record the stop event and count the launch.
+void gp_prof_post(gp_ctx* ctx, const char* name);
+
+// Launch a kernel of this library: counted, traced while profiling, checked.
+#define GP_KERNEL(ctx, name, ...)                            \
+  do {                                                       \
+    gp_prof_pre(ctx);                                        \
+    __VA_ARGS__;                                             \
+    gp_prof_post(ctx, name);                                 \
+    GP_LAUNCH_CHECK(ctx, name);                              \
+  } while (0)
+
+// Number of fp64 partial-sum slots the reduction kernels may use per call.
+constexpr int GP_MAX_PARTIAL_BLOCKS = 4096;
+// Device int slots of gp_band::dev_ints.
+enum { GP_DI_NVALID = 0, GP_DI_ERROR = 1, GP_DI_COUNT = 8 };
+// Error bits raised by kernels in dev_ints[GP_DI_ERROR].
+enum { GP_EF_NUMERIC = 1, GP_EF_TIMEOUT = 2, GP_EF_RANGE = 4 };
+
+struct gp_band {
+  gp_ctx* ctx = nullptr;
+  int R = 0, M1 = 0, M2 = 0, nb = 0, knn_k = 0, G = 0;
+  uint32_t flags = 0;
+  int64_t J = 0, n_bricks = 0, n_active = 0;
+  int64_t V_trainable = 0, V_tv = 0, n_pull = 0, n_occ = 0;
+
+  // Brick storage: brick_table[(bz*nb + by)*nb + bx] = slot or -1.
+  int32_t* brick_table = nullptr;
+  int32_t* brick_coord = nullptr;  // n_bricks x 3 (bx, by, bz)
+  uint32_t* masks = nullptr;       // n_bricks x 48 words: [T 16][trainable 16][pull 16]
+  int32_t* active = nullptr;       // slots of bricks with a trainable vertex
+  float* D = nullptr;              // values, V_stored
+  float* m = nullptr;              // Adam first moment
+  float* v = nullptr;              // Adam second moment
+  unsigned long long* acc = nullptr;  // deterministic fixed-point gradient (V_stored)
+
+  // Point cloud: original order copy, cell list sorted copy, sigma, permutation.
+  float* pts = nullptr;            // J x 3
+  float4* pts_sorted = nullptr;    // J: x, y, z, original index (int bits)
+  int32_t* cell_start = nullptr;   // G^3 + 1
+  float* sigma = nullptr;          // J
+  int32_t* perm = nullptr;         // J: Pi_e of the cached epoch
+  bool perm_valid = false;
+  uint64_t perm_seed = 0;
+  uint32_t perm_epoch = 0;
+
+  // Scratch for reductions and counters.
+  double* partials = nullptr;      // GP_MAX_PARTIAL_BLOCKS x 8
+  int32_t* dev_ints = nullptr;     // GP_DI_COUNT
+
+  int64_t V_stored() const { return n_bricks * 512; }
+};
+
+// ------------------------------------------------------------ error helpers
+gp_status gp_fail(gp_ctx* ctx, gp_status st, const std::string& msg);
+gp_status gp_cuda_fail(gp_ctx* ctx, cudaError_t e, const char* what);
+
+#define GP_CUDA(ctx, call)                                   \
+  do {                                                       \
+    cudaError_t _e = (call);                                 \
+    if (_e != cudaSuccess) return gp_cuda_fail(ctx, _e, #call); \
+  } while (0)
+
+#define GP_LAUNCH_CHECK(ctx, what)                           \
+  do {                                                       \
+    cudaError_t _e = cudaGetLastError();                     \
+    if (_e != cudaSuccess) return gp_cuda_fail(ctx, _e, what); \
+  } while (0)
+
+template <typename T>
+gp_status gp_alloc(gp_ctx* ctx, T** p, size_t count, const char* what) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return gp_fail(ctx, e == cudaErrorMemoryAllocation ? GP_ERR_OOM : GP_ERR_CUDA,
+                   std::string("cudaMalloc failed for ") + what + ": " + cudaGetErrorString(e));
+  }
+  return GP_OK;
+}
+
+inline void gp_free(void* p) {
+  if (p) cudaFree(p);
+}
+
+inline unsigned gp_blocks(int64_t n, int threads, int64_t cap = 1 << 30) {
+  int64_t b = (n + threads - 1) / threads;
+  if (b < 1) b = 1;
+  if (b > cap) b = cap;
+  return (unsigned)b;
+}
+
+// Device-wide exclusive scan of n int32 counts in place; returns the total in
+// *total_host (synchronises).  Scratch is allocated and freed inside (set-up
+// paths only).
+gp_status gp_exclusive_scan_i32(gp_ctx* ctx, int32_t* data, int64_t n, int64_t* total_host);
+
+// Feistel round-trip used by the sampler (also needed on the host for checks).
+gp_status gp_build_permutation(gp_band* band, uint64_t seed, uint32_t epoch);
+
+// ------------------------------------------------------ device: geometry
+// Exact cell of one float32 coordinate: t = (x + 1) * R/2.  x + 1 is split
+// into s + e without error (TwoSum) and R/2 is a power of two, so t_hi + t_lo
+// is the real value; floor is taken on it.  The _rn intrinsics keep the
+// compiler from contracting any step into an FMA.
+struct gp_cell1 {
+  int c;      // floor(t), unclamped
+  float t;    // t - c, in [0, 1]
+};
+
+__device__ __forceinline__ gp_cell1 gp_cell_exact(float x, float half_r) {
+  gp_cell1 out;
+  if (!(fabsf(x) < 1.0e30f)) {  // NaN or huge: far outside
+    out.c = -(1 << 30);
+    out.t = 0.f;
+    return out;
+  }
+  float s = __fadd_rn(x, 1.0f);
+  float bb = __fsub_rn(s, x);
+  float e = __fadd_rn(__fsub_rn(x, __fsub_rn(s, bb)), __fsub_rn(1.0f, bb));
+  float thi = __fmul_rn(s, half_r);
+  float tlo = __fmul_rn(e, half_r);
+  float fl = floorf(thi);
+  if (thi == fl && tlo < 0.f) fl -= 1.0f;
+  out.c = (int)fl;
+  out.t = __fadd_rn(__fsub_rn(thi, fl), tlo);
+  return out;
+}
+
+// Brick slot of vertex (i,j,k), or -1 when the brick is not stored or the
+// vertex is outside the virtual brick grid.
+__device__ __forceinline__ int gp_brick_slot(const int32_t* __restrict__ table, int nb, int i, int j,
+                                             int k) {
+  int bx = i >> 3, by = j >> 3, bz = k >> 3;
+  if ((unsigned)bx >= (unsigned)nb || (unsigned)by >= (unsigned)nb || (unsigned)bz >= (unsigned)nb) return -1;
+  return __ldg(table + ((int64_t)bz * nb + by) * nb + bx);
+}
+
+__device__ __forceinline__ int gp_local(int i, int j, int k) {
+  return (((k & 7) << 3) | (j & 7)) << 3 | (i & 7);
+}
+
+__device__ __forceinline__ int64_t gp_vaddr(int slot, int i, int j, int k) {
+  return (int64_t)slot * 512 + gp_local(i, j, k);
+}
+
+__device__ __forceinline__ bool gp_mask_bit(const uint32_t* __restrict__ masks, int slot, int which,
+                                            int local) {
+  uint32_t w = __ldg(masks + (int64_t)slot * 48 + which * 16 + (local >> 5));
+  return (w >> (local & 31)) & 1u;
+}
+
+// --------------------------------------------------- device: Philox4x32-10
+// Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3"
+// (SC'11): ten rounds of two 32x32->64 products; the key is bumped by the
+// Weyl increments between rounds.
+struct gp_u4 {
+  uint32_t x, y, z, w;
+};
+
+__device__ __forceinline__ gp_u4 gp_philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                           uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    uint32_t lo0 = 0xD2511F53u * c0;
+    uint32_t hi0 = __umulhi(0xD2511F53u, c0);
+    uint32_t lo1 = 0xCD9E8D57u * c2;
+    uint32_t hi1 = __umulhi(0xCD9E8D57u, c2);
+    uint32_t n0 = hi1 ^ c1 ^ k0;
+    uint32_t n2 = hi0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return {c0, c1, c2, c3};
+}
+
+// Box-Muller on two word pairs -> three standard normals (float32).
+__device__ __forceinline__ float3 gp_box_muller3(gp_u4 w) {
+  const float s24 = 5.9604644775390625e-08f;  // 2^-24
+  float u1 = (float)((w.x >> 8) + 1u) * s24;
+  float u2 = (float)(w.y >> 8) * s24;
+  float u3 = (float)((w.z >> 8) + 1u) * s24;
+  float u4 = (float)(w.w >> 8) * s24;
+  float r1 = sqrtf(-2.0f * logf(u1));
+  float r2 = sqrtf(-2.0f * logf(u3));
+  float s1, c1, s2, c2;
+  sincospif(2.0f * u2, &s1, &c1);
+  sincospif(2.0f * u4, &s2, &c2);
+  return make_float3(r1 * c1, r1 * s1, r2 * c2);
+}
+
+// 4-round balanced Feistel network on 2*half bits; the round function is word
+// 0 of Philox4x32-10 at counter (value, round, epoch, 1).
+__device__ __forceinline__ uint32_t gp_feistel(uint32_t x, int half, uint32_t epoch, uint32_t k0,
+                                               uint32_t k1) {
+  uint32_t mask = (half >= 32) ? 0xFFFFFFFFu : ((1u << half) - 1u);
+  uint32_t left = x >> half, right = x & mask;
+#pragma unroll
+  for (uint32_t r = 0; r < 4; ++r) {
+    uint32_t f = gp_philox(right, r, epoch, 1u, k0, k1).x & mask;
+    uint32_t nl = right;
+    right = left ^ f;
+    left = nl;
+  }
+  return (left << half) | right;
+}
+
+__host__ __device__ inline int gp_feistel_bits(int64_t J) {
+  int m = 2;
+  while ((int64_t(1) << m) < J) ++m;
+  return m + (m & 1);
+}
+
+// ------------------------------------------------------ device: reductions
+__device__ __forceinline__ float gp_warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ double gp_warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ int gp_warp_sum_i(int v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}

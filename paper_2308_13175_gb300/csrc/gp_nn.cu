@@ -1,0 +1,337 @@
+// Nearest surface point NN(q) (Eq. 4) and the per-point sampling sigma
+// (distance to the k-th nearest other point), both by an exact search over a
+// uniform cell list of the cloud.  The paper organises the points in a KD-tree
+// (Sec. 3 "Discrete Grids"); a GPU walks a uniform grid far better than a
+// pointer-chasing tree, and the search below is exact all the same.
+//
+// Exactness of gp_nn.  The answer is defined in float64:
+//   D_j = ((qx-sx)^2 + (qy-sy)^2) + (qz-sz)^2 from the float32 inputs,
+//   NN = argmin_j D_j, ties to the lowest j.
+// The scan works in float32.  With E_j the exact squared distance, the float32
+// value is within a relative 5u (u = 2^-24) of E_j (plus an absolute 1e-30
+// covering underflow) and the float64 value within 3*2^-53.  Keeping the
+// smallest float32 distance b1 (index j1) and the second smallest b2 over all
+// scanned points: if b2 > b1 (1 + 2 eps) + 1e-30 with eps = 2^-18 >> 5u, every
+// other point has E_k > E_j1 (1 + eps), hence a larger float64 value, so j1 is
+// the float64 answer.  Otherwise (a near tie, e.g. duplicate points) the
+// scanned cells are visited again and every point within that margin is ranked
+// by its float64 value and index.  Rings of cells are scanned around the
+// query's cell until the distance from q to the scanned box, less a rounding
+// margin of 1e-5 (1 + |q|_inf), exceeds sqrt(b1 (1 + 8 eps)), so no unscanned
+// point can enter the comparison.
+#include <cmath>
+
+#include "gp_internal.cuh"
+
+namespace {
+
+constexpr float NN_EPS = 3.814697265625e-06f;  // 2^-18
+constexpr float NN_TINY = 1e-30f;
+
+struct NNGrid {
+  const float4* __restrict__ pts;      // sorted by cell: x, y, z, original index bits
+  const int32_t* __restrict__ start;   // G^3 + 1
+  int G;
+  float half_g;  // G / 2
+  float cs;      // 2 / G
+};
+
+__device__ __forceinline__ int nn_cell(float x, const NNGrid& g) {
+  float t = __fmul_rn(__fadd_rn(x, 1.0f), g.half_g);
+  int c = (t < 0.f) ? -1 : (int)floorf(fminf(t, 1.0e6f));
+  return min(max(c, 0), g.G - 1);
+}
+
+// Lower bound on the distance from q to any point outside the box of cells
+// [c - r, c + r]; returns +inf when the box covers the whole grid.
+__device__ __forceinline__ float nn_gap(const float q[3], const int c[3], int r, const NNGrid& g) {
+  float gap = INFINITY;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (c[a] - r > 0) {
+      float lo = -1.0f + (float)(c[a] - r) * g.cs;
+      gap = fminf(gap, q[a] - lo);
+    }
+    if (c[a] + r < g.G - 1) {
+      float hi = -1.0f + (float)(c[a] + r + 1) * g.cs;
+      gap = fminf(gap, hi - q[a]);
+    }
+  }
+  return gap;
+}
+
+__device__ __forceinline__ float nn_margin(const float q[3]) {
+  float m = fmaxf(fabsf(q[0]), fmaxf(fabsf(q[1]), fabsf(q[2])));
+  return 1e-5f * (2.0f + m);
+}
+
+// Visit every cell of ring r (Chebyshev shell) as contiguous point ranges.
+template <typename F>
+__device__ __forceinline__ void nn_ring(const int c[3], int r, const NNGrid& g, F&& visit) {
+  const int G = g.G;
+  for (int dz = -r; dz <= r; ++dz) {
+    int cz = c[2] + dz;
+    if (cz < 0 || cz >= G) continue;
+    for (int dy = -r; dy <= r; ++dy) {
+      int cy = c[1] + dy;
+      if (cy < 0 || cy >= G) continue;
+      int64_t row = ((int64_t)cz * G + cy) * G;
+      bool full = (dz == -r || dz == r || dy == -r || dy == r);
+      if (full) {
+        int x0 = max(c[0] - r, 0), x1 = min(c[0] + r, G - 1);
+        visit(__ldg(g.start + row + x0), __ldg(g.start + row + x1 + 1));
+      } else {
+        int xa = c[0] - r, xb = c[0] + r;
+        if (xa >= 0) visit(__ldg(g.start + row + xa), __ldg(g.start + row + xa + 1));
+        if (xb < G) visit(__ldg(g.start + row + xb), __ldg(g.start + row + xb + 1));
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ double nn_d64(const float q[3], float4 p) {
+  double dx = __dsub_rn((double)q[0], (double)p.x);
+  double dy = __dsub_rn((double)q[1], (double)p.y);
+  double dz = __dsub_rn((double)q[2], (double)p.z);
+  return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+}
+
+__global__ void k_point_cells(const float* __restrict__ pts, int64_t J, NNGrid g, int32_t* __restrict__ cid,
+                              int32_t* __restrict__ counts) {
+  int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= J) return;
+  int cx = nn_cell(pts[3 * j], g), cy = nn_cell(pts[3 * j + 1], g), cz = nn_cell(pts[3 * j + 2], g);
+  int32_t c = (int32_t)(((int64_t)cz * g.G + cy) * g.G + cx);
+  cid[j] = c;
+  atomicAdd(counts + c, 1);
+}
+
+__global__ void k_point_scatter(const float* __restrict__ pts, int64_t J, const int32_t* __restrict__ cid,
+                                const int32_t* __restrict__ start, int32_t* __restrict__ cursor,
+                                float4* __restrict__ sorted) {
+  int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= J) return;
+  int32_t c = cid[j];
+  int32_t pos = start[c] + atomicAdd(cursor + c, 1);
+  sorted[pos] = make_float4(pts[3 * j], pts[3 * j + 1], pts[3 * j + 2], __int_as_float((int)j));
+}
+
+// sigma_j: distance to the k-th nearest other point, by a bounded max-heap.
+__global__ void __launch_bounds__(128) k_knn_sigma(NNGrid g, int64_t J, int k, float* __restrict__ sigma) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= J) return;
+  float4 me = g.pts[t];
+  int self = __float_as_int(me.w);
+  float heap[64];
+  int cnt = 0;
+  if (k <= 0) {
+    sigma[self] = 0.f;
+    return;
+  }
+  float q[3] = {me.x, me.y, me.z};
+  int c[3] = {nn_cell(q[0], g), nn_cell(q[1], g), nn_cell(q[2], g)};
+  float margin = nn_margin(q);
+  for (int r = 0; r <= g.G; ++r) {
+    nn_ring(c, r, g, [&](int a, int b) {
+      for (int p = a; p < b; ++p) {
+        float4 P = g.pts[p];
+        if (__float_as_int(P.w) == self) continue;
+        float dx = q[0] - P.x, dy = q[1] - P.y, dz = q[2] - P.z;
+        float d = dx * dx + dy * dy + dz * dz;
+        if (cnt < k) {
+          // sift up
+          int i = cnt++;
+          while (i > 0) {
+            int par = (i - 1) >> 1;
+            if (heap[par] >= d) break;
+            heap[i] = heap[par];
+            i = par;
+          }
+          heap[i] = d;
+        } else if (d < heap[0]) {
+          // replace root, sift down
+          int i = 0;
+          while (true) {
+            int l = 2 * i + 1;
+            if (l >= k) break;
+            int m = (l + 1 < k && heap[l + 1] > heap[l]) ? l + 1 : l;
+            if (heap[m] <= d) break;
+            heap[i] = heap[m];
+            i = m;
+          }
+          heap[i] = d;
+        }
+      }
+    });
+    if (cnt == k) {
+      float gap = nn_gap(q, c, r, g);
+      if (gap == INFINITY) break;
+      float gs = gap - margin;
+      if (gs > 0.f && gs * gs > heap[0] * (1.0f + 8.0f * NN_EPS) + NN_TINY) break;
+    } else if (nn_gap(q, c, r, g) == INFINITY) {
+      break;
+    }
+  }
+  sigma[self] = cnt > 0 ? sqrtf(heap[0]) : 0.f;
+}
+
+__global__ void __launch_bounds__(256) k_nn(NNGrid g, const float* __restrict__ qin, int64_t n,
+                                            const float* __restrict__ pts_orig, int32_t* __restrict__ nn_out,
+                                            float* __restrict__ rec) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float q[3] = {qin[3 * i], qin[3 * i + 1], qin[3 * i + 2]};
+  int c[3] = {nn_cell(q[0], g), nn_cell(q[1], g), nn_cell(q[2], g)};
+  float margin = nn_margin(q);
+  float b1 = INFINITY, b2 = INFINITY;
+  int j1 = 0x7fffffff;
+  int r_end = 0;
+  for (int r = 0; r <= g.G; ++r) {
+    nn_ring(c, r, g, [&](int a, int b) {
+      for (int p = a; p < b; ++p) {
+        float4 P = g.pts[p];
+        float dx = q[0] - P.x, dy = q[1] - P.y, dz = q[2] - P.z;
+        float d = dx * dx + dy * dy + dz * dz;
+        int j = __float_as_int(P.w);
+        if (d < b1 || (d == b1 && j < j1)) {
+          b2 = b1;
+          b1 = d;
+          j1 = j;
+        } else if (d < b2) {
+          b2 = d;
+        }
+      }
+    });
+    r_end = r;
+    float gap = nn_gap(q, c, r, g);
+    if (gap == INFINITY) break;
+    if (b1 < INFINITY) {
+      float gs = gap - margin;
+      if (gs > 0.f && gs * gs > b1 * (1.0f + 8.0f * NN_EPS) + NN_TINY) break;
+    }
+  }
+  int best = j1;
+  if (j1 == 0x7fffffff) {
+    // Non-finite query: no point compares below it.  Report -1, NaN record.
+    if (nn_out) nn_out[i] = -1;
+    if (rec) {
+      for (int a = 0; a < 6; ++a) rec[6 * i + a] = a < 3 ? q[a] : __int_as_float(0x7fc00000);
+    }
+    return;
+  }
+  if (!(b2 > b1 * (1.0f + 2.0f * NN_EPS) + NN_TINY)) {
+    // Near tie: rank every point within the margin by its float64 distance.
+    float thr = b1 * (1.0f + 2.0f * NN_EPS) + NN_TINY;
+    double bd = INFINITY;
+    int bj = 0x7fffffff;
+    for (int r = 0; r <= r_end; ++r) {
+      nn_ring(c, r, g, [&](int a, int b) {
+        for (int p = a; p < b; ++p) {
+          float4 P = g.pts[p];
+          float dx = q[0] - P.x, dy = q[1] - P.y, dz = q[2] - P.z;
+          float d = dx * dx + dy * dy + dz * dz;
+          if (d > thr) continue;
+          int j = __float_as_int(P.w);
+          double dd = nn_d64(q, P);
+          if (dd < bd || (dd == bd && j < bj)) {
+            bd = dd;
+            bj = j;
+          }
+        }
+      });
+    }
+    if (bj != 0x7fffffff) best = bj;
+  }
+  if (nn_out) nn_out[i] = best;
+  if (rec) {
+    rec[6 * i + 0] = q[0];
+    rec[6 * i + 1] = q[1];
+    rec[6 * i + 2] = q[2];
+    rec[6 * i + 3] = pts_orig[3 * (int64_t)best];
+    rec[6 * i + 4] = pts_orig[3 * (int64_t)best + 1];
+    rec[6 * i + 5] = pts_orig[3 * (int64_t)best + 2];
+  }
+}
+
+NNGrid make_grid(const gp_band* b) {
+  NNGrid g;
+  g.pts = b->pts_sorted;
+  g.start = b->cell_start;
+  g.G = b->G;
+  g.half_g = 0.5f * (float)b->G;
+  g.cs = 2.0f / (float)b->G;
+  return g;
+}
+
+}  // namespace
+
+// Point copy, cell list and sigma (called by gp_build_band).
+gp_status gp_build_points(gp_band* b, const float* pts_dev) {
+  gp_ctx* ctx = b->ctx;
+  cudaStream_t s = ctx->stream;
+  const int64_t J = b->J;
+  if (b->G <= 0) {
+    int G = (int)std::sqrt((double)J / 3.0);
+    b->G = std::min(std::max(G, 4), 512);
+  }
+  const int G = b->G;
+  const int64_t ncell = (int64_t)G * G * G;
+  gp_status st;
+  if ((st = gp_alloc(ctx, &b->pts, 3 * J, "points"))) return st;
+  GP_CUDA(ctx, cudaMemcpyAsync(b->pts, pts_dev, 3 * J * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  if ((st = gp_alloc(ctx, &b->pts_sorted, J, "sorted points"))) return st;
+  if ((st = gp_alloc(ctx, &b->cell_start, ncell + 1, "cell starts"))) return st;
+  int32_t *cid = nullptr, *cursor = nullptr;
+  if ((st = gp_alloc(ctx, &cid, J, "point cells"))) return st;
+  if ((st = gp_alloc(ctx, &cursor, ncell, "cell cursor"))) {
+    cudaFree(cid);
+    return st;
+  }
+  NNGrid g = make_grid(b);
+  cudaError_t e = cudaMemsetAsync(b->cell_start, 0, (ncell + 1) * sizeof(int32_t), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(cursor, 0, ncell * sizeof(int32_t), s);
+  if (e == cudaSuccess) {
+    k_point_cells<<<gp_blocks(J, 256), 256, 0, s>>>(b->pts, J, g, cid, b->cell_start);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) {
+    int64_t total = 0;
+    st = gp_exclusive_scan_i32(ctx, b->cell_start, ncell + 1, &total);
+    if (!st) {
+      k_point_scatter<<<gp_blocks(J, 256), 256, 0, s>>>(b->pts, J, cid, b->cell_start, cursor, b->pts_sorted);
+      e = cudaGetLastError();
+    }
+  }
+  cudaStreamSynchronize(s);
+  cudaFree(cid);
+  cudaFree(cursor);
+  if (st) return st;
+  if (e != cudaSuccess) return gp_cuda_fail(ctx, e, "point cell list");
+  if (b->knn_k > 0) {
+    if ((st = gp_alloc(ctx, &b->sigma, J, "sigma"))) return st;
+    if ((st = gp_alloc(ctx, &b->perm, J, "permutation"))) return st;
+    int k = (int)std::min<int64_t>(b->knn_k, J - 1);
+    GP_KERNEL(ctx, "k_knn_sigma", k_knn_sigma<<<gp_blocks(J, 128), 128, 0, s>>>(g, J, k, b->sigma));
+  }
+  return GP_OK;
+}
+
+extern "C" gp_status gp_band_sigma(const gp_band* b, float* sigma_dev) {
+  if (!b) return GP_ERR_ARG;
+  if (!sigma_dev) return gp_fail(b->ctx, GP_ERR_ARG, "gp_band_sigma: null output");
+  if (!b->sigma) return gp_fail(b->ctx, GP_ERR_STATE, "gp_band_sigma: band built with knn_k = 0");
+  GP_CUDA(b->ctx, cudaMemcpyAsync(sigma_dev, b->sigma, b->J * sizeof(float), cudaMemcpyDeviceToDevice,
+                                  b->ctx->stream));
+  return GP_OK;
+}
+
+extern "C" gp_status gp_nn(gp_band* b, const float* q_dev, int64_t n, int32_t* nn_dev, float* rec_dev) {
+  if (!b) return GP_ERR_ARG;
+  gp_ctx* ctx = b->ctx;
+  if (n < 0 || n >= (int64_t(1) << 31)) return gp_fail(ctx, GP_ERR_ARG, "gp_nn: n must be in [0, 2^31)");
+  if (n == 0) return GP_OK;
+  if (!q_dev || (!nn_dev && !rec_dev)) return gp_fail(ctx, GP_ERR_ARG, "gp_nn: null pointer");
+  NNGrid g = make_grid(b);
+  GP_KERNEL(ctx, "k_nn", k_nn<<<gp_blocks(n, 256), 256, 0, ctx->stream>>>(g, q_dev, n, b->pts, nn_dev, rec_dev));
+  return GP_OK;
+}

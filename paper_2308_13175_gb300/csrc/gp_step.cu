@@ -1,0 +1,530 @@
+// gp_step: the loss of Eq. 8 and its gradient dL/dD in one forward +
+// hand-written backward pass, and gp_update: Adam on the trainable vertices.
+//
+// Per valid query (q, s = NN(q)):
+//   f, g = grad f at q from the 8 corners of cell(q) (Eq. 3, in the cell's
+//          local coordinate t: trilinear lerps, g = dt f * R/2),
+//   n = g / max(|g|, 1e-12),  p = q - f n  (Sec. 3),  r = (q - s) - f n,
+//   l_pull = |r|  (Eq. 4),
+//   f_s, g_s at s from the 8 corners of cell(s),  n_s = g_s / max(|g_s|, 1e-12),
+//   l_grad = 1 - n . n_s  (Eq. 7),  l_surf = |f_s|  (Eq. 6).
+// Backward (w = 1/B_v):  u = r / |r|;  dL/df = -w u.n;
+//   dL/dn = -w f u - w gamma n_s;  dL/dg = (I - n n^T) dL/dn / |g|;
+//   dL/dn_s = -w gamma n;  dL/dg_s = (I - n_s n_s^T) dL/dn_s / |g_s|;
+//   dL/df_s = w beta sign(f_s);
+// each corner c of a cell receives dL/df w_c(t) + sum_a dL/dt_a dw_c/dt_a.
+// L_TV (Eq. 5): TV_i = sqrt(sum over in-grid axis neighbours (d_i - d_n)^2)
+// over the TV set T, averaged; its gradient is gathered per vertex,
+//   dTV/dd_i = [i in T] sum_n (d_i - d_n)/TV_i + sum_{n in T} (d_i - d_n)/TV_n.
+#include <cmath>
+
+#include "gp_internal.cuh"
+
+namespace {
+
+constexpr int Q_THREADS = 256;
+constexpr int TV_THREADS = 512;
+constexpr float NORM_FLOOR = 1e-12f;
+constexpr double FIX_SCALE = 4294967296.0;  // 2^32: fixed-point unit of the deterministic sums
+constexpr double FIX_LIMIT = 4.0e18;        // |value * 2^32| beyond this flags an overflow
+
+struct Grid {
+  const int32_t* __restrict__ table;
+  const uint32_t* __restrict__ masks;
+  const float* __restrict__ D;
+  int nb;
+  int R;
+  float half_r;  // R/2 = 1/h
+};
+
+struct Eval {
+  float f;
+  float gt[3];  // df/dt (t = local coordinate in cell units)
+};
+
+__device__ __forceinline__ void load_corners(const Grid& G, const int c[3], int slot, float d[8], bool& ok) {
+  if ((c[0] & 7) != 7 && (c[1] & 7) != 7 && (c[2] & 7) != 7) {
+    const float* base = G.D + gp_vaddr(slot, c[0], c[1], c[2]);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) d[k] = __ldg(base + (k & 1) + ((k >> 1) & 1) * 8 + (k >> 2) * 64);
+    return;
+  }
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    int i = c[0] + (k & 1), j = c[1] + ((k >> 1) & 1), kk = c[2] + (k >> 2);
+    int s = gp_brick_slot(G.table, G.nb, i, j, kk);
+    if (s < 0) {
+      ok = false;
+      d[k] = 0.f;
+    } else {
+      d[k] = __ldg(G.D + gp_vaddr(s, i, j, kk));
+    }
+  }
+}
+
+// Trilinear interpolation of Eq. 3 written as lerps along x, then y, then z.
+__device__ __forceinline__ Eval trilerp(const float d[8], const float t[3]) {
+  float a00 = d[1] - d[0], a10 = d[3] - d[2], a01 = d[5] - d[4], a11 = d[7] - d[6];
+  float e00 = fmaf(t[0], a00, d[0]), e10 = fmaf(t[0], a10, d[2]);
+  float e01 = fmaf(t[0], a01, d[4]), e11 = fmaf(t[0], a11, d[6]);
+  float by0 = e10 - e00, by1 = e11 - e01;
+  float f0 = fmaf(t[1], by0, e00), f1 = fmaf(t[1], by1, e01);
+  Eval r;
+  r.f = fmaf(t[2], f1 - f0, f0);
+  r.gt[2] = f1 - f0;
+  r.gt[1] = fmaf(t[2], by1 - by0, by0);
+  float ax0 = fmaf(t[1], a10 - a00, a00), ax1 = fmaf(t[1], a11 - a01, a01);
+  r.gt[0] = fmaf(t[2], ax1 - ax0, ax0);
+  return r;
+}
+
+struct Cells {
+  int cq[3], cs[3];
+  float tq[3], ts[3];
+  int slot_q, slot_s;
+};
+
+// Validity of a record (Sec. 3 pull band; readings in the header): q inside
+// the domain, cell(q) and cell(s) in the M1 band.
+__device__ __forceinline__ bool classify(const Grid& G, const float q[3], const float s[3], Cells& C) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    gp_cell1 g = gp_cell_exact(q[a], G.half_r);
+    if (g.c < 0 || g.c > G.R - 1) return false;
+    C.cq[a] = g.c;
+    C.tq[a] = g.t;
+    gp_cell1 h = gp_cell_exact(s[a], G.half_r);
+    if (h.c == -(1 << 30)) return false;
+    int cc = min(max(h.c, 0), G.R - 1);
+    C.cs[a] = cc;
+    C.ts[a] = h.t + (float)(h.c - cc);
+  }
+  C.slot_q = gp_brick_slot(G.table, G.nb, C.cq[0], C.cq[1], C.cq[2]);
+  if (C.slot_q < 0 || !gp_mask_bit(G.masks, C.slot_q, 2, gp_local(C.cq[0], C.cq[1], C.cq[2]))) return false;
+  C.slot_s = gp_brick_slot(G.table, G.nb, C.cs[0], C.cs[1], C.cs[2]);
+  if (C.slot_s < 0 || !gp_mask_bit(G.masks, C.slot_s, 2, gp_local(C.cs[0], C.cs[1], C.cs[2]))) return false;
+  return true;
+}
+
+__device__ __forceinline__ void load_rec(const float* __restrict__ rec, int64_t i, float q[3], float s[3]) {
+  const float2* r2 = reinterpret_cast<const float2*>(rec + 6 * i);
+  float2 a = __ldg(r2), b = __ldg(r2 + 1), c = __ldg(r2 + 2);
+  q[0] = a.x;
+  q[1] = a.y;
+  q[2] = b.x;
+  s[0] = b.y;
+  s[1] = c.x;
+  s[2] = c.y;
+}
+
+__global__ void k_count_valid(Grid G, const float* __restrict__ rec, int64_t B, int32_t* __restrict__ nvalid) {
+  int cnt = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < B; i += (int64_t)gridDim.x * blockDim.x) {
+    float q[3], s[3];
+    load_rec(rec, i, q, s);
+    Cells C;
+    cnt += classify(G, q, s, C) ? 1 : 0;
+  }
+  int w = gp_warp_sum_i(cnt);
+  if ((threadIdx.x & 31) == 0 && w) atomicAdd(nvalid, w);
+}
+
+// Scatter of one cell's 8 corner contributions.
+template <bool DET>
+__device__ __forceinline__ void scatter8(const Grid& G, float* __restrict__ grad, unsigned long long* __restrict__ acc,
+                                         int32_t* __restrict__ err, const int c[3], int slot, const float t[3],
+                                         float A, const float Gt[3]) {
+  float wx[2] = {1.f - t[0], t[0]}, wy[2] = {1.f - t[1], t[1]}, wz[2] = {1.f - t[2], t[2]};
+  bool fast = (c[0] & 7) != 7 && (c[1] & 7) != 7 && (c[2] & 7) != 7;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    int dx = k & 1, dy = (k >> 1) & 1, dz = k >> 2;
+    float sx = dx ? 1.f : -1.f, sy = dy ? 1.f : -1.f, sz = dz ? 1.f : -1.f;
+    float wyz = wy[dy] * wz[dz];
+    float val = A * wx[dx] * wyz + Gt[0] * sx * wyz + Gt[1] * wx[dx] * sy * wz[dz] + Gt[2] * wx[dx] * wy[dy] * sz;
+    int64_t addr;
+    if (fast) {
+      addr = gp_vaddr(slot, c[0], c[1], c[2]) + dx + dy * 8 + dz * 64;
+    } else {
+      int i = c[0] + dx, j = c[1] + dy, kk = c[2] + dz;
+      int s = gp_brick_slot(G.table, G.nb, i, j, kk);
+      if (s < 0) continue;
+      addr = gp_vaddr(s, i, j, kk);
+    }
+    if (DET) {
+      double x = (double)val * FIX_SCALE;
+      if (!(fabs(x) < FIX_LIMIT)) {
+        atomicOr(err, GP_EF_NUMERIC);
+        continue;
+      }
+      atomicAdd(acc + addr, (unsigned long long)(long long)llrint(x));
+    } else {
+      atomicAdd(grad + addr, val);
+    }
+  }
+}
+
+// Block reduction of three float sums into partials[block*8 + 0..2] (fp64).
+__device__ __forceinline__ void block_store3(double* __restrict__ partials, float a, float b, float c) {
+  __shared__ float red[3][Q_THREADS / 32];
+  a = gp_warp_sum(a);
+  b = gp_warp_sum(b);
+  c = gp_warp_sum(c);
+  int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    red[0][w] = a;
+    red[1][w] = b;
+    red[2][w] = c;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s0 = 0, s1 = 0, s2 = 0;
+    for (int k = 0; k < Q_THREADS / 32; ++k) {
+      s0 += red[0][k];
+      s1 += red[1][k];
+      s2 += red[2][k];
+    }
+    double* p = partials + (int64_t)blockIdx.x * 8;
+    p[0] = s0;
+    p[1] = s1;
+    p[2] = s2;
+  }
+}
+
+template <bool DET, bool GRAD>
+__global__ void __launch_bounds__(Q_THREADS) k_query(Grid G, const float* __restrict__ rec, int64_t B,
+                                                     const int32_t* __restrict__ nproc,
+                                                     const int32_t* __restrict__ bv, float beta, float gamma,
+                                                     float* __restrict__ grad, unsigned long long* __restrict__ acc,
+                                                     double* __restrict__ partials, int32_t* __restrict__ err) {
+  int64_t n = nproc ? (int64_t)(*nproc) : B;
+  if (n > B) n = B;
+  int bvv = *bv;
+  float w = bvv > 0 ? 1.0f / (float)bvv : 0.f;
+  if (DET) w = 1.0f;  // fixed-point sums are scaled by 1/B_v at the end
+  float sp = 0.f, sg = 0.f, ss = 0.f;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    float q[3], s[3];
+    load_rec(rec, i, q, s);
+    Cells C;
+    if (!classify(G, q, s, C)) continue;
+    bool ok = true;
+    float dq[8], ds[8];
+    load_corners(G, C.cq, C.slot_q, dq, ok);
+    load_corners(G, C.cs, C.slot_s, ds, ok);
+    if (!ok) {
+      atomicOr(err, GP_EF_RANGE);
+      continue;
+    }
+    Eval eq = trilerp(dq, C.tq);
+    Eval es = trilerp(ds, C.ts);
+    float g[3] = {eq.gt[0] * G.half_r, eq.gt[1] * G.half_r, eq.gt[2] * G.half_r};
+    float gs[3] = {es.gt[0] * G.half_r, es.gt[1] * G.half_r, es.gt[2] * G.half_r};
+    float gl = sqrtf(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+    float gls = sqrtf(gs[0] * gs[0] + gs[1] * gs[1] + gs[2] * gs[2]);
+    float inv = 1.0f / fmaxf(gl, NORM_FLOOR), invs = 1.0f / fmaxf(gls, NORM_FLOOR);
+    float nv[3] = {g[0] * inv, g[1] * inv, g[2] * inv};
+    float ns[3] = {gs[0] * invs, gs[1] * invs, gs[2] * invs};
+    float f = eq.f, fs = es.f;
+    float r[3] = {(q[0] - s[0]) - f * nv[0], (q[1] - s[1]) - f * nv[1], (q[2] - s[2]) - f * nv[2]};
+    float lp = sqrtf(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+    float cosv = nv[0] * ns[0] + nv[1] * ns[1] + nv[2] * ns[2];
+    sp += lp;
+    sg += 1.0f - cosv;
+    ss += fabsf(fs);
+    if (!GRAD) continue;
+    float ilp = lp > 0.f ? 1.0f / lp : 0.f;
+    float u[3] = {r[0] * ilp, r[1] * ilp, r[2] * ilp};
+    float un = u[0] * nv[0] + u[1] * nv[1] + u[2] * nv[2];
+    float dfq = -w * un;
+    float dn[3], dns[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      dn[a] = -w * f * u[a] - w * gamma * ns[a];
+      dns[a] = -w * gamma * nv[a];
+    }
+    float ndn = nv[0] * dn[0] + nv[1] * dn[1] + nv[2] * dn[2];
+    float nsdns = ns[0] * dns[0] + ns[1] * dns[1] + ns[2] * dns[2];
+    bool big = gl > NORM_FLOOR, bigs = gls > NORM_FLOOR;
+    float Gq[3], Gs[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      float dg = big ? (dn[a] - nv[a] * ndn) * inv : dn[a] * inv;
+      float dgs = bigs ? (dns[a] - ns[a] * nsdns) * invs : dns[a] * invs;
+      Gq[a] = dg * G.half_r;  // dL/dt = dL/dg * dg/dt
+      Gs[a] = dgs * G.half_r;
+    }
+    float dfs = fs > 0.f ? w * beta : (fs < 0.f ? -w * beta : 0.f);
+    scatter8<DET>(G, grad, acc, err, C.cq, C.slot_q, C.tq, dfq, Gq);
+    scatter8<DET>(G, grad, acc, err, C.cs, C.slot_s, C.ts, dfs, Gs);
+  }
+  block_store3(partials, sp, sg, ss);
+}
+
+__device__ __forceinline__ float vload(const Grid& G, int i, int j, int k, bool& ok) {
+  int s = gp_brick_slot(G.table, G.nb, i, j, k);
+  if (s < 0) {
+    ok = false;
+    return 0.f;
+  }
+  return __ldg(G.D + gp_vaddr(s, i, j, k));
+}
+
+__device__ __forceinline__ bool vin_t(const Grid& G, int i, int j, int k) {
+  int s = gp_brick_slot(G.table, G.nb, i, j, k);
+  return s >= 0 && gp_mask_bit(G.masks, s, 0, gp_local(i, j, k));
+}
+
+// TV_n of vertex (i,j,k) from its in-grid axis neighbours.
+__device__ __forceinline__ float tv_of(const Grid& G, int i, int j, int k, float dc, bool& ok) {
+  const int di[6] = {-1, 1, 0, 0, 0, 0}, dj[6] = {0, 0, -1, 1, 0, 0}, dk[6] = {0, 0, 0, 0, -1, 1};
+  float s = 0.f;
+#pragma unroll
+  for (int t = 0; t < 6; ++t) {
+    int a = i + di[t], b = j + dj[t], c = k + dk[t];
+    if (a < 0 || b < 0 || c < 0 || a > G.R || b > G.R || c > G.R) continue;
+    float e = dc - vload(G, a, b, c, ok);
+    s = fmaf(e, e, s);
+  }
+  return sqrtf(s);
+}
+
+// One block of 512 threads per brick (grid-stride over bricks).  Writes the
+// gradient of every stored slot: alpha/|T| * dTV/dd_i (+ the fixed-point query
+// sums in deterministic mode, which are cleared for the next step).
+template <bool DET, bool GRAD, bool TV>
+__global__ void __launch_bounds__(TV_THREADS) k_tv(Grid G, const int32_t* __restrict__ coord, int64_t n_bricks,
+                                                   float tv_scale, float* __restrict__ grad,
+                                                   unsigned long long* __restrict__ acc,
+                                                   const int32_t* __restrict__ bv, double* __restrict__ partials,
+                                                   int32_t* __restrict__ err) {
+  float tsum = 0.f;
+  float qscale = 0.f;
+  if (DET) {
+    int b = *bv;
+    qscale = b > 0 ? (float)(1.0 / ((double)b * FIX_SCALE)) : 0.f;
+  }
+  const int l = threadIdx.x;
+  for (int64_t slot = blockIdx.x; slot < n_bricks; slot += gridDim.x) {
+    int i = coord[3 * slot] * 8 + (l & 7);
+    int j = coord[3 * slot + 1] * 8 + ((l >> 3) & 7);
+    int k = coord[3 * slot + 2] * 8 + (l >> 6);
+    int64_t addr = slot * 512 + l;
+    float gsum = 0.f;
+    bool ok = true;
+    if (TV && i <= G.R && j <= G.R && k <= G.R) {
+      float di = __ldg(G.D + addr);
+      if (gp_mask_bit(G.masks, (int)slot, 0, l)) {
+        float tvi = tv_of(G, i, j, k, di, ok);
+        tsum += tvi;
+        if (GRAD && tvi > 0.f) {
+          const int xi[6] = {-1, 1, 0, 0, 0, 0}, xj[6] = {0, 0, -1, 1, 0, 0}, xk[6] = {0, 0, 0, 0, -1, 1};
+          float inv = 1.0f / tvi;
+          for (int t = 0; t < 6; ++t) {
+            int a = i + xi[t], b = j + xj[t], c = k + xk[t];
+            if (a < 0 || b < 0 || c < 0 || a > G.R || b > G.R || c > G.R) continue;
+            gsum += (di - vload(G, a, b, c, ok)) * inv;
+          }
+        }
+      }
+      if (GRAD) {
+        const int xi[6] = {-1, 1, 0, 0, 0, 0}, xj[6] = {0, 0, -1, 1, 0, 0}, xk[6] = {0, 0, 0, 0, -1, 1};
+        for (int t = 0; t < 6; ++t) {
+          int a = i + xi[t], b = j + xj[t], c = k + xk[t];
+          if (a < 0 || b < 0 || c < 0 || a > G.R || b > G.R || c > G.R) continue;
+          if (!vin_t(G, a, b, c)) continue;
+          float dn = vload(G, a, b, c, ok);
+          float tvn = tv_of(G, a, b, c, dn, ok);
+          if (tvn > 0.f) gsum += (di - dn) / tvn;
+        }
+      }
+    }
+    if (!ok) atomicOr(err, GP_EF_RANGE);
+    if (GRAD) {
+      float gv = tv_scale * gsum;
+      if (DET) {
+        long long a = (long long)acc[addr];
+        acc[addr] = 0ull;
+        gv += (float)((double)a * (double)qscale);
+      }
+      grad[addr] = gv;
+    }
+  }
+  // block reduction of the TV sum into partials[block*8 + 3]
+  __shared__ float red[TV_THREADS / 32];
+  float w = gp_warp_sum(tsum);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = w;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0;
+    for (int k = 0; k < TV_THREADS / 32; ++k) s += red[k];
+    partials[(int64_t)blockIdx.x * 8 + 3] = s;
+  }
+}
+
+__global__ void k_finalize(const double* __restrict__ partials, int q_blocks, int tv_blocks,
+                           const int32_t* __restrict__ bv, int64_t n_tv, float alpha, float beta, float gamma,
+                           int tv_on, float* __restrict__ loss) {
+  __shared__ double red[4][32];
+  double s[4] = {0, 0, 0, 0};
+  for (int b = threadIdx.x; b < q_blocks; b += blockDim.x) {
+    s[0] += partials[(int64_t)b * 8 + 0];
+    s[1] += partials[(int64_t)b * 8 + 1];
+    s[2] += partials[(int64_t)b * 8 + 2];
+  }
+  for (int b = threadIdx.x; b < tv_blocks; b += blockDim.x) s[3] += partials[(int64_t)b * 8 + 3];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    double v = gp_warp_sum_d(s[c]);
+    if ((threadIdx.x & 31) == 0) red[c][threadIdx.x >> 5] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t[4] = {0, 0, 0, 0};
+    for (int c = 0; c < 4; ++c)
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t[c] += red[c][w];
+    int b = *bv;
+    double lp = b > 0 ? t[0] / b : 0.0, lg = b > 0 ? t[1] / b : 0.0, ls = b > 0 ? t[2] / b : 0.0;
+    double lt = (tv_on && n_tv > 0) ? t[3] / (double)n_tv : 0.0;
+    loss[GP_LOSS_TOTAL] = (float)(lp + alpha * lt + beta * ls + gamma * lg);
+    loss[GP_LOSS_PULL] = (float)lp;
+    loss[GP_LOSS_GRAD] = (float)lg;
+    loss[GP_LOSS_SURF] = (float)ls;
+    loss[GP_LOSS_TV] = (float)lt;
+    loss[GP_LOSS_BV] = (float)b;
+    loss[GP_LOSS_T] = (float)n_tv;
+    loss[7] = 0.f;
+  }
+}
+
+__global__ void __launch_bounds__(512) k_adam(const int32_t* __restrict__ active, int64_t n_active,
+                                              const uint32_t* __restrict__ masks, const float* __restrict__ grad,
+                                              float* __restrict__ D, float* __restrict__ m, float* __restrict__ v,
+                                              float lr, float b1, float b2, float eps, float bc1, float bc2) {
+  const int l = threadIdx.x;
+  for (int64_t a = blockIdx.x; a < n_active; a += gridDim.x) {
+    int slot = active[a];
+    if (!gp_mask_bit(masks, slot, 1, l)) continue;
+    int64_t addr = (int64_t)slot * 512 + l;
+    float g = grad[addr];
+    float mm = fmaf(b1, m[addr], (1.0f - b1) * g);
+    float vv = fmaf(b2, v[addr], (1.0f - b2) * g * g);
+    m[addr] = mm;
+    v[addr] = vv;
+    float mh = mm / bc1, vh = vv / bc2;
+    D[addr] -= lr * mh / (sqrtf(vh) + eps);
+  }
+}
+
+unsigned q_grid(const gp_ctx* ctx, int64_t B) {
+  return gp_blocks(B, Q_THREADS, GP_MAX_PARTIAL_BLOCKS);
+}
+
+unsigned tv_grid(const gp_ctx* ctx, int64_t n_bricks) {
+  int64_t cap = (int64_t)ctx->num_sms * 4;
+  if (cap > GP_MAX_PARTIAL_BLOCKS) cap = GP_MAX_PARTIAL_BLOCKS;
+  return gp_blocks(n_bricks, 1, cap);
+}
+
+}  // namespace
+
+extern "C" gp_status gp_step(gp_band* b, const float* rec_dev, int64_t B, const int32_t* nvalid_dev,
+                             const float* d_dev, const gp_loss_w* w, float* grad_dev, float* loss_dev,
+                             uint32_t flags) {
+  if (!b) return GP_ERR_ARG;
+  gp_ctx* ctx = b->ctx;
+  if (B < 0 || B >= (int64_t(1) << 31)) return gp_fail(ctx, GP_ERR_ARG, "gp_step: B must be in [0, 2^31)");
+  if (!loss_dev || !w || (B > 0 && !rec_dev)) return gp_fail(ctx, GP_ERR_ARG, "gp_step: null pointer");
+  const bool grad_on = !(flags & GP_STEP_LOSS_ONLY);
+  const bool det = (flags & GP_STEP_DETERMINISTIC) != 0;
+  const bool tv_on = !(flags & GP_STEP_NO_TV);
+  if (grad_on && !grad_dev) return gp_fail(ctx, GP_ERR_ARG, "gp_step: null gradient output");
+  if (((uintptr_t)rec_dev & 7u) != 0) return gp_fail(ctx, GP_ERR_ARG, "gp_step: records must be 8-byte aligned");
+  if (det && grad_on && !b->acc)
+    return gp_fail(ctx, GP_ERR_STATE, "gp_step: deterministic mode needs a band built with GP_BAND_DETERMINISTIC");
+  cudaStream_t s = ctx->stream;
+  Grid G;
+  G.table = b->brick_table;
+  G.masks = b->masks;
+  G.D = d_dev ? d_dev : b->D;
+  G.nb = b->nb;
+  G.R = b->R;
+  G.half_r = 0.5f * (float)b->R;
+  int32_t* err = b->dev_ints + GP_DI_ERROR;
+  const int32_t* bv = nvalid_dev;
+  if (!bv) {
+    int32_t* cnt = b->dev_ints + GP_DI_NVALID;
+    GP_CUDA(ctx, cudaMemsetAsync(cnt, 0, sizeof(int32_t), s));
+    if (B > 0) {
+      GP_KERNEL(ctx, "k_count_valid", k_count_valid<<<q_grid(ctx, B), Q_THREADS, 0, s>>>(G, rec_dev, B, cnt));
+    }
+    bv = cnt;
+  }
+  const unsigned qb = q_grid(ctx, B);
+  const unsigned tb = tv_grid(ctx, b->n_bricks);
+  const float tv_scale = (tv_on && b->V_tv > 0) ? w->alpha / (float)b->V_tv : 0.f;
+  auto launch_tv = [&]() -> gp_status {
+    if (b->n_bricks == 0) {
+      GP_CUDA(ctx, cudaMemsetAsync(b->partials + 3, 0, sizeof(double), s));
+      return GP_OK;
+    }
+#define GP_TV(D_, G_, T_) \
+  k_tv<D_, G_, T_><<<tb, TV_THREADS, 0, s>>>(G, b->brick_coord, b->n_bricks, tv_scale, grad_dev, b->acc, bv, b->partials, err)
+    gp_prof_pre(ctx);
+    if (det && grad_on) {
+      if (tv_on) GP_TV(true, true, true); else GP_TV(true, true, false);
+    } else if (grad_on) {
+      if (tv_on) GP_TV(false, true, true); else GP_TV(false, true, false);
+    } else {
+      if (tv_on) GP_TV(false, false, true); else GP_TV(false, false, false);
+    }
+#undef GP_TV
+    gp_prof_post(ctx, "k_tv");
+    GP_LAUNCH_CHECK(ctx, "k_tv");
+    return GP_OK;
+  };
+  auto launch_q = [&]() -> gp_status {
+    gp_prof_pre(ctx);
+    if (det && grad_on)
+      k_query<true, true><<<qb, Q_THREADS, 0, s>>>(G, rec_dev, B, nvalid_dev, bv, w->beta, w->gamma, grad_dev, b->acc,
+                                                   b->partials, err);
+    else if (grad_on)
+      k_query<false, true><<<qb, Q_THREADS, 0, s>>>(G, rec_dev, B, nvalid_dev, bv, w->beta, w->gamma, grad_dev, b->acc,
+                                                    b->partials, err);
+    else
+      k_query<false, false><<<qb, Q_THREADS, 0, s>>>(G, rec_dev, B, nvalid_dev, bv, w->beta, w->gamma, grad_dev,
+                                                     b->acc, b->partials, err);
+    gp_prof_post(ctx, "k_query");
+    GP_LAUNCH_CHECK(ctx, "k_query");
+    return GP_OK;
+  };
+  gp_status st;
+  // The TV sweep writes (overwrites) the gradient; the query pass adds to it.
+  // In deterministic mode the query pass fills the fixed-point sums first and
+  // the sweep folds them in.
+  if (det && grad_on) {
+    if ((st = launch_q())) return st;
+    if ((st = launch_tv())) return st;
+  } else {
+    if ((st = launch_tv())) return st;
+    if ((st = launch_q())) return st;
+  }
+  GP_KERNEL(ctx, "k_finalize", k_finalize<<<1, 256, 0, s>>>(b->partials, (int)qb, b->n_bricks ? (int)tb : 1, bv, b->V_tv, w->alpha, w->beta,
+                               w->gamma, tv_on ? 1 : 0, loss_dev));
+  return GP_OK;
+}
+
+extern "C" gp_status gp_update(gp_band* b, const float* grad_dev, const gp_adam* hp, int64_t step) {
+  if (!b) return GP_ERR_ARG;
+  gp_ctx* ctx = b->ctx;
+  if (!grad_dev || !hp) return gp_fail(ctx, GP_ERR_ARG, "gp_update: null pointer");
+  if (step < 1) return gp_fail(ctx, GP_ERR_ARG, "gp_update: step must be >= 1");
+  if (b->n_active == 0) return GP_OK;
+  double bc1 = 1.0 - std::pow((double)hp->beta1, (double)step);
+  double bc2 = 1.0 - std::pow((double)hp->beta2, (double)step);
+  int64_t cap = (int64_t)ctx->num_sms * 4;
+  GP_KERNEL(ctx, "k_adam", k_adam<<<gp_blocks(b->n_active, 1, cap), 512, 0, ctx->stream>>>(b->active, b->n_active, b->masks, grad_dev, b->D,
+                                                                  b->m, b->v, hp->lr, hp->beta1, hp->beta2, hp->eps,
+                                                                  (float)bc1, (float)bc2));
+  return GP_OK;
+}

@@ -324,13 +324,28 @@ def gaussian_queries(points: np.ndarray, n: int, sigma, seed: int):
 
 def sphere_field(coords_ijk: np.ndarray, R: int, radius: float, noise_std: float, seed: int,
                  center=(0.0, 0.0, 0.0)) -> np.ndarray:
-    """Grid values |v - c| - radius (+ Gaussian noise) at integer vertex coordinates."""
+    """Grid values |v - c| - radius + noise at integer vertex coordinates.
+
+    The noise of a vertex depends only on (seed, vertex): one normal draw per
+    vertex of the whole (R+1)^3 grid, indexed by i + (R+1)(j + (R+1)k), so the
+    same vertex gets the same value whichever subset of vertices is asked for."""
     h = 2.0 / R
-    v = -1.0 + h * coords_ijk.astype(np.float64)
+    ijk = np.asarray(coords_ijk, dtype=np.int64)
+    v = -1.0 + h * ijk.astype(np.float64)
     d = np.linalg.norm(v - np.asarray(center), axis=1) - radius
     if noise_std > 0:
-        d = d + _rng(seed).normal(scale=noise_std, size=len(d))
+        n1 = R + 1
+        noise = _rng(seed).standard_normal(n1 ** 3, dtype=np.float32)
+        key = ijk[:, 0] + n1 * (ijk[:, 1] + n1 * ijk[:, 2])
+        d = d + noise_std * noise[key].astype(np.float64)
     return d.astype(np.float32)
+
+
+def all_vertices(R: int) -> np.ndarray:
+    """Integer coordinates of every vertex of the (R+1)^3 grid, key order."""
+    n1 = R + 1
+    k = np.arange(n1 ** 3, dtype=np.int64)
+    return np.stack([k % n1, (k // n1) % n1, k // (n1 * n1)], axis=1)
 
 
 def random_field(coords_ijk: np.ndarray, scale: float, seed: int) -> np.ndarray:

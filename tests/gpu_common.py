@@ -1,0 +1,61 @@
+"""Helpers shared by the GPU parity tests: build the library, move band
+exports to numpy, compare against the oracle with the stated tolerances."""
+import numpy as np
+import pytest
+
+# Tolerance of the parity contract: float32 GPU vs float64 oracle.
+REL_TOL = 1e-5
+
+
+def have_gpu():
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:
+        return False
+
+
+def build_lib():
+    from paper_2308_13175_gb300 import build
+    return build.build()
+
+
+def export_band(band):
+    """(ijk, values, flags, exists) of every stored slot, as numpy."""
+    from paper_2308_13175_gb300 import binding as gb
+    ijk, d, fl = gb.gp_band_export(band)
+    ijk = ijk.cpu().numpy().astype(np.int64)
+    d = d.cpu().numpy()
+    fl = fl.cpu().numpy()
+    return ijk, d, fl, (fl & 4) != 0
+
+
+def vertex_keys(ijk, R):
+    n = R + 1
+    return ijk[:, 0] + n * (ijk[:, 1] + n * ijk[:, 2])
+
+
+def dense_from_band(values, ijk, exists, R):
+    """Float64 dense grid ((R+1)^3,) holding the band's stored values."""
+    D = np.zeros((R + 1) ** 3, dtype=np.float64)
+    D[vertex_keys(ijk[exists], R)] = values[exists].astype(np.float64)
+    return D
+
+
+def assert_rel(got, want, tol=REL_TOL, what="value"):
+    got, want = float(got), float(want)
+    assert abs(got - want) <= tol * abs(want) + 1e-30, f"{what}: got {got!r}, want {want!r}"
+
+
+def assert_grad_close(g, ref, tol=REL_TOL, what="grad"):
+    """Norm-wise relative error <= tol and per-vertex
+    |g_i - ref_i| <= tol * max(|ref_i|, 1e-3 * max|ref|)."""
+    g = np.asarray(g, np.float64)
+    ref = np.asarray(ref, np.float64)
+    nrm = np.linalg.norm(ref)
+    err = np.linalg.norm(g - ref)
+    assert err <= tol * nrm, f"{what}: |g - ref| / |ref| = {err / max(nrm, 1e-300):.3e}"
+    floor = 1e-3 * np.max(np.abs(ref))
+    per = np.abs(g - ref) / np.maximum(np.abs(ref), floor)
+    worst = int(np.argmax(per))
+    assert per[worst] <= tol, f"{what}: vertex {worst} rel err {per[worst]:.3e} (got {g[worst]}, want {ref[worst]})"

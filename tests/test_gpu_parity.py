@@ -1,0 +1,393 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Contract: integer and set results bit-exact (band sets, NN indices); floating
+point within 1e-5 relative (loss terms; gradients norm-wise and per vertex
+against max(|g*_i|, 1e-3 max|g*|)); Adam deltas within 1e-5 * lr.  Inputs come
+from the seeded generators; expected values from the oracle only.
+"""
+import numpy as np
+import pytest
+
+from oracle import gridpull as o
+from paper_2308_13175_gb300 import synth
+
+from gpu_common import (REL_TOL, assert_grad_close, assert_rel, build_lib, dense_from_band, export_band,
+                         have_gpu, vertex_keys)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gb():
+    if not have_gpu():
+        pytest.skip("no CUDA device")
+    build_lib()
+    from paper_2308_13175_gb300 import binding
+    return binding
+
+
+@pytest.fixture(scope="module")
+def ctx(gb):
+    return gb.gp_create(0)
+
+
+@pytest.fixture(scope="module")
+def sphere5k():
+    return synth.sphere_cloud(5000, 0.5, seed=0)
+
+
+@pytest.fixture(scope="module")
+def object100k():
+    return synth.object_cloud(100_000, seed=1)
+
+
+def _band(gb, ctx, pts, R, M1, M2, knn_k=50, deterministic=False):
+    import torch
+    return gb.gp_build_band(ctx, torch.from_numpy(np.ascontiguousarray(pts)).cuda(), R, M1, M2, knn_k,
+                            deterministic=deterministic)
+
+
+def _edge_points():
+    return np.array([[1, 1, 1], [-1, -1, -1], [1, -1, 0.3], [-1, 0.999, -0.2], [0, 0, 0],
+                     [0.0625, -0.0625, 0.5]], np.float32)
+
+
+# ------------------------------------------------------------------ band
+@pytest.mark.parametrize("case", [("sphere", 64, 2, 2), ("sphere", 64, 1, 3), ("sphere", 32, 3, 1),
+                                  ("sphere", 16, -1, -1), ("object", 256, 2, 2), ("edge", 16, 3, 3),
+                                  ("edge", 16, 0, 0)])
+def test_band_sets_match_oracle(gb, ctx, sphere5k, object100k, case):
+    name, R, M1, M2 = case
+    pts = {"sphere": sphere5k, "object": object100k, "edge": _edge_points()}[name]
+    band = _band(gb, ctx, pts, R, M1, M2, knn_k=0)
+    ijk, d, fl, exists = export_band(band)
+    ref = o.band_sets(pts, R, M1, M2)
+    keys = vertex_keys(ijk, R)
+    assert np.all(fl[~exists] == 0)
+    assert np.array_equal(np.sort(keys[exists & ((fl & 1) != 0)]), ref["tv"])
+    assert np.array_equal(np.sort(keys[exists & ((fl & 2) != 0)]), ref["trainable"])
+    pull_v = ijk[exists & ((fl & 8) != 0)]
+    assert np.array_equal(np.sort(o.cell_key(pull_v, R)), ref["pull_cells"])
+    assert np.all(np.isin(ref["required"], keys[exists]))
+    assert len(np.unique(keys[exists])) == int(exists.sum())
+    info = band.info
+    assert info["V_tv"] == len(ref["tv"]) and info["V_trainable"] == len(ref["trainable"])
+    assert info["n_pull_cells"] == len(ref["pull_cells"])
+    assert info["n_occupied_cells"] == len(ref["occupied"])
+
+
+def test_init_sphere_matches_oracle(gb, ctx, sphere5k):
+    R = 64
+    band = _band(gb, ctx, sphere5k, R, 2, 2, knn_k=0)
+    gb.gp_band_init_sphere(band, (0.05, -0.02, 0.1), 0.3, 0.01, seed=7)
+    want_all = o.sphere_init(np.arange((R + 1) ** 3), R, (0.05, -0.02, 0.1), 0.3, 0.01, 7)
+    ijk, d, fl, exists = export_band(band)
+    want = want_all[vertex_keys(ijk[exists], R)]
+    assert np.max(np.abs(d[exists] - want) / (1 + np.abs(want))) < 2e-6
+    assert np.all(d[~exists] == 0)
+
+
+# ----------------------------------------------------------------- sigma
+def test_sigma_matches_oracle(gb, ctx, sphere5k, object100k):
+    pts = np.concatenate([sphere5k, sphere5k[:7]])  # exact duplicates
+    band = _band(gb, ctx, pts, 64, 2, 2, knn_k=50)
+    sig = gb.gp_band_sigma(band).cpu().numpy()
+    want = o.knn_sigma(pts, 50)
+    assert np.max(np.abs(sig - want) / want) < 1e-6
+    band = _band(gb, ctx, object100k, 256, 2, 2, knn_k=50)
+    sig = gb.gp_band_sigma(band).cpu().numpy()
+    idx = np.random.default_rng(0).choice(len(object100k), 1500, replace=False)
+    want = o.knn_sigma(object100k, 50, idx=idx)
+    assert np.max(np.abs(sig[idx] - want) / want) < 1e-6
+
+
+def test_sigma_small_clouds(gb, ctx):
+    pts = np.array([[0.1, 0.2, 0.3], [0.4, -0.1, 0.0], [0.1, 0.2, 0.3]], np.float32)
+    band = _band(gb, ctx, pts, 16, 1, 1, knn_k=50)
+    assert np.allclose(gb.gp_band_sigma(band).cpu().numpy(), o.knn_sigma(pts, 50), rtol=1e-6)
+    band = _band(gb, ctx, pts[:1], 16, 1, 1, knn_k=50)
+    assert gb.gp_band_sigma(band).cpu().numpy()[0] == 0.0
+
+
+# ------------------------------------------------------------ nearest point
+def _nn_gpu(gb, band, q):
+    import torch
+    qt = torch.from_numpy(np.ascontiguousarray(q, np.float32)).cuda()
+    nn = torch.empty(len(q), dtype=torch.int32, device="cuda")
+    rec = torch.empty((len(q), 6), dtype=torch.float32, device="cuda")
+    gb.gp_nn(band, qt, nn, rec)
+    return nn.cpu().numpy().astype(np.int64), rec.cpu().numpy()
+
+
+def test_nn_matches_bruteforce_sphere(gb, ctx, sphere5k):
+    band = _band(gb, ctx, sphere5k, 64, 2, 2, knn_k=0)
+    q1, _ = synth.gaussian_queries(sphere5k, 20000, 0.02, seed=3)
+    q2 = np.random.default_rng(4).uniform(-1.3, 1.3, size=(3001, 3)).astype(np.float32)
+    q = np.concatenate([q1, q2])
+    nn, rec = _nn_gpu(gb, band, q)
+    want = o.nearest_point(q, sphere5k)
+    assert np.array_equal(nn, want)
+    assert np.array_equal(rec[:, :3], q) and np.array_equal(rec[:, 3:], sphere5k[want])
+
+
+def test_nn_ties_go_to_lowest_index(gb, ctx):
+    base = synth.sphere_cloud(300, 0.4, seed=5)
+    pts = np.concatenate([base, base[::-1], base]).astype(np.float32)  # every point three times
+    # Equidistant pair around the origin and queries sitting exactly on points.
+    pair = np.array([[0.0, 0.0, 0.25], [0.0, 0.0, -0.25]], np.float32)
+    pts = np.concatenate([pts, pair, pair]).astype(np.float32)
+    band = _band(gb, ctx, pts, 32, 1, 1, knn_k=0)
+    q = np.concatenate([base, np.zeros((1, 3), np.float32),
+                        synth.gaussian_queries(base, 3000, 0.05, seed=6)[0]]).astype(np.float32)
+    nn, _ = _nn_gpu(gb, band, q)
+    want = o.nearest_point(q, pts)
+    assert np.array_equal(nn, want)
+    assert np.array_equal(nn[:300], np.arange(300))
+
+
+def test_nn_matches_bruteforce_object_full_size(gb, ctx, object100k):
+    """The single-object workload (100,000 points, R=256): sampled queries."""
+    band = _band(gb, ctx, object100k, 256, 2, 2, knn_k=0)
+    q, _ = synth.gaussian_queries(object100k, 3000, 2.0 / 256, seed=7)
+    nn, _ = _nn_gpu(gb, band, q)
+    assert np.array_equal(nn, o.nearest_point(q, object100k))
+
+
+# ---------------------------------------------------------------- sampler
+@pytest.mark.parametrize("J,Q,first,count,epoch", [(5000, 50000, 12345, 20000, 3), (5000, 50000, 0, 50000, 0),
+                                                   (7, 70, 3, 61, 1)])
+def test_sampler_matches_oracle(gb, ctx, sphere5k, J, Q, first, count, epoch):
+    import torch
+    pts = sphere5k[:J]
+    band = _band(gb, ctx, pts, 32, 1, 1, knn_k=min(50, J - 1))
+    q = gb.gp_sample(band, 5, epoch, Q, first, count).cpu().numpy().astype(np.float64)
+    sig = o.knn_sigma(pts, min(50, J - 1))
+    want, j = o.sample_queries(pts, sig, 5, epoch, np.arange(first, first + count))
+    z = (want - pts[j]) / sig[j][:, None]
+    bound = 2e-6 * (np.abs(pts[j]) + sig[j][:, None] * (1 + np.abs(z))) + 1e-7
+    assert np.all(np.abs(q - want) <= bound)
+
+
+def test_sampler_bench_sizes(gb, ctx, object100k):
+    """Single-object workload: pool of 2,000,000 queries, batches of 262,144."""
+    band = _band(gb, ctx, object100k, 256, 2, 2, knn_k=50)
+    Q, B = 2_000_000, 262_144
+    first = 7 * B  # the ragged last batch of the epoch
+    q = gb.gp_sample(band, 11, 2, Q, first, Q - first).cpu().numpy().astype(np.float64)
+    sel = np.random.default_rng(1).choice(Q - first, 2000, replace=False)
+    pos = first + sel
+    j = o.point_permutation(len(object100k), 11, 2, pos % len(object100k))
+    sig = o.knn_sigma(object100k, 50, idx=np.unique(j))
+    sig_full = np.zeros(len(object100k))
+    sig_full[np.unique(j)] = sig
+    want, jj = o.sample_queries(object100k, sig_full, 11, 2, pos)
+    assert np.array_equal(jj, j)
+    z = (want - object100k[j]) / sig_full[j][:, None]
+    bound = 2e-6 * (np.abs(object100k[j]) + sig_full[j][:, None] * (1 + np.abs(z))) + 1e-7
+    assert np.all(np.abs(q[sel] - want) <= bound)
+
+
+# ------------------------------------------------------------------- step
+def _step_inputs(pts, R, M1, M2, n_queries, sigma, seed, use_nn):
+    sets = o.band_sets(pts, R, M1, M2)
+    q, j = synth.gaussian_queries(pts, n_queries, sigma, seed=seed)
+    s = pts[o.nearest_point(q, pts)] if use_nn else pts[j]
+    return sets, q, s
+
+
+def _filter_ambiguous(D, R, sets, q, s):
+    """Drop queries whose sign(f(s)) or unit residual is decided within float32
+    rounding (both choices are valid subgradients there)."""
+    res = o.query_terms(D, R, sets["pull_cells"], q, s, 1.0, 0.005, with_grad=False)
+    if res["Bv"] == 0:
+        return q, s
+    scale = 1.0 + np.max(np.abs(D))
+    keep = np.ones(len(q), bool)
+    v = res["valid"]
+    fs = np.full(len(q), np.inf)
+    fs[v] = res["fs"]
+    keep &= np.abs(fs) > 1e-5 * scale
+    lp = res["l_pull"]
+    dq = np.linalg.norm(q.astype(np.float64) - s.astype(np.float64), axis=1)
+    keep &= ~v | (lp > 1e-4 * (dq + 1e-3))
+    return q[keep], s[keep]
+
+
+def _run_step(gb, band, q, s, weights, flags=0, d=None):
+    import torch
+    rec = torch.from_numpy(np.ascontiguousarray(np.concatenate([q, s], axis=1), np.float32)).cuda()
+    grad = torch.full((band.V_stored,), 7.0, dtype=torch.float32, device="cuda")
+    loss = torch.zeros(8, dtype=torch.float32, device="cuda")
+    gb.gp_step(band, rec, len(q), grad, loss, weights, d=d, flags=flags)
+    return grad.cpu().numpy(), loss.cpu().numpy()
+
+
+def _set_field(gb, band, sets, R, radius, noise, seed, center=(0.0, 0.0, 0.0)):
+    """Generator values at the band's stored slots (uploaded) and, for the
+    oracle, the same generator at the oracle's own required vertices."""
+    import torch
+    ijk, _, _, exists = export_band(band)
+    vals = np.zeros(band.V_stored, np.float32)
+    vals[exists] = synth.sphere_field(ijk[exists], R, radius, noise, seed, center)
+    gb.gp_band_set_values(band, torch.from_numpy(vals).cuda())
+    D = np.zeros((R + 1) ** 3)
+    req = sets["required"]
+    D[req] = synth.sphere_field(o.key_to_vertex(req, R), R, radius, noise, seed, center)
+    return D, vals
+
+
+def _check_step(gb, band, R, sets, q, s, weights, D, flags=0, d_override=None):
+    """GPU step on the band's values (or d_override) against the oracle on D."""
+    import torch
+    ijk, _, _, exists = export_band(band)
+    q, s = _filter_ambiguous(D, R, sets, q, s)
+    sets_use = dict(sets)
+    if flags & gb.GP_STEP_NO_TV:
+        sets_use["tv"] = np.zeros(0, np.int64)
+    ref = o.step_loss_grad(D, R, sets_use, q, s, weights)
+    dt = None if d_override is None else torch.from_numpy(d_override).cuda()
+    grad, loss = _run_step(gb, band, q, s, weights, flags, dt)
+    assert loss[gb.GP_LOSS_BV] == ref["Bv"]
+    assert loss[gb.GP_LOSS_T] == len(sets["tv"])
+    for slot, key in ((gb.GP_LOSS_PULL, "l_pull"), (gb.GP_LOSS_GRAD, "l_grad"), (gb.GP_LOSS_SURF, "l_surf"),
+                      (gb.GP_LOSS_TV, "l_tv"), (gb.GP_LOSS_TOTAL, "loss")):
+        assert_rel(loss[slot], ref[key], what=key)
+    if flags & gb.GP_STEP_LOSS_ONLY:
+        assert np.all(grad == 7.0)
+        return ref
+    assert np.all(grad[~exists] == 0.0)
+    keys = vertex_keys(ijk[exists], R)
+    assert_grad_close(grad[exists], ref["grad"][keys])
+    # Nothing outside the stored set receives gradient in the oracle.
+    assert np.sum(np.abs(ref["grad"])) == pytest.approx(np.sum(np.abs(ref["grad"][keys])), rel=1e-12)
+    return ref
+
+
+def test_step_dense_sphere(gb, ctx, sphere5k):
+    """Dense 64^3 grid, |x| - 0.5 + noise, 50,000 queries with their true NN."""
+    R = 64
+    band = _band(gb, ctx, sphere5k, R, -1, -1, knn_k=0)
+    sets, q, s = _step_inputs(sphere5k, R, -1, -1, 50000, 2.0 / R, seed=2, use_nn=True)
+    D, _ = _set_field(gb, band, sets, R, 0.5, 0.1, seed=1)
+    _check_step(gb, band, R, sets, q, s, (1.0, 1.0, 0.005), D)
+
+
+@pytest.mark.parametrize("weights", [(1.0, 1.0, 0.005), (2.0, 0.5, 0.3)])
+def test_step_band_object_full_batch(gb, ctx, object100k, weights):
+    """Single-object workload at full size: 256^3 band of 8^3 bricks, batch 262,144."""
+    R = 256
+    band = _band(gb, ctx, object100k, R, 2, 2, knn_k=0)
+    c = 0.5 * (object100k.min(0) + object100k.max(0))
+    sets, q, s = _step_inputs(object100k, R, 2, 2, 262_144, 2.0 / R, seed=4, use_nn=False)
+    D, _ = _set_field(gb, band, sets, R, 0.3, 2e-3, seed=3, center=c)
+    _check_step(gb, band, R, sets, q, s, weights, D)
+
+
+def test_step_flags_and_override(gb, ctx, sphere5k):
+    R = 64
+    band = _band(gb, ctx, sphere5k, R, 2, 3, knn_k=0)
+    sets, q, s = _step_inputs(sphere5k, R, 2, 3, 12345, 0.05, seed=10, use_nn=False)
+    D, vals = _set_field(gb, band, sets, R, 0.45, 0.05, seed=9)
+    w = (1.0, 1.0, 0.005)
+    _check_step(gb, band, R, sets, q, s, w, D, flags=gb.GP_STEP_NO_TV)
+    _check_step(gb, band, R, sets, q, s, w, D, flags=gb.GP_STEP_LOSS_ONLY)
+    _check_step(gb, band, R, sets, q, s, w, D * 1.1 + 0.01, d_override=(vals * 1.1 + 0.01).astype(np.float32))
+
+
+def test_step_edge_cases(gb, ctx, sphere5k):
+    R = 32
+    band = _band(gb, ctx, sphere5k, R, 1, 1, knn_k=0)
+    sets = o.band_sets(sphere5k, R, 1, 1)
+    D, _ = _set_field(gb, band, sets, R, 0.4, 0.05, seed=1)
+    w = (1.0, 1.0, 0.005)
+    empty = np.zeros((0, 3), np.float32)
+    ref = _check_step(gb, band, R, sets, empty, empty, w, D)            # B = 0: TV only
+    assert ref["Bv"] == 0
+    outside = np.array([[1.5, 0, 0], [0, -1.0000001, 0], [0, 0, 1.0], [0.9, 0.9, 0.9]], np.float32)
+    ref = _check_step(gb, band, R, sets, outside, sphere5k[:4], w, D)   # all masked
+    assert ref["Bv"] == 0
+    # Queries snapped onto cell faces (one coordinate on a grid plane), among
+    # them brick faces (planes 8k), near the surface so that they are valid.
+    h = 2.0 / R
+    rng = np.random.default_rng(3)
+    base = sphere5k[rng.choice(len(sphere5k), 400, replace=False)].astype(np.float64)
+    qs = base + rng.normal(scale=0.3 * h, size=base.shape)
+    axis = rng.integers(0, 3, len(qs))
+    plane = np.round((qs[np.arange(len(qs)), axis] + 1) / h)
+    plane[::3] = np.round(plane[::3] / 8) * 8
+    qs[np.arange(len(qs)), axis] = -1 + h * plane
+    qs = qs.astype(np.float32)
+    ss = sphere5k[o.nearest_point(qs, sphere5k)]
+    ref = _check_step(gb, band, R, sets, qs, ss, w, D)
+    assert ref["Bv"] > 300
+
+
+def test_step_deterministic_is_bitwise_repeatable(gb, ctx, object100k):
+    R = 256
+    band = _band(gb, ctx, object100k, R, 2, 2, knn_k=0, deterministic=True)
+    c = 0.5 * (object100k.min(0) + object100k.max(0))
+    sets, q, s = _step_inputs(object100k, R, 2, 2, 100_000, 2.0 / R, seed=5, use_nn=False)
+    D, _ = _set_field(gb, band, sets, R, 0.3, 0.002, seed=4, center=c)
+    w = (1.0, 1.0, 0.005)
+    ref = _check_step(gb, band, R, sets, q, s, w, D, flags=gb.GP_STEP_DETERMINISTIC)
+    ijk, d, fl, exists = export_band(band)
+    qf, sf = _filter_ambiguous(D, R, sets, q, s)
+    g1, l1 = _run_step(gb, band, qf, sf, w, gb.GP_STEP_DETERMINISTIC)
+    g2, l2 = _run_step(gb, band, qf, sf, w, gb.GP_STEP_DETERMINISTIC)
+    assert np.array_equal(g1, g2) and np.array_equal(l1, l2)
+    g3, _ = _run_step(gb, band, qf, sf, w, 0)
+    assert_grad_close(g3[exists], g1[exists].astype(np.float64), what="atomic vs deterministic")
+    assert ref["Bv"] > 90_000
+
+
+def test_step_deterministic_needs_band_flag(gb, ctx, sphere5k):
+    band = _band(gb, ctx, sphere5k, 32, 1, 1, knn_k=0)
+    with pytest.raises(gb.GridPullError):
+        _run_step(gb, band, sphere5k[:10], sphere5k[:10], (1, 1, 0.005), gb.GP_STEP_DETERMINISTIC)
+
+
+# ------------------------------------------------------------------ Adam
+def test_update_matches_oracle(gb, ctx, sphere5k):
+    import torch
+    R = 64
+    band = _band(gb, ctx, sphere5k, R, 2, 2, knn_k=0)
+    sets = o.band_sets(sphere5k, R, 2, 2)
+    D, _ = _set_field(gb, band, sets, R, 0.5, 0.01, seed=0)
+    ijk, _, fl, exists = export_band(band)
+    train = exists & ((fl & 2) != 0)
+    keys = vertex_keys(ijk, R)
+    d0 = np.zeros(band.V_stored)
+    d0[exists] = D[keys[exists]]
+    rng = np.random.default_rng(0)
+    d = d0.copy()
+    m = np.zeros_like(d)
+    v = np.zeros_like(d)
+    lr = 1e-3
+    for t in range(1, 4):
+        g = rng.normal(scale=10.0 ** rng.uniform(-6, 0, size=len(d)), size=len(d)).astype(np.float32)
+        gb.gp_update(band, torch.from_numpy(g).cuda(), lr, t)
+        d_new, m_new, v_new = o.adam(d[train], g[train].astype(np.float64), m[train], v[train], t, lr)
+        d[train], m[train], v[train] = d_new, m_new, v_new
+        dg, mg, vg = [x.cpu().numpy().astype(np.float64) for x in gb.gp_band_values(band)]
+        # Adam deltas within 1e-5 lr per step, plus the float32 rounding of the
+        # stored values themselves (half an ulp of |d| per step).
+        bound = t * (REL_TOL * lr + 2.0 ** -24 * np.abs(d[train]))
+        assert np.all(np.abs((dg[train] - d0[train]) - (d[train] - d0[train])) <= bound + 2.0 ** -24 * np.abs(d0[train]))
+        assert np.array_equal(dg[exists & ~train], d0[exists & ~train].astype(np.float32).astype(np.float64))
+        assert np.all(mg[~train] == 0) and np.all(vg[~train] == 0)
+        assert np.allclose(mg[train], m[train], rtol=1e-5, atol=1e-12)
+        assert np.allclose(vg[train], v[train], rtol=1e-5, atol=1e-18)
+
+
+# -------------------------------------------------------------- fit step
+def test_fit_steps_reduce_the_loss(gb, ctx, sphere5k):
+    import torch
+    from paper_2308_13175_gb300.fit import FitStep
+    band = _band(gb, ctx, sphere5k, 64, -1, -1, knn_k=50)
+    gb.gp_band_init_sphere(band, (0, 0, 0), 0.5, 0.1, seed=0)
+    step = FitStep(band, Q=50_000, B=50_000, seed=0, lr=1e-3)
+    losses = [float(step.run(t)[gb.GP_LOSS_TOTAL]) for t in range(30)]
+    torch.cuda.synchronize()
+    assert all(np.isfinite(losses))
+    assert losses[-1] < losses[0]
+    gb.gp_band_check(band)
