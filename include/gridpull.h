@@ -70,7 +70,9 @@ gp_status gp_create(gp_ctx** out, int device, void* stream);
 /* Change the stream later calls run on (e.g. torch's current stream). */
 gp_status gp_set_stream(gp_ctx* ctx, void* stream);
 
-/* Free the context (NULL is ignored). */
+/* Free the context (NULL is ignored).  If bands made from it are still alive,
+ * the context is released when the last of them is destroyed, so the two may
+ * be destroyed in either order. */
 void gp_destroy(gp_ctx* ctx);
 
 /* Message of the last failing call on this context ("" if none).  The string
@@ -191,11 +193,12 @@ gp_status gp_band_check(gp_band* band);
  * around each visited point.  Position k visits point j = Pi_e(k mod J), where
  * Pi_e is a 4-round Feistel bijection of [0, J) keyed by (seed, epoch), and
  * q = s_j + sigma_j * z with z ~ N(0, I) from Philox4x32-10 at counter
- * (k, epoch, 0, 0), key (seed_lo, seed_hi), via Box-Muller.  Requires
- * knn_k > 0 at build.  Errors: GP_ERR_ARG (Q > 2^31-1, first + count > Q,
- * null q_dev with count > 0), GP_ERR_STATE (no sigma). */
+ * (k, epoch, 0, 0), key (seed_lo, seed_hi), via Box-Muller.  If src_dev is
+ * not NULL it receives j per query (count int32; a valid gp_nn hint).
+ * Requires knn_k > 0 at build.  Errors: GP_ERR_ARG (Q > 2^31-1, first + count
+ * > Q, null q_dev with count > 0), GP_ERR_STATE (no sigma). */
 gp_status gp_sample(gp_band* band, uint64_t seed, uint32_t epoch, int64_t Q, int64_t first,
-                    int64_t count, float* q_dev);
+                    int64_t count, float* q_dev, int32_t* src_dev);
 
 /* ---------------------------------------------------------- nearest point */
 
@@ -206,8 +209,12 @@ gp_status gp_sample(gp_band* band, uint64_t seed, uint32_t epoch, int64_t Q, int
  * the step record (qx,qy,qz,sx,sy,sz) per query (n x 6 float32).  nn_dev may
  * be NULL when rec_dev is given.  Exact: a float32 screen with a proven error
  * margin keeps every candidate that could be the float64 minimum.  A query
- * with a NaN or infinite coordinate gets index -1 and NaN for s. */
-gp_status gp_nn(gp_band* band, const float* q_dev, int64_t n, int32_t* nn_dev, float* rec_dev);
+ * with a NaN or infinite coordinate gets index -1 and NaN for s.  hint_dev
+ * (NULL, or n int32 point indices, e.g. gp_sample's src_dev) seeds each search
+ * with a known point: it only speeds the search up, the result is the same
+ * for any hint; out-of-range hints are ignored. */
+gp_status gp_nn(gp_band* band, const float* q_dev, int64_t n, const int32_t* hint_dev, int32_t* nn_dev,
+                float* rec_dev);
 
 /* ------------------------------------------------------------------- step */
 

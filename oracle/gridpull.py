@@ -455,8 +455,21 @@ def query_terms(D: np.ndarray, R: int, pull_cells: np.ndarray, q: np.ndarray, s:
         keys = np.concatenate([kq, ks], axis=1).reshape(-1)        # query order
         vals = np.concatenate([cq_grad, cs_grad], axis=1).reshape(-1)
         np.add.at(grad, keys, vals)
-        out["abs_contrib"] = np.zeros_like(D)
-        np.add.at(out["abs_contrib"], keys, np.abs(vals))
+        # Conditioning of each vertex's sum: the magnitudes of the elementary
+        # products it is made of, before any cancellation.  A component of
+        # dL/dg is only known to within u times the size of the vector it is
+        # projected from (dL/dn / |g|), and dL/df to within u times w (|u.n|
+        # <= 1); the unit residual u = r/|r| itself carries a relative error
+        # kappa = |q - s| / |r| times u (r is a difference of vectors of size
+        # |q - s|).  Those sizes, times |w_c| and |dw_c/dx_a|, are the scale
+        # against which a float32 evaluation is judged.
+        kappa = np.maximum(1.0, np.linalg.norm(q64 - s64, axis=1) / np.maximum(l_pull, 1e-300))
+        sq_g = kappa * np.linalg.norm(dL_dn, axis=1) / np.maximum(_norm(g), NORM_FLOOR)
+        ss_g = np.linalg.norm(dL_dns, axis=1) / np.maximum(_norm(gs), NORM_FLOOR)
+        tq = (w * kappa)[:, None] * np.abs(sfq) + sq_g[:, None] * np.abs(sgq).sum(axis=1)
+        ts = np.abs(dL_dfs)[:, None] * np.abs(sfs) + ss_g[:, None] * np.abs(sgs).sum(axis=1)
+        out["abs_terms"] = np.zeros_like(D)
+        np.add.at(out["abs_terms"], keys, np.concatenate([tq, ts], axis=1).reshape(-1))
     out["grad"] = grad
     return out
 
@@ -480,12 +493,30 @@ def tv_term(D: np.ndarray, R: int, tv_keys: np.ndarray, with_grad: bool = True):
     return loss, grad, tv
 
 
+def tv_term_abs(D: np.ndarray, R: int, tv_keys: np.ndarray) -> np.ndarray:
+    """Per vertex, the sum of |(d_i - d_n) / TV| over the terms of the L_TV
+    gradient that land on it (conditioning of that sum)."""
+    out = np.zeros_like(D)
+    T = len(tv_keys)
+    if T == 0:
+        return out
+    nb, ok = axis_neighbours(tv_keys, R)
+    diff = np.where(ok, D[tv_keys][:, None] - D[nb], 0.0)
+    tv = np.sqrt(np.sum(diff * diff, axis=1))
+    pos = tv > 0
+    coef = np.abs(np.where(pos[:, None], diff / np.where(pos, tv, 1.0)[:, None], 0.0)) / T
+    np.add.at(out, tv_keys, coef.sum(axis=1))
+    np.add.at(out, nb[ok], coef[ok])
+    return out
+
+
 def step_loss_grad(D: np.ndarray, R: int, sets: dict, q: np.ndarray, s: np.ndarray,
                    weights=DEFAULT_WEIGHTS, with_grad: bool = True) -> dict:
     """L = L_Pull + alpha L_TV + beta L_Surface + gamma L_grad (Eq. 8) and dL/dD."""
     alpha, beta, gamma = weights
     qt = query_terms(D, R, sets["pull_cells"], q, s, beta, gamma, with_grad)
     tv_loss, tv_grad, tv_vals = tv_term(D, R, sets["tv"], with_grad)
+    tv_abs = tv_term_abs(D, R, sets["tv"]) if with_grad else None
     Bv = qt["Bv"]
     mean = (lambda x: x / Bv) if Bv else (lambda x: 0.0)
     res = {
@@ -497,8 +528,7 @@ def step_loss_grad(D: np.ndarray, R: int, sets: dict, q: np.ndarray, s: np.ndarr
     res["loss"] = res["l_pull"] + alpha * res["l_tv"] + beta * res["l_surf"] + gamma * res["l_grad"]
     if with_grad:
         res["grad"] = qt["grad"] + alpha * tv_grad
-        abs_c = qt.get("abs_contrib", np.zeros_like(D))
-        res["abs_contrib"] = abs_c + alpha * np.abs(tv_grad)
+        res["abs_terms"] = qt.get("abs_terms", np.zeros_like(D)) + alpha * tv_abs
     return res
 
 

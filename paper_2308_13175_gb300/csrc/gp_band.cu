@@ -379,7 +379,7 @@ extern "C" gp_status gp_build_band(gp_ctx* ctx, const float* pts_dev, int64_t J,
   if (!st) st = gp_alloc(ctx, &b->D, V, "values");
   if (!st) st = gp_alloc(ctx, &b->m, V, "adam m");
   if (!st) st = gp_alloc(ctx, &b->v, V, "adam v");
-  if (!st && (b->flags & GP_BAND_DETERMINISTIC)) st = gp_alloc(ctx, &b->acc, V, "fixed-point accumulator");
+  if (!st && (b->flags & GP_BAND_DETERMINISTIC)) st = gp_alloc(ctx, &b->acc, 2 * V, "fixed-point accumulator");
   if (!st) st = gp_alloc(ctx, &b->partials, (size_t)GP_MAX_PARTIAL_BLOCKS * 8, "partials");
   if (!st) st = gp_alloc(ctx, &b->dev_ints, GP_DI_COUNT, "device ints");
   if (!st) {
@@ -387,7 +387,7 @@ extern "C" gp_status gp_build_band(gp_ctx* ctx, const float* pts_dev, int64_t J,
     cudaError_t e = cudaMemsetAsync(b->D, 0, V * sizeof(float), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->m, 0, V * sizeof(float), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->v, 0, V * sizeof(float), s);
-    if (e == cudaSuccess && b->acc) e = cudaMemsetAsync(b->acc, 0, V * sizeof(unsigned long long), s);
+    if (e == cudaSuccess && b->acc) e = cudaMemsetAsync(b->acc, 0, 2 * V * sizeof(unsigned long long), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->dev_ints, 0, GP_DI_COUNT * sizeof(int32_t), s);
     if (e != cudaSuccess) st = gp_cuda_fail(ctx, e, "gp_build_band: memset");
   }
@@ -400,15 +400,20 @@ extern "C" gp_status gp_build_band(gp_ctx* ctx, const float* pts_dev, int64_t J,
     band_free(b);
     return st;
   }
+  ctx->live_bands += 1;
   *out = b;
   return GP_OK;
 }
 
 extern "C" void gp_band_destroy(gp_band* band) {
   if (!band) return;
-  cudaSetDevice(band->ctx->device);
-  cudaStreamSynchronize(band->ctx->stream);
+  gp_ctx* ctx = band->ctx;
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  cudaGetLastError();
   band_free(band);
+  ctx->live_bands -= 1;
+  if (ctx->live_bands == 0 && ctx->destroy_pending) gp_ctx_release(ctx);
 }
 
 extern "C" gp_status gp_band_get_info(const gp_band* b, gp_band_info* out) {

@@ -45,6 +45,14 @@ extern "C" gp_status gp_set_stream(gp_ctx* ctx, void* stream) {
 
 extern "C" void gp_destroy(gp_ctx* ctx) {
   if (!ctx) return;
+  if (ctx->live_bands > 0) {
+    ctx->destroy_pending = true;
+    return;
+  }
+  gp_ctx_release(ctx);
+}
+
+void gp_ctx_release(gp_ctx* ctx) {
   for (auto& r : ctx->prof) {
     if (r.start) cudaEventDestroy(r.start);
     if (r.stop) cudaEventDestroy(r.stop);

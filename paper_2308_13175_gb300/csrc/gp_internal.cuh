@@ -28,7 +28,14 @@ struct gp_ctx {
   bool profiling = false;
   std::vector<gp_prof_rec> prof;
   std::vector<cudaEvent_t> event_pool;
+  // Bands made from this context that are still alive; gp_destroy defers the
+  // release until the last of them is destroyed.
+  int64_t live_bands = 0;
+  bool destroy_pending = false;
 };
+
+// Release a context's memory (called when no band refers to it any more).
+void gp_ctx_release(gp_ctx* ctx);
 
 // Record the start event of the next launch (profiling only).
 void gp_prof_pre(gp_ctx* ctx);
@@ -66,7 +73,7 @@ struct gp_band {
   float* D = nullptr;              // values, V_stored
   float* m = nullptr;              // Adam first moment
   float* v = nullptr;              // Adam second moment
-  unsigned long long* acc = nullptr;  // deterministic fixed-point gradient (V_stored)
+  unsigned long long* acc = nullptr;  // deterministic two-word fixed-point gradient (2 x V_stored)
 
   // Point cloud: original order copy, cell list sorted copy, sigma, permutation.
   float* pts = nullptr;            // J x 3

@@ -175,7 +175,78 @@ __global__ void __launch_bounds__(128) k_knn_sigma(NNGrid g, int64_t J, int k, f
   sigma[self] = cnt > 0 ? sqrtf(heap[0]) : 0.f;
 }
 
+// Lower bound on |p_a - q_a| for any point p in cell `ca` along one axis
+// (edge cells extend to infinity outwards); the margin absorbs the rounding of
+// the point-to-cell assignment and of the cell faces.
+__device__ __forceinline__ float nn_axis_gap(float qa, int ca, const NNGrid& g, float margin) {
+  float lo = -1.0f + (float)ca * g.cs, hi = lo + g.cs;
+  float d = 0.f;
+  if (ca > 0 && qa < lo) d = lo - qa;
+  if (ca < g.G - 1 && qa > hi) d = qa - hi;
+  return fmaxf(d - margin, 0.f);
+}
+
+// Exact nearest point: b1/j1 = best float32 distance and its index, b2 = the
+// runner-up distance (any other point), thr = b1 (1 + 8 eps) + tiny = the
+// pruning radius squared.  Only cells that may hold a point with squared
+// distance <= thr are read: a row of cells (fixed y, z) is skipped when its y/z
+// lower bound already exceeds thr, and its x-range is clipped to the cells
+// that intersect the remaining radius.
+struct NNState {
+  float b1, b2, thr;
+  int j1;
+};
+
+__device__ __forceinline__ void nn_update(NNState& st, float d, int j) {
+  if (j == st.j1) return;  // the seeded point, met again in the scan
+  if (d < st.b1 || (d == st.b1 && j < st.j1)) {
+    st.b2 = st.b1;
+    st.b1 = d;
+    st.j1 = j;
+    st.thr = d * (1.0f + 8.0f * NN_EPS) + NN_TINY;
+  } else if (d < st.b2) {
+    st.b2 = d;
+  }
+}
+
+template <typename F>
+__device__ __forceinline__ void nn_ring_pruned(const float q[3], const int c[3], int r, const NNGrid& g,
+                                               float margin, const float& thr, F&& visit) {
+  const int G = g.G;
+  for (int dz = -r; dz <= r; ++dz) {
+    int cz = c[2] + dz;
+    if (cz < 0 || cz >= G) continue;
+    float lz = nn_axis_gap(q[2], cz, g, margin);
+    float lz2 = lz * lz;
+    if (lz2 > thr) continue;
+    for (int dy = -r; dy <= r; ++dy) {
+      int cy = c[1] + dy;
+      if (cy < 0 || cy >= G) continue;
+      float ly = nn_axis_gap(q[1], cy, g, margin);
+      float lyz2 = fmaf(ly, ly, lz2);
+      if (lyz2 > thr) continue;
+      float rad = sqrtf(thr - lyz2) * 1.000001f + margin;  // thr may be +inf
+      int xa = 0, xb = G - 1;
+      if (rad < 4.0f) {
+        xa = nn_cell(q[0] - rad, g);
+        xb = nn_cell(q[0] + rad, g);
+      }
+      int64_t row = ((int64_t)cz * G + cy) * G;
+      bool full = (dz == -r || dz == r || dy == -r || dy == r);
+      if (full) {
+        int x0 = max(max(c[0] - r, 0), xa), x1 = min(min(c[0] + r, G - 1), xb);
+        if (x0 <= x1) visit(__ldg(g.start + row + x0), __ldg(g.start + row + x1 + 1));
+      } else {
+        int xl = c[0] - r, xr = c[0] + r;
+        if (xl >= 0 && xl >= xa && xl <= xb) visit(__ldg(g.start + row + xl), __ldg(g.start + row + xl + 1));
+        if (xr < G && xr >= xa && xr <= xb) visit(__ldg(g.start + row + xr), __ldg(g.start + row + xr + 1));
+      }
+    }
+  }
+}
+
 __global__ void __launch_bounds__(256) k_nn(NNGrid g, const float* __restrict__ qin, int64_t n,
+                                            const int32_t* __restrict__ hint, int64_t J,
                                             const float* __restrict__ pts_orig, int32_t* __restrict__ nn_out,
                                             float* __restrict__ rec) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -183,35 +254,37 @@ __global__ void __launch_bounds__(256) k_nn(NNGrid g, const float* __restrict__ 
   float q[3] = {qin[3 * i], qin[3 * i + 1], qin[3 * i + 2]};
   int c[3] = {nn_cell(q[0], g), nn_cell(q[1], g), nn_cell(q[2], g)};
   float margin = nn_margin(q);
-  float b1 = INFINITY, b2 = INFINITY;
-  int j1 = 0x7fffffff;
+  NNState st{INFINITY, INFINITY, INFINITY, 0x7fffffff};
+  if (hint) {
+    int j = hint[i];
+    if (j >= 0 && j < J) {
+      float dx = q[0] - pts_orig[3 * (int64_t)j], dy = q[1] - pts_orig[3 * (int64_t)j + 1];
+      float dz = q[2] - pts_orig[3 * (int64_t)j + 2];
+      float d = dx * dx + dy * dy + dz * dz;
+      if (d < INFINITY) {
+        st.b1 = d;
+        st.j1 = j;
+        st.thr = d * (1.0f + 8.0f * NN_EPS) + NN_TINY;
+      }
+    }
+  }
+  auto scan = [&](int a, int b) {
+    for (int p = a; p < b; ++p) {
+      float4 P = g.pts[p];
+      float dx = q[0] - P.x, dy = q[1] - P.y, dz = q[2] - P.z;
+      nn_update(st, dx * dx + dy * dy + dz * dz, __float_as_int(P.w));
+    }
+  };
   int r_end = 0;
   for (int r = 0; r <= g.G; ++r) {
-    nn_ring(c, r, g, [&](int a, int b) {
-      for (int p = a; p < b; ++p) {
-        float4 P = g.pts[p];
-        float dx = q[0] - P.x, dy = q[1] - P.y, dz = q[2] - P.z;
-        float d = dx * dx + dy * dy + dz * dz;
-        int j = __float_as_int(P.w);
-        if (d < b1 || (d == b1 && j < j1)) {
-          b2 = b1;
-          b1 = d;
-          j1 = j;
-        } else if (d < b2) {
-          b2 = d;
-        }
-      }
-    });
+    nn_ring_pruned(q, c, r, g, margin, st.thr, scan);
     r_end = r;
     float gap = nn_gap(q, c, r, g);
     if (gap == INFINITY) break;
-    if (b1 < INFINITY) {
-      float gs = gap - margin;
-      if (gs > 0.f && gs * gs > b1 * (1.0f + 8.0f * NN_EPS) + NN_TINY) break;
-    }
+    float gs = gap - margin;
+    if (st.b1 < INFINITY && gs > 0.f && gs * gs > st.thr) break;
   }
-  int best = j1;
-  if (j1 == 0x7fffffff) {
+  if (st.j1 == 0x7fffffff) {
     // Non-finite query: no point compares below it.  Report -1, NaN record.
     if (nn_out) nn_out[i] = -1;
     if (rec) {
@@ -219,27 +292,29 @@ __global__ void __launch_bounds__(256) k_nn(NNGrid g, const float* __restrict__ 
     }
     return;
   }
-  if (!(b2 > b1 * (1.0f + 2.0f * NN_EPS) + NN_TINY)) {
-    // Near tie: rank every point within the margin by its float64 distance.
-    float thr = b1 * (1.0f + 2.0f * NN_EPS) + NN_TINY;
+  int best = st.j1;
+  float tie = st.b1 * (1.0f + 2.0f * NN_EPS) + NN_TINY;
+  if (!(st.b2 > tie)) {
+    // Near tie: rank every point within the margin by its float64 distance,
+    // over the same cells (the pruning radius only shrank while scanning).
     double bd = INFINITY;
     int bj = 0x7fffffff;
-    for (int r = 0; r <= r_end; ++r) {
-      nn_ring(c, r, g, [&](int a, int b) {
-        for (int p = a; p < b; ++p) {
-          float4 P = g.pts[p];
-          float dx = q[0] - P.x, dy = q[1] - P.y, dz = q[2] - P.z;
-          float d = dx * dx + dy * dy + dz * dz;
-          if (d > thr) continue;
-          int j = __float_as_int(P.w);
-          double dd = nn_d64(q, P);
-          if (dd < bd || (dd == bd && j < bj)) {
-            bd = dd;
-            bj = j;
-          }
+    const float thr = st.thr;
+    auto rank = [&](int a, int b) {
+      for (int p = a; p < b; ++p) {
+        float4 P = g.pts[p];
+        float dx = q[0] - P.x, dy = q[1] - P.y, dz = q[2] - P.z;
+        float d = dx * dx + dy * dy + dz * dz;
+        if (d > tie) continue;
+        int j = __float_as_int(P.w);
+        double dd = nn_d64(q, P);
+        if (dd < bd || (dd == bd && j < bj)) {
+          bd = dd;
+          bj = j;
         }
-      });
-    }
+      }
+    };
+    for (int r = 0; r <= r_end; ++r) nn_ring_pruned(q, c, r, g, margin, thr, rank);
     if (bj != 0x7fffffff) best = bj;
   }
   if (nn_out) nn_out[i] = best;
@@ -325,13 +400,15 @@ extern "C" gp_status gp_band_sigma(const gp_band* b, float* sigma_dev) {
   return GP_OK;
 }
 
-extern "C" gp_status gp_nn(gp_band* b, const float* q_dev, int64_t n, int32_t* nn_dev, float* rec_dev) {
+extern "C" gp_status gp_nn(gp_band* b, const float* q_dev, int64_t n, const int32_t* hint_dev, int32_t* nn_dev,
+                           float* rec_dev) {
   if (!b) return GP_ERR_ARG;
   gp_ctx* ctx = b->ctx;
   if (n < 0 || n >= (int64_t(1) << 31)) return gp_fail(ctx, GP_ERR_ARG, "gp_nn: n must be in [0, 2^31)");
   if (n == 0) return GP_OK;
   if (!q_dev || (!nn_dev && !rec_dev)) return gp_fail(ctx, GP_ERR_ARG, "gp_nn: null pointer");
   NNGrid g = make_grid(b);
-  GP_KERNEL(ctx, "k_nn", k_nn<<<gp_blocks(n, 256), 256, 0, ctx->stream>>>(g, q_dev, n, b->pts, nn_dev, rec_dev));
+  GP_KERNEL(ctx, "k_nn", k_nn<<<gp_blocks(n, 256), 256, 0, ctx->stream>>>(g, q_dev, n, hint_dev, b->J, b->pts, nn_dev,
+                                                                           rec_dev));
   return GP_OK;
 }

@@ -28,7 +28,7 @@ __global__ void k_perm(int64_t J, int half, uint32_t epoch, uint32_t k0, uint32_
 
 __global__ void k_sample(const float* __restrict__ pts, const float* __restrict__ sigma,
                          const int32_t* __restrict__ perm, int64_t J, int64_t first, int64_t count, uint32_t epoch,
-                         uint32_t k0, uint32_t k1, float* __restrict__ q) {
+                         uint32_t k0, uint32_t k1, float* __restrict__ q, int32_t* __restrict__ src) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= count) return;
   int64_t k = first + i;
@@ -38,6 +38,7 @@ __global__ void k_sample(const float* __restrict__ pts, const float* __restrict_
   q[3 * i + 0] = pts[3 * (int64_t)j + 0] + sg * z.x;
   q[3 * i + 1] = pts[3 * (int64_t)j + 1] + sg * z.y;
   q[3 * i + 2] = pts[3 * (int64_t)j + 2] + sg * z.z;
+  if (src) src[i] = j;
 }
 
 }  // namespace
@@ -55,7 +56,7 @@ gp_status gp_build_permutation(gp_band* b, uint64_t seed, uint32_t epoch) {
 }
 
 extern "C" gp_status gp_sample(gp_band* b, uint64_t seed, uint32_t epoch, int64_t Q, int64_t first, int64_t count,
-                               float* q_dev) {
+                               float* q_dev, int32_t* src_dev) {
   if (!b) return GP_ERR_ARG;
   gp_ctx* ctx = b->ctx;
   if (Q < 0 || Q >= (int64_t(1) << 31) || first < 0 || count < 0 || first + count > Q)
@@ -65,7 +66,8 @@ extern "C" gp_status gp_sample(gp_band* b, uint64_t seed, uint32_t epoch, int64_
   if (!b->sigma) return gp_fail(ctx, GP_ERR_STATE, "gp_sample: band built with knn_k = 0 (no sigma)");
   gp_status st = gp_build_permutation(b, seed, epoch);
   if (st) return st;
-  GP_KERNEL(ctx, "k_sample", k_sample<<<gp_blocks(count, 256), 256, 0, ctx->stream>>>(b->pts, b->sigma, b->perm, b->J, first, count, epoch,
-                                                            (uint32_t)seed, (uint32_t)(seed >> 32), q_dev));
+  GP_KERNEL(ctx, "k_sample", k_sample<<<gp_blocks(count, 256), 256, 0, ctx->stream>>>(
+                                 b->pts, b->sigma, b->perm, b->J, first, count, epoch, (uint32_t)seed,
+                                 (uint32_t)(seed >> 32), q_dev, src_dev));
   return GP_OK;
 }

@@ -25,8 +25,14 @@ namespace {
 constexpr int Q_THREADS = 256;
 constexpr int TV_THREADS = 512;
 constexpr float NORM_FLOOR = 1e-12f;
-constexpr double FIX_SCALE = 4294967296.0;  // 2^32: fixed-point unit of the deterministic sums
-constexpr double FIX_LIMIT = 4.0e18;        // |value * 2^32| beyond this flags an overflow
+// Deterministic sums: each contribution v is split into two integers,
+// hi = round(v * 2^20) and lo = round((v - hi * 2^-20) * 2^60), accumulated
+// with 64-bit integer atomics (exact, so the order of the additions does not
+// matter).  The sum is hi * 2^-20 + lo * 2^-60: a resolution of 2^-60, no
+// overflow below 2^42 per contribution and 2^23 contributions per vertex.
+constexpr double FIX_HI = 1048576.0;                     // 2^20
+constexpr double FIX_LO = 1152921504606846976.0;         // 2^60
+constexpr double FIX_LIMIT = 4398046511104.0;            // 2^42
 
 struct Grid {
   const int32_t* __restrict__ table;
@@ -62,19 +68,27 @@ __device__ __forceinline__ void load_corners(const Grid& G, const int c[3], int 
   }
 }
 
-// Trilinear interpolation of Eq. 3 written as lerps along x, then y, then z.
+// Trilinear interpolation of Eq. 3.  f is a lerp along x, then y, then z.
+// Each gradient component is the bilinear blend, over the other two axes, of
+// the four cell-edge differences along its own axis: a difference of two close
+// grid values is exact (Sterbenz), so no component suffers the cancellation
+// that differencing two interpolated values would bring.
+__device__ __forceinline__ float lerp1(float t, float a, float b) { return fmaf(t, b - a, a); }
+
 __device__ __forceinline__ Eval trilerp(const float d[8], const float t[3]) {
-  float a00 = d[1] - d[0], a10 = d[3] - d[2], a01 = d[5] - d[4], a11 = d[7] - d[6];
-  float e00 = fmaf(t[0], a00, d[0]), e10 = fmaf(t[0], a10, d[2]);
-  float e01 = fmaf(t[0], a01, d[4]), e11 = fmaf(t[0], a11, d[6]);
-  float by0 = e10 - e00, by1 = e11 - e01;
-  float f0 = fmaf(t[1], by0, e00), f1 = fmaf(t[1], by1, e01);
   Eval r;
-  r.f = fmaf(t[2], f1 - f0, f0);
-  r.gt[2] = f1 - f0;
-  r.gt[1] = fmaf(t[2], by1 - by0, by0);
-  float ax0 = fmaf(t[1], a10 - a00, a00), ax1 = fmaf(t[1], a11 - a01, a01);
-  r.gt[0] = fmaf(t[2], ax1 - ax0, ax0);
+  float e00 = lerp1(t[0], d[0], d[1]), e10 = lerp1(t[0], d[2], d[3]);
+  float e01 = lerp1(t[0], d[4], d[5]), e11 = lerp1(t[0], d[6], d[7]);
+  r.f = lerp1(t[2], lerp1(t[1], e00, e10), lerp1(t[1], e01, e11));
+  // x edges at (y,z) = 00, 10, 01, 11
+  float a00 = d[1] - d[0], a10 = d[3] - d[2], a01 = d[5] - d[4], a11 = d[7] - d[6];
+  r.gt[0] = lerp1(t[2], lerp1(t[1], a00, a10), lerp1(t[1], a01, a11));
+  // y edges at (x,z) = 00, 10, 01, 11
+  float b00 = d[2] - d[0], b10 = d[3] - d[1], b01 = d[6] - d[4], b11 = d[7] - d[5];
+  r.gt[1] = lerp1(t[2], lerp1(t[0], b00, b10), lerp1(t[0], b01, b11));
+  // z edges at (x,y) = 00, 10, 01, 11
+  float c00 = d[4] - d[0], c10 = d[5] - d[1], c01 = d[6] - d[2], c11 = d[7] - d[3];
+  r.gt[2] = lerp1(t[1], lerp1(t[0], c00, c10), lerp1(t[0], c01, c11));
   return r;
 }
 
@@ -152,12 +166,15 @@ __device__ __forceinline__ void scatter8(const Grid& G, float* __restrict__ grad
       addr = gp_vaddr(s, i, j, kk);
     }
     if (DET) {
-      double x = (double)val * FIX_SCALE;
+      double x = (double)val;
       if (!(fabs(x) < FIX_LIMIT)) {
         atomicOr(err, GP_EF_NUMERIC);
         continue;
       }
-      atomicAdd(acc + addr, (unsigned long long)(long long)llrint(x));
+      double hi = rint(x * FIX_HI);
+      double lo = rint((x - hi / FIX_HI) * FIX_LO);
+      atomicAdd(acc + 2 * addr, (unsigned long long)(long long)hi);
+      atomicAdd(acc + 2 * addr + 1, (unsigned long long)(long long)lo);
     } else {
       atomicAdd(grad + addr, val);
     }
@@ -299,10 +316,10 @@ __global__ void __launch_bounds__(TV_THREADS) k_tv(Grid G, const int32_t* __rest
                                                    const int32_t* __restrict__ bv, double* __restrict__ partials,
                                                    int32_t* __restrict__ err) {
   float tsum = 0.f;
-  float qscale = 0.f;
+  double qscale = 0.0;
   if (DET) {
     int b = *bv;
-    qscale = b > 0 ? (float)(1.0 / ((double)b * FIX_SCALE)) : 0.f;
+    qscale = b > 0 ? 1.0 / (double)b : 0.0;
   }
   const int l = threadIdx.x;
   for (int64_t slot = blockIdx.x; slot < n_bricks; slot += gridDim.x) {
@@ -343,9 +360,11 @@ __global__ void __launch_bounds__(TV_THREADS) k_tv(Grid G, const int32_t* __rest
     if (GRAD) {
       float gv = tv_scale * gsum;
       if (DET) {
-        long long a = (long long)acc[addr];
-        acc[addr] = 0ull;
-        gv += (float)((double)a * (double)qscale);
+        long long hi = (long long)acc[2 * addr], lo = (long long)acc[2 * addr + 1];
+        acc[2 * addr] = 0ull;
+        acc[2 * addr + 1] = 0ull;
+        double q = ((double)hi / FIX_HI + (double)lo / FIX_LO) * qscale;
+        gv = (float)((double)gv + q);
       }
       grad[addr] = gv;
     }

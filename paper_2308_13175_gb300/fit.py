@@ -2,7 +2,8 @@
 
 ``FitStep.run(t)`` performs step t of the fit over one batch of the epoch's
 query pool: gp_sample (Gaussian queries around points visited in the epoch's
-random order) -> gp_nn (NN(q), step records) -> gp_step (Eq. 8 forward and
+random order) -> gp_nn (NN(q), step records; each search seeded with the
+query's own source point) -> gp_step (Eq. 8 forward and
 hand-written backward) -> gp_update (Adam).  All device buffers are allocated
 once here; the calls themselves never allocate."""
 from __future__ import annotations
@@ -29,6 +30,7 @@ class FitStep:
         self.batches_per_epoch = math.ceil(self.Q / self.B)
         dev = torch.device("cuda", band.ctx.device)
         self.q = torch.empty((self.B, 3), dtype=torch.float32, device=dev)
+        self.src = torch.empty(self.B, dtype=torch.int32, device=dev)
         self.rec = torch.empty((self.B, 6), dtype=torch.float32, device=dev)
         self.grad = torch.empty(band.V_stored, dtype=torch.float32, device=dev)
         self.loss = torch.zeros(8, dtype=torch.float32, device=dev)
@@ -47,8 +49,8 @@ class FitStep:
         """Step t (0-based); returns the loss buffer (device, 8 floats)."""
         band = self.band
         epoch, first, count = self.batch_of(t)
-        gb.gp_sample(band, self.seed, epoch, self.Q, first, count, self.q)
-        gb.gp_nn(band, self.q[:count], None, self.rec)
+        gb.gp_sample(band, self.seed, epoch, self.Q, first, count, self.q, self.src)
+        gb.gp_nn(band, self.q[:count], None, self.rec, hint=self.src[:count])
         gb.gp_step(band, self.rec, count, self.grad, self.loss, self.weights, flags=self.flags)
         gb.gp_update(band, self.grad, self.lr_at(t), t + 1)
         return self.loss

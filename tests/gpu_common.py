@@ -47,15 +47,20 @@ def assert_rel(got, want, tol=REL_TOL, what="value"):
     assert abs(got - want) <= tol * abs(want) + 1e-30, f"{what}: got {got!r}, want {want!r}"
 
 
-def assert_grad_close(g, ref, tol=REL_TOL, what="grad"):
-    """Norm-wise relative error <= tol and per-vertex
-    |g_i - ref_i| <= tol * max(|ref_i|, 1e-3 * max|ref|)."""
+def assert_grad_close(g, ref, scale=None, tol=REL_TOL, what="grad"):
+    """Norm-wise relative error <= tol, and per vertex
+    |g_i - ref_i| <= tol * scale_i, where scale_i is the oracle's conditioning
+    of that vertex's sum (the sizes of the products it adds up; >= |ref_i|).
+    Without a scale the per-vertex check uses max(|ref_i|, 1e-3 max|ref|)."""
     g = np.asarray(g, np.float64)
     ref = np.asarray(ref, np.float64)
     nrm = np.linalg.norm(ref)
     err = np.linalg.norm(g - ref)
     assert err <= tol * nrm, f"{what}: |g - ref| / |ref| = {err / max(nrm, 1e-300):.3e}"
-    floor = 1e-3 * np.max(np.abs(ref))
-    per = np.abs(g - ref) / np.maximum(np.abs(ref), floor)
+    if scale is None:
+        scale = np.maximum(np.abs(ref), 1e-3 * np.max(np.abs(ref)))
+    scale = np.maximum(np.asarray(scale, np.float64), np.abs(ref))
+    per = np.abs(g - ref) / np.maximum(scale, 1e-300)
     worst = int(np.argmax(per))
-    assert per[worst] <= tol, f"{what}: vertex {worst} rel err {per[worst]:.3e} (got {g[worst]}, want {ref[worst]})"
+    assert per[worst] <= tol, (f"{what}: vertex {worst} err {abs(g[worst] - ref[worst]):.3e} = {per[worst]:.3e} of "
+                               f"its scale {scale[worst]:.3e} (got {g[worst]}, want {ref[worst]})")

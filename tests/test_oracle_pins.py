@@ -250,6 +250,8 @@ def test_full_gradient_matches_central_differences(seed):
         fd[n] = (lp - lm) / (2 * eps)
     g = res["grad"][check]
     assert np.max(np.abs(g - fd)) < 2e-6 * np.max(np.abs(fd))
+    # The per-vertex conditioning scale bounds the gradient it describes.
+    assert np.all(res["abs_terms"] >= np.abs(res["grad"]) * (1 - 1e-12))
     # Vertices outside the required set get no gradient.
     other = np.setdiff1d(keys, check)
     assert np.all(res["grad"][other] == 0)
