@@ -58,7 +58,6 @@ def alg_bytes(name, n, J, Vs, Vt):
         "k_count_valid": 24 * n,
         "k_tv": 8 * Vs,
         "k_query": 24 * n + 8 * Vt,
-        "k_finalize": 0,
         "k_adam": 28 * Vt,
     }.get(name, 0)
 
@@ -334,8 +333,8 @@ def run_ours(args, world, rank, local):
         flush.fill_(float(k))
         e_start.record(stream)
         dq.copy_(hq[k], non_blocking=True)
-        gb.gp_nn(band, dq, None, fit.rec)
-        gb.gp_step(band, fit.rec, B, fit.grad, fit.loss, PAPER_WEIGHTS)
+        gb.gp_nn(band, dq, None, fit.rec, nvalid_out=fit.nvalid)
+        gb.gp_step(band, fit.rec, B, fit.grad, fit.loss, PAPER_WEIGHTS, nvalid=fit.nvalid)
         gb.gp_update(band, fit.grad, wl["lr"], step_t + k + 1)
         hloss[k].copy_(fit.loss, non_blocking=True)
         e_end.record(stream)

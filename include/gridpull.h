@@ -209,12 +209,16 @@ gp_status gp_sample(gp_band* band, uint64_t seed, uint32_t epoch, int64_t Q, int
  * the step record (qx,qy,qz,sx,sy,sz) per query (n x 6 float32).  nn_dev may
  * be NULL when rec_dev is given.  Exact: a float32 screen with a proven error
  * margin keeps every candidate that could be the float64 minimum.  A query
- * with a NaN or infinite coordinate gets index -1 and NaN for s.  hint_dev
+ * with a NaN, infinite or larger-than-1e18 coordinate (whose squared
+ * distances would overflow float32) gets index -1 and NaN for s.  hint_dev
  * (NULL, or n int32 point indices, e.g. gp_sample's src_dev) seeds each search
  * with a known point: it only speeds the search up, the result is the same
- * for any hint; out-of-range hints are ignored. */
+ * for any hint; out-of-range hints are ignored.  If nvalid_dev is not NULL
+ * (one int32) it receives the number of records gp_step will count as valid
+ * (q inside the domain, cell(q) and cell(NN(q)) in the pull band): pass it to
+ * gp_step to skip its own count. */
 gp_status gp_nn(gp_band* band, const float* q_dev, int64_t n, const int32_t* hint_dev, int32_t* nn_dev,
-                float* rec_dev);
+                float* rec_dev, int32_t* nvalid_dev);
 
 /* ------------------------------------------------------------------- step */
 
@@ -244,9 +248,9 @@ typedef struct gp_loss_w {
  * averaged over the B_v valid queries, L_TV over T.  Writes the loss slots to
  * loss_dev (8 floats) and, unless GP_STEP_LOSS_ONLY, overwrites grad_dev
  * (V_stored floats, storage order) with dL/dD at every stored slot (0 at
- * padding).  If nvalid_dev is not NULL, only the first *nvalid_dev records are
- * read and B_v is taken from it (records must then all be valid); otherwise all
- * B records are read and B_v is counted.  If d_dev is not NULL the values are
+ * padding).  All B records are read; invalid ones are masked.  If nvalid_dev is
+ * not NULL it holds B_v, the number of valid records among them (as gp_nn
+ * counts it); otherwise gp_step counts them first.  If d_dev is not NULL the values are
  * read from it (V_stored floats) instead of the band's own.  Errors:
  * GP_ERR_ARG (B < 0, null rec/loss, B >= 2^31, rec_dev not 8-byte aligned),
  * GP_ERR_STATE (deterministic

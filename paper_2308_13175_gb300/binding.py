@@ -76,7 +76,7 @@ SIGNATURES = {
     "gp_band_reset_adam": (ctypes.c_int, [_vp]),
     "gp_band_check": (ctypes.c_int, [_vp]),
     "gp_sample": (ctypes.c_int, [_vp, _u64, _u32, _i64, _i64, _i64, _vp, _vp]),
-    "gp_nn": (ctypes.c_int, [_vp, _vp, _i64, _vp, _vp, _vp]),
+    "gp_nn": (ctypes.c_int, [_vp, _vp, _i64, _vp, _vp, _vp, _vp]),
     "gp_step": (ctypes.c_int, [_vp, _vp, _i64, _vp, _vp, ctypes.POINTER(LossW), _vp, _vp, _u32]),
     "gp_update": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(Adam), _i64]),
 }
@@ -304,15 +304,17 @@ def gp_sample(band: Band, seed: int, epoch: int, Q: int, first: int, count: int,
     return out
 
 
-def gp_nn(band: Band, q, nn_out=None, rec_out=None, hint=None):
+def gp_nn(band: Band, q, nn_out=None, rec_out=None, hint=None, nvalid_out=None):
     import torch
     _need(q, torch.float32, name="q")
     n = q.numel() // 3
     _need(nn_out, torch.int32, n, "nn")
     _need(rec_out, torch.float32, 6 * n, "records")
     _need(hint, torch.int32, n, "hint")
+    _need(nvalid_out, torch.int32, 1, "nvalid")
     band.ctx.sync_stream()
-    band.ctx.check(band.ctx.lib.gp_nn(band.handle, _ptr(q), n, _ptr(hint), _ptr(nn_out), _ptr(rec_out)))
+    band.ctx.check(band.ctx.lib.gp_nn(band.handle, _ptr(q), n, _ptr(hint), _ptr(nn_out), _ptr(rec_out),
+                                      _ptr(nvalid_out)))
     return nn_out, rec_out
 
 

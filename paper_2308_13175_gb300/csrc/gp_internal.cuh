@@ -54,7 +54,7 @@ void gp_prof_post(gp_ctx* ctx, const char* name);
 // Number of fp64 partial-sum slots the reduction kernels may use per call.
 constexpr int GP_MAX_PARTIAL_BLOCKS = 4096;
 // Device int slots of gp_band::dev_ints.
-enum { GP_DI_NVALID = 0, GP_DI_ERROR = 1, GP_DI_COUNT = 8 };
+enum { GP_DI_NVALID = 0, GP_DI_ERROR = 1, GP_DI_DONE = 2, GP_DI_COUNT = 8 };
 // Error bits raised by kernels in dev_ints[GP_DI_ERROR].
 enum { GP_EF_NUMERIC = 1, GP_EF_TIMEOUT = 2, GP_EF_RANGE = 4 };
 
@@ -276,3 +276,54 @@ __device__ __forceinline__ int gp_warp_sum_i(int v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
+
+// ------------------------------------------------------ device: step records
+// The band as the step kernels see it.
+struct Grid {
+  const int32_t* __restrict__ table;
+  const uint32_t* __restrict__ masks;
+  const float* __restrict__ D;
+  int nb;
+  int R;
+  float half_r;  // R/2 = 1/h
+};
+
+struct Cells {
+  int cq[3], cs[3];
+  float tq[3], ts[3];
+  int slot_q, slot_s;
+};
+
+// Validity of a record (Sec. 3 pull band; readings in the header): q inside
+// the domain, cell(q) and cell(s) in the M1 band.
+__device__ __forceinline__ bool classify(const Grid& G, const float q[3], const float s[3], Cells& C) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    gp_cell1 g = gp_cell_exact(q[a], G.half_r);
+    if (g.c < 0 || g.c > G.R - 1) return false;
+    C.cq[a] = g.c;
+    C.tq[a] = g.t;
+    gp_cell1 h = gp_cell_exact(s[a], G.half_r);
+    if (h.c == -(1 << 30)) return false;
+    int cc = min(max(h.c, 0), G.R - 1);
+    C.cs[a] = cc;
+    C.ts[a] = h.t + (float)(h.c - cc);
+  }
+  C.slot_q = gp_brick_slot(G.table, G.nb, C.cq[0], C.cq[1], C.cq[2]);
+  if (C.slot_q < 0 || !gp_mask_bit(G.masks, C.slot_q, 2, gp_local(C.cq[0], C.cq[1], C.cq[2]))) return false;
+  C.slot_s = gp_brick_slot(G.table, G.nb, C.cs[0], C.cs[1], C.cs[2]);
+  if (C.slot_s < 0 || !gp_mask_bit(G.masks, C.slot_s, 2, gp_local(C.cs[0], C.cs[1], C.cs[2]))) return false;
+  return true;
+}
+
+__device__ __forceinline__ void load_rec(const float* __restrict__ rec, int64_t i, float q[3], float s[3]) {
+  const float2* r2 = reinterpret_cast<const float2*>(rec + 6 * i);
+  float2 a = __ldg(r2), b = __ldg(r2 + 1), c = __ldg(r2 + 2);
+  q[0] = a.x;
+  q[1] = a.y;
+  q[2] = b.x;
+  s[0] = b.y;
+  s[1] = c.x;
+  s[2] = c.y;
+}
+

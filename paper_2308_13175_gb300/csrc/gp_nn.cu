@@ -209,49 +209,101 @@ __device__ __forceinline__ void nn_update(NNState& st, float d, int j) {
   }
 }
 
+// Lower bound on the y/z distance from q to any point in a row outside the
+// square of rows [c - r, c + r]^2 (y, z); +inf when that square covers the grid.
+__device__ __forceinline__ float nn_gap_yz(const float q[3], const int c[3], int r, const NNGrid& g) {
+  float gap = INFINITY;
+#pragma unroll
+  for (int a = 1; a < 3; ++a) {
+    if (c[a] - r > 0) gap = fminf(gap, q[a] - (-1.0f + (float)(c[a] - r) * g.cs));
+    if (c[a] + r < g.G - 1) gap = fminf(gap, (-1.0f + (float)(c[a] + r + 1) * g.cs) - q[a]);
+  }
+  return gap;
+}
+
+// Visit the rows (fixed y, z) of square ring r around the query's row, each
+// clipped to the cells whose points may lie within sqrt(thr) of q.  Rows whose
+// y/z lower bound alone exceeds thr are skipped.  thr is read live, so rows
+// visited later use the tighter radius.
 template <typename F>
-__device__ __forceinline__ void nn_ring_pruned(const float q[3], const int c[3], int r, const NNGrid& g,
-                                               float margin, const float& thr, F&& visit) {
+__device__ __forceinline__ void nn_row_ring(const float q[3], const int c[3], int r, const NNGrid& g, float margin,
+                                            const float& thr, F&& visit) {
   const int G = g.G;
   for (int dz = -r; dz <= r; ++dz) {
     int cz = c[2] + dz;
     if (cz < 0 || cz >= G) continue;
     float lz = nn_axis_gap(q[2], cz, g, margin);
     float lz2 = lz * lz;
-    if (lz2 > thr) continue;
-    for (int dy = -r; dy <= r; ++dy) {
+    bool zedge = (dz == -r || dz == r);
+    int step = zedge ? 1 : 2 * r;
+    for (int dy = -r; dy <= r; dy += (step > 0 ? step : 1)) {
       int cy = c[1] + dy;
       if (cy < 0 || cy >= G) continue;
       float ly = nn_axis_gap(q[1], cy, g, margin);
       float lyz2 = fmaf(ly, ly, lz2);
       if (lyz2 > thr) continue;
-      float rad = sqrtf(thr - lyz2) * 1.000001f + margin;  // thr may be +inf
       int xa = 0, xb = G - 1;
-      if (rad < 4.0f) {
+      float rem = thr - lyz2;
+      if (rem < 16.0f) {
+        float rad = sqrtf(rem) * 1.000001f + margin;
         xa = nn_cell(q[0] - rad, g);
         xb = nn_cell(q[0] + rad, g);
       }
       int64_t row = ((int64_t)cz * G + cy) * G;
-      bool full = (dz == -r || dz == r || dy == -r || dy == r);
-      if (full) {
-        int x0 = max(max(c[0] - r, 0), xa), x1 = min(min(c[0] + r, G - 1), xb);
-        if (x0 <= x1) visit(__ldg(g.start + row + x0), __ldg(g.start + row + x1 + 1));
-      } else {
-        int xl = c[0] - r, xr = c[0] + r;
-        if (xl >= 0 && xl >= xa && xl <= xb) visit(__ldg(g.start + row + xl), __ldg(g.start + row + xl + 1));
-        if (xr < G && xr >= xa && xr <= xb) visit(__ldg(g.start + row + xr), __ldg(g.start + row + xr + 1));
-      }
+      visit(__ldg(g.start + row + xa), __ldg(g.start + row + xb + 1));
+      if (r == 0) break;
     }
+  }
+}
+
+// Scan rows ring by ring until no unscanned row can hold a point within the
+// pruning radius; returns the last ring visited.
+template <typename F>
+__device__ __forceinline__ int nn_ball_scan(const float q[3], const int c[3], const NNGrid& g, float margin,
+                                            const float& thr, const float& b1, F&& visit) {
+  int r = 0;
+  for (; r <= g.G; ++r) {
+    if (r > 0) {
+      float gap = nn_gap_yz(q, c, r - 1, g);
+      if (gap == INFINITY) break;
+      float gs = gap - margin;
+      if (b1 < INFINITY && gs > 0.f && gs * gs > thr) break;
+    }
+    nn_row_ring(q, c, r, g, margin, thr, visit);
+  }
+  return r - 1;
+}
+
+// Count of the records gp_step will treat as valid (q inside the domain, the
+// cells of q and of its nearest point in the pull band), one atomic per warp.
+__device__ __forceinline__ void nn_count_valid(int32_t* nvalid, bool valid) {
+  unsigned m = __activemask();
+  unsigned vb = __ballot_sync(m, valid);
+  if ((int)(threadIdx.x & 31) == __ffs(m) - 1 && vb) atomicAdd(nvalid, __popc(vb));
+}
+
+// NaN surface point for queries outside the domain of the search.
+__device__ __forceinline__ void nn_invalid(int64_t i, const float q[3], int32_t* nn_out, float* rec) {
+  if (nn_out) nn_out[i] = -1;
+  if (rec) {
+    for (int a = 0; a < 6; ++a) rec[6 * i + a] = a < 3 ? q[a] : __int_as_float(0x7fc00000);
   }
 }
 
 __global__ void __launch_bounds__(256) k_nn(NNGrid g, const float* __restrict__ qin, int64_t n,
                                             const int32_t* __restrict__ hint, int64_t J,
                                             const float* __restrict__ pts_orig, int32_t* __restrict__ nn_out,
-                                            float* __restrict__ rec) {
+                                            float* __restrict__ rec, Grid band, int32_t* __restrict__ nvalid) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   float q[3] = {qin[3 * i], qin[3 * i + 1], qin[3 * i + 2]};
+  if (!(fabsf(q[0]) <= 1e18f && fabsf(q[1]) <= 1e18f && fabsf(q[2]) <= 1e18f)) {
+    // Non-finite or huge query (its squared distances would overflow float32):
+    // outside the domain of the search.  Report -1 and a NaN surface point.
+    nn_invalid(i, q, nn_out, rec);
+    if (nvalid) nn_count_valid(nvalid, false);
+    return;
+  }
   int c[3] = {nn_cell(q[0], g), nn_cell(q[1], g), nn_cell(q[2], g)};
   float margin = nn_margin(q);
   NNState st{INFINITY, INFINITY, INFINITY, 0x7fffffff};
@@ -275,21 +327,10 @@ __global__ void __launch_bounds__(256) k_nn(NNGrid g, const float* __restrict__ 
       nn_update(st, dx * dx + dy * dy + dz * dz, __float_as_int(P.w));
     }
   };
-  int r_end = 0;
-  for (int r = 0; r <= g.G; ++r) {
-    nn_ring_pruned(q, c, r, g, margin, st.thr, scan);
-    r_end = r;
-    float gap = nn_gap(q, c, r, g);
-    if (gap == INFINITY) break;
-    float gs = gap - margin;
-    if (st.b1 < INFINITY && gs > 0.f && gs * gs > st.thr) break;
-  }
-  if (st.j1 == 0x7fffffff) {
-    // Non-finite query: no point compares below it.  Report -1, NaN record.
-    if (nn_out) nn_out[i] = -1;
-    if (rec) {
-      for (int a = 0; a < 6; ++a) rec[6 * i + a] = a < 3 ? q[a] : __int_as_float(0x7fc00000);
-    }
+  const int r_end = nn_ball_scan(q, c, g, margin, st.thr, st.b1, scan);
+  if (st.j1 == 0x7fffffff) {  // cannot happen for J >= 1 and a finite query
+    nn_invalid(i, q, nn_out, rec);
+    if (nvalid) nn_count_valid(nvalid, false);
     return;
   }
   int best = st.j1;
@@ -314,17 +355,22 @@ __global__ void __launch_bounds__(256) k_nn(NNGrid g, const float* __restrict__ 
         }
       }
     };
-    for (int r = 0; r <= r_end; ++r) nn_ring_pruned(q, c, r, g, margin, thr, rank);
+    for (int r = 0; r <= r_end; ++r) nn_row_ring(q, c, r, g, margin, thr, rank);
     if (bj != 0x7fffffff) best = bj;
   }
+  float s3[3] = {pts_orig[3 * (int64_t)best], pts_orig[3 * (int64_t)best + 1], pts_orig[3 * (int64_t)best + 2]};
   if (nn_out) nn_out[i] = best;
   if (rec) {
     rec[6 * i + 0] = q[0];
     rec[6 * i + 1] = q[1];
     rec[6 * i + 2] = q[2];
-    rec[6 * i + 3] = pts_orig[3 * (int64_t)best];
-    rec[6 * i + 4] = pts_orig[3 * (int64_t)best + 1];
-    rec[6 * i + 5] = pts_orig[3 * (int64_t)best + 2];
+    rec[6 * i + 3] = s3[0];
+    rec[6 * i + 4] = s3[1];
+    rec[6 * i + 5] = s3[2];
+  }
+  if (nvalid) {
+    Cells C;
+    nn_count_valid(nvalid, classify(band, q, s3, C));
   }
 }
 
@@ -401,14 +447,22 @@ extern "C" gp_status gp_band_sigma(const gp_band* b, float* sigma_dev) {
 }
 
 extern "C" gp_status gp_nn(gp_band* b, const float* q_dev, int64_t n, const int32_t* hint_dev, int32_t* nn_dev,
-                           float* rec_dev) {
+                           float* rec_dev, int32_t* nvalid_dev) {
   if (!b) return GP_ERR_ARG;
   gp_ctx* ctx = b->ctx;
   if (n < 0 || n >= (int64_t(1) << 31)) return gp_fail(ctx, GP_ERR_ARG, "gp_nn: n must be in [0, 2^31)");
+  if (nvalid_dev) GP_CUDA(ctx, cudaMemsetAsync(nvalid_dev, 0, sizeof(int32_t), ctx->stream));
   if (n == 0) return GP_OK;
   if (!q_dev || (!nn_dev && !rec_dev)) return gp_fail(ctx, GP_ERR_ARG, "gp_nn: null pointer");
   NNGrid g = make_grid(b);
+  Grid band;
+  band.table = b->brick_table;
+  band.masks = b->masks;
+  band.D = b->D;
+  band.nb = b->nb;
+  band.R = b->R;
+  band.half_r = 0.5f * (float)b->R;
   GP_KERNEL(ctx, "k_nn", k_nn<<<gp_blocks(n, 256), 256, 0, ctx->stream>>>(g, q_dev, n, hint_dev, b->J, b->pts, nn_dev,
-                                                                           rec_dev));
+                                                                           rec_dev, band, nvalid_dev));
   return GP_OK;
 }

@@ -34,15 +34,6 @@ constexpr double FIX_HI = 1048576.0;                     // 2^20
 constexpr double FIX_LO = 1152921504606846976.0;         // 2^60
 constexpr double FIX_LIMIT = 4398046511104.0;            // 2^42
 
-struct Grid {
-  const int32_t* __restrict__ table;
-  const uint32_t* __restrict__ masks;
-  const float* __restrict__ D;
-  int nb;
-  int R;
-  float half_r;  // R/2 = 1/h
-};
-
 struct Eval {
   float f;
   float gt[3];  // df/dt (t = local coordinate in cell units)
@@ -92,43 +83,64 @@ __device__ __forceinline__ Eval trilerp(const float d[8], const float t[3]) {
   return r;
 }
 
-struct Cells {
-  int cq[3], cs[3];
-  float tq[3], ts[3];
-  int slot_q, slot_s;
+// Loss slots from the per-block partial sums, in a fixed order (run by one
+// whole block).
+struct FinalArgs {
+  int32_t* done;       // blocks of the last kernel that have finished
+  int q_blocks, tv_blocks;
+  const int32_t* bv;
+  int64_t n_tv;
+  float alpha, beta, gamma;
+  int tv_on;
+  float* loss;
 };
 
-// Validity of a record (Sec. 3 pull band; readings in the header): q inside
-// the domain, cell(q) and cell(s) in the M1 band.
-__device__ __forceinline__ bool classify(const Grid& G, const float q[3], const float s[3], Cells& C) {
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    gp_cell1 g = gp_cell_exact(q[a], G.half_r);
-    if (g.c < 0 || g.c > G.R - 1) return false;
-    C.cq[a] = g.c;
-    C.tq[a] = g.t;
-    gp_cell1 h = gp_cell_exact(s[a], G.half_r);
-    if (h.c == -(1 << 30)) return false;
-    int cc = min(max(h.c, 0), G.R - 1);
-    C.cs[a] = cc;
-    C.ts[a] = h.t + (float)(h.c - cc);
+__device__ void finalize_loss(const double* __restrict__ partials, const FinalArgs& fa) {
+  __shared__ double red[4][32];
+  double sums[4] = {0, 0, 0, 0};
+  for (int b = threadIdx.x; b < fa.q_blocks; b += blockDim.x) {
+    sums[0] += __ldcg(partials + (int64_t)b * 8 + 0);
+    sums[1] += __ldcg(partials + (int64_t)b * 8 + 1);
+    sums[2] += __ldcg(partials + (int64_t)b * 8 + 2);
   }
-  C.slot_q = gp_brick_slot(G.table, G.nb, C.cq[0], C.cq[1], C.cq[2]);
-  if (C.slot_q < 0 || !gp_mask_bit(G.masks, C.slot_q, 2, gp_local(C.cq[0], C.cq[1], C.cq[2]))) return false;
-  C.slot_s = gp_brick_slot(G.table, G.nb, C.cs[0], C.cs[1], C.cs[2]);
-  if (C.slot_s < 0 || !gp_mask_bit(G.masks, C.slot_s, 2, gp_local(C.cs[0], C.cs[1], C.cs[2]))) return false;
-  return true;
+  for (int b = threadIdx.x; b < fa.tv_blocks; b += blockDim.x) sums[3] += __ldcg(partials + (int64_t)b * 8 + 3);
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    double v = gp_warp_sum_d(sums[c]);
+    if ((threadIdx.x & 31) == 0) red[c][threadIdx.x >> 5] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t[4] = {0, 0, 0, 0};
+    for (int c = 0; c < 4; ++c)
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t[c] += red[c][w];
+    int b = *fa.bv;
+    double lp = b > 0 ? t[0] / b : 0.0, lg = b > 0 ? t[1] / b : 0.0, ls = b > 0 ? t[2] / b : 0.0;
+    double lt = (fa.tv_on && fa.n_tv > 0) ? t[3] / (double)fa.n_tv : 0.0;
+    float* loss = fa.loss;
+    loss[GP_LOSS_TOTAL] = (float)(lp + fa.alpha * lt + fa.beta * ls + fa.gamma * lg);
+    loss[GP_LOSS_PULL] = (float)lp;
+    loss[GP_LOSS_GRAD] = (float)lg;
+    loss[GP_LOSS_SURF] = (float)ls;
+    loss[GP_LOSS_TV] = (float)lt;
+    loss[GP_LOSS_BV] = (float)b;
+    loss[GP_LOSS_T] = (float)fa.n_tv;
+    loss[7] = 0.f;
+  }
 }
 
-__device__ __forceinline__ void load_rec(const float* __restrict__ rec, int64_t i, float q[3], float s[3]) {
-  const float2* r2 = reinterpret_cast<const float2*>(rec + 6 * i);
-  float2 a = __ldg(r2), b = __ldg(r2 + 1), c = __ldg(r2 + 2);
-  q[0] = a.x;
-  q[1] = a.y;
-  q[2] = b.x;
-  s[0] = b.y;
-  s[1] = c.x;
-  s[2] = c.y;
+// The last block of the step's last kernel to finish (threadfence reduction)
+// writes the loss slots and re-arms the counter for the next call.
+__device__ void finish_if_last(const double* __restrict__ partials, const FinalArgs& fa) {
+  __shared__ int am_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) am_last = (atomicAdd(fa.done, 1) == (int)gridDim.x - 1);
+  __syncthreads();
+  if (!am_last) return;
+  __threadfence();
+  finalize_loss(partials, fa);
+  if (threadIdx.x == 0) *fa.done = 0;
 }
 
 __global__ void k_count_valid(Grid G, const float* __restrict__ rec, int64_t B, int32_t* __restrict__ nvalid) {
@@ -208,14 +220,13 @@ __device__ __forceinline__ void block_store3(double* __restrict__ partials, floa
   }
 }
 
-template <bool DET, bool GRAD>
+template <bool DET, bool GRAD, bool LAST>
 __global__ void __launch_bounds__(Q_THREADS) k_query(Grid G, const float* __restrict__ rec, int64_t B,
-                                                     const int32_t* __restrict__ nproc,
                                                      const int32_t* __restrict__ bv, float beta, float gamma,
                                                      float* __restrict__ grad, unsigned long long* __restrict__ acc,
-                                                     double* __restrict__ partials, int32_t* __restrict__ err) {
-  int64_t n = nproc ? (int64_t)(*nproc) : B;
-  if (n > B) n = B;
+                                                     double* __restrict__ partials, int32_t* __restrict__ err,
+                                                     FinalArgs fa) {
+  const int64_t n = B;
   int bvv = *bv;
   float w = bvv > 0 ? 1.0f / (float)bvv : 0.f;
   if (DET) w = 1.0f;  // fixed-point sums are scaled by 1/B_v at the end
@@ -276,45 +287,33 @@ __global__ void __launch_bounds__(Q_THREADS) k_query(Grid G, const float* __rest
     scatter8<DET>(G, grad, acc, err, C.cs, C.slot_s, C.ts, dfs, Gs);
   }
   block_store3(partials, sp, sg, ss);
+  if (LAST) finish_if_last(partials, fa);
 }
 
-__device__ __forceinline__ float vload(const Grid& G, int i, int j, int k, bool& ok) {
-  int s = gp_brick_slot(G.table, G.nb, i, j, k);
-  if (s < 0) {
-    ok = false;
-    return 0.f;
-  }
-  return __ldg(G.D + gp_vaddr(s, i, j, k));
-}
+// One block of 512 threads per brick (grid-stride over bricks).  The brick and
+// a two-vertex halo (12^3 values, with stored / in-grid / T flags) are staged in
+// shared memory; TV and 1/TV are computed for the brick plus a one-vertex halo
+// (10^3), and each of the 512 vertices then gathers its gradient from shared
+// memory.  Writes the gradient of every stored slot: alpha/|T| * dTV/dd_i (+ the
+// fixed-point query sums in deterministic mode, which are cleared for the next
+// step).  Each TV_i enters the loss sum once, from the brick that stores i.
+constexpr int HS = 12;            // staged edge: brick (8) + 2 on each side
+constexpr int HN = HS * HS * HS;  // 1728
+constexpr int IS = 10;            // TV edge: brick + 1 on each side
+constexpr int IN = IS * IS * IS;  // 1000
 
-__device__ __forceinline__ bool vin_t(const Grid& G, int i, int j, int k) {
-  int s = gp_brick_slot(G.table, G.nb, i, j, k);
-  return s >= 0 && gp_mask_bit(G.masks, s, 0, gp_local(i, j, k));
-}
+__device__ __forceinline__ int hidx(int x, int y, int z) { return ((z + 2) * HS + (y + 2)) * HS + (x + 2); }
+__device__ __forceinline__ int iidx(int x, int y, int z) { return ((z + 1) * IS + (y + 1)) * IS + (x + 1); }
 
-// TV_n of vertex (i,j,k) from its in-grid axis neighbours.
-__device__ __forceinline__ float tv_of(const Grid& G, int i, int j, int k, float dc, bool& ok) {
-  const int di[6] = {-1, 1, 0, 0, 0, 0}, dj[6] = {0, 0, -1, 1, 0, 0}, dk[6] = {0, 0, 0, 0, -1, 1};
-  float s = 0.f;
-#pragma unroll
-  for (int t = 0; t < 6; ++t) {
-    int a = i + di[t], b = j + dj[t], c = k + dk[t];
-    if (a < 0 || b < 0 || c < 0 || a > G.R || b > G.R || c > G.R) continue;
-    float e = dc - vload(G, a, b, c, ok);
-    s = fmaf(e, e, s);
-  }
-  return sqrtf(s);
-}
-
-// One block of 512 threads per brick (grid-stride over bricks).  Writes the
-// gradient of every stored slot: alpha/|T| * dTV/dd_i (+ the fixed-point query
-// sums in deterministic mode, which are cleared for the next step).
-template <bool DET, bool GRAD, bool TV>
+template <bool DET, bool GRAD, bool TV, bool LAST>
 __global__ void __launch_bounds__(TV_THREADS) k_tv(Grid G, const int32_t* __restrict__ coord, int64_t n_bricks,
                                                    float tv_scale, float* __restrict__ grad,
                                                    unsigned long long* __restrict__ acc,
                                                    const int32_t* __restrict__ bv, double* __restrict__ partials,
-                                                   int32_t* __restrict__ err) {
+                                                   int32_t* __restrict__ err, FinalArgs fa) {
+  __shared__ float sD[HN];
+  __shared__ uint8_t sF[HN];  // bit0: stored and inside [0,R]^3, bit1: in T
+  __shared__ float sInv[IN];  // 1/TV of T vertices of the inner region, else 0
   float tsum = 0.f;
   double qscale = 0.0;
   if (DET) {
@@ -322,43 +321,73 @@ __global__ void __launch_bounds__(TV_THREADS) k_tv(Grid G, const int32_t* __rest
     qscale = b > 0 ? 1.0 / (double)b : 0.0;
   }
   const int l = threadIdx.x;
+  const int lx = l & 7, ly = (l >> 3) & 7, lz = l >> 6;
   for (int64_t slot = blockIdx.x; slot < n_bricks; slot += gridDim.x) {
-    int i = coord[3 * slot] * 8 + (l & 7);
-    int j = coord[3 * slot + 1] * 8 + ((l >> 3) & 7);
-    int k = coord[3 * slot + 2] * 8 + (l >> 6);
-    int64_t addr = slot * 512 + l;
-    float gsum = 0.f;
-    bool ok = true;
-    if (TV && i <= G.R && j <= G.R && k <= G.R) {
-      float di = __ldg(G.D + addr);
-      if (gp_mask_bit(G.masks, (int)slot, 0, l)) {
-        float tvi = tv_of(G, i, j, k, di, ok);
-        tsum += tvi;
-        if (GRAD && tvi > 0.f) {
-          const int xi[6] = {-1, 1, 0, 0, 0, 0}, xj[6] = {0, 0, -1, 1, 0, 0}, xk[6] = {0, 0, 0, 0, -1, 1};
-          float inv = 1.0f / tvi;
-          for (int t = 0; t < 6; ++t) {
-            int a = i + xi[t], b = j + xj[t], c = k + xk[t];
-            if (a < 0 || b < 0 || c < 0 || a > G.R || b > G.R || c > G.R) continue;
-            gsum += (di - vload(G, a, b, c, ok)) * inv;
+    const int ox = coord[3 * slot] * 8, oy = coord[3 * slot + 1] * 8, oz = coord[3 * slot + 2] * 8;
+    const int64_t addr = slot * 512 + l;
+    if (TV) {
+      __syncthreads();  // previous brick done with the shared arrays
+      for (int h = l; h < HN; h += TV_THREADS) {
+        int hx = h % HS - 2, hy = (h / HS) % HS - 2, hz = h / (HS * HS) - 2;
+        int i = ox + hx, j = oy + hy, k = oz + hz;
+        float v = 0.f;
+        uint8_t f = 0;
+        if (i >= 0 && j >= 0 && k >= 0 && i <= G.R && j <= G.R && k <= G.R) {
+          int s = gp_brick_slot(G.table, G.nb, i, j, k);
+          if (s >= 0) {
+            int loc = gp_local(i, j, k);
+            v = __ldg(G.D + (int64_t)s * 512 + loc);
+            f = 1 | (gp_mask_bit(G.masks, s, 0, loc) ? 2 : 0);
           }
         }
+        sD[h] = v;
+        sF[h] = f;
       }
-      if (GRAD) {
-        const int xi[6] = {-1, 1, 0, 0, 0, 0}, xj[6] = {0, 0, -1, 1, 0, 0}, xk[6] = {0, 0, 0, 0, -1, 1};
-        for (int t = 0; t < 6; ++t) {
-          int a = i + xi[t], b = j + xj[t], c = k + xk[t];
-          if (a < 0 || b < 0 || c < 0 || a > G.R || b > G.R || c > G.R) continue;
-          if (!vin_t(G, a, b, c)) continue;
-          float dn = vload(G, a, b, c, ok);
-          float tvn = tv_of(G, a, b, c, dn, ok);
-          if (tvn > 0.f) gsum += (di - dn) / tvn;
+      __syncthreads();
+      for (int h = l; h < IN; h += TV_THREADS) {
+        int x = h % IS - 1, y = (h / IS) % IS - 1, z = h / (IS * IS) - 1;
+        int c = hidx(x, y, z);
+        float inv = 0.f;
+        if ((sF[c] & 3) == 3) {
+          float dc = sD[c], acc2 = 0.f;
+          const int nb6[6] = {hidx(x - 1, y, z), hidx(x + 1, y, z), hidx(x, y - 1, z),
+                              hidx(x, y + 1, z), hidx(x, y, z - 1), hidx(x, y, z + 1)};
+#pragma unroll
+          for (int t = 0; t < 6; ++t) {
+            if (sF[nb6[t]] & 1) {
+              float e = dc - sD[nb6[t]];
+              acc2 = fmaf(e, e, acc2);
+            }
+          }
+          float tv = sqrtf(acc2);
+          if (x >= 0 && y >= 0 && z >= 0 && x < 8 && y < 8 && z < 8) tsum += tv;
+          inv = tv > 0.f ? 1.0f / tv : 0.f;
+        }
+        sInv[h] = inv;
+      }
+      __syncthreads();
+    }
+    if (GRAD) {
+      float gv = 0.f;
+      if (TV) {
+        int c = hidx(lx, ly, lz);
+        if (sF[c] & 1) {
+          float di = sD[c];
+          float own = sInv[iidx(lx, ly, lz)];
+          const int hn[6] = {hidx(lx - 1, ly, lz), hidx(lx + 1, ly, lz), hidx(lx, ly - 1, lz),
+                             hidx(lx, ly + 1, lz), hidx(lx, ly, lz - 1), hidx(lx, ly, lz + 1)};
+          const int in6[6] = {iidx(lx - 1, ly, lz), iidx(lx + 1, ly, lz), iidx(lx, ly - 1, lz),
+                              iidx(lx, ly + 1, lz), iidx(lx, ly, lz - 1), iidx(lx, ly, lz + 1)};
+          float gsum = 0.f;
+#pragma unroll
+          for (int t = 0; t < 6; ++t) {
+            if (!(sF[hn[t]] & 1)) continue;  // outside the grid or not stored
+            float e = di - sD[hn[t]];
+            gsum += e * own + e * sInv[in6[t]];
+          }
+          gv = tv_scale * gsum;
         }
       }
-    }
-    if (!ok) atomicOr(err, GP_EF_RANGE);
-    if (GRAD) {
-      float gv = tv_scale * gsum;
       if (DET) {
         long long hi = (long long)acc[2 * addr], lo = (long long)acc[2 * addr + 1];
         acc[2 * addr] = 0ull;
@@ -375,45 +404,12 @@ __global__ void __launch_bounds__(TV_THREADS) k_tv(Grid G, const int32_t* __rest
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = w;
   __syncthreads();
   if (threadIdx.x == 0) {
-    double s = 0;
-    for (int k = 0; k < TV_THREADS / 32; ++k) s += red[k];
-    partials[(int64_t)blockIdx.x * 8 + 3] = s;
+    double sum = 0;
+    for (int k = 0; k < TV_THREADS / 32; ++k) sum += red[k];
+    partials[(int64_t)blockIdx.x * 8 + 3] = sum;
   }
-}
-
-__global__ void k_finalize(const double* __restrict__ partials, int q_blocks, int tv_blocks,
-                           const int32_t* __restrict__ bv, int64_t n_tv, float alpha, float beta, float gamma,
-                           int tv_on, float* __restrict__ loss) {
-  __shared__ double red[4][32];
-  double s[4] = {0, 0, 0, 0};
-  for (int b = threadIdx.x; b < q_blocks; b += blockDim.x) {
-    s[0] += partials[(int64_t)b * 8 + 0];
-    s[1] += partials[(int64_t)b * 8 + 1];
-    s[2] += partials[(int64_t)b * 8 + 2];
-  }
-  for (int b = threadIdx.x; b < tv_blocks; b += blockDim.x) s[3] += partials[(int64_t)b * 8 + 3];
-#pragma unroll
-  for (int c = 0; c < 4; ++c) {
-    double v = gp_warp_sum_d(s[c]);
-    if ((threadIdx.x & 31) == 0) red[c][threadIdx.x >> 5] = v;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t[4] = {0, 0, 0, 0};
-    for (int c = 0; c < 4; ++c)
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t[c] += red[c][w];
-    int b = *bv;
-    double lp = b > 0 ? t[0] / b : 0.0, lg = b > 0 ? t[1] / b : 0.0, ls = b > 0 ? t[2] / b : 0.0;
-    double lt = (tv_on && n_tv > 0) ? t[3] / (double)n_tv : 0.0;
-    loss[GP_LOSS_TOTAL] = (float)(lp + alpha * lt + beta * ls + gamma * lg);
-    loss[GP_LOSS_PULL] = (float)lp;
-    loss[GP_LOSS_GRAD] = (float)lg;
-    loss[GP_LOSS_SURF] = (float)ls;
-    loss[GP_LOSS_TV] = (float)lt;
-    loss[GP_LOSS_BV] = (float)b;
-    loss[GP_LOSS_T] = (float)n_tv;
-    loss[7] = 0.f;
-  }
+  if (LAST) finish_if_last(partials, fa);
+  (void)err;
 }
 
 __global__ void __launch_bounds__(512) k_adam(const int32_t* __restrict__ active, int64_t n_active,
@@ -470,6 +466,7 @@ extern "C" gp_status gp_step(gp_band* b, const float* rec_dev, int64_t B, const 
   G.R = b->R;
   G.half_r = 0.5f * (float)b->R;
   int32_t* err = b->dev_ints + GP_DI_ERROR;
+  // B_v: given by the caller (e.g. counted by gp_nn) or counted here.
   const int32_t* bv = nvalid_dev;
   if (!bv) {
     int32_t* cnt = b->dev_ints + GP_DI_NVALID;
@@ -480,22 +477,38 @@ extern "C" gp_status gp_step(gp_band* b, const float* rec_dev, int64_t B, const 
     bv = cnt;
   }
   const unsigned qb = q_grid(ctx, B);
-  const unsigned tb = tv_grid(ctx, b->n_bricks);
+  const unsigned tb = b->n_bricks ? tv_grid(ctx, b->n_bricks) : 1;
   const float tv_scale = (tv_on && b->V_tv > 0) ? w->alpha / (float)b->V_tv : 0.f;
+  FinalArgs fa;
+  fa.done = b->dev_ints + GP_DI_DONE;
+  fa.q_blocks = (int)qb;
+  fa.tv_blocks = (int)tb;
+  fa.bv = bv;
+  fa.n_tv = b->V_tv;
+  fa.alpha = w->alpha;
+  fa.beta = w->beta;
+  fa.gamma = w->gamma;
+  fa.tv_on = tv_on ? 1 : 0;
+  fa.loss = loss_dev;
+  // The TV sweep writes (overwrites) the gradient and the query pass adds to
+  // it; in deterministic mode the query pass fills the fixed-point sums first
+  // and the sweep folds them in.  Whichever runs second writes the loss.
+  const bool tv_last = det && grad_on;
   auto launch_tv = [&]() -> gp_status {
     if (b->n_bricks == 0) {
       GP_CUDA(ctx, cudaMemsetAsync(b->partials + 3, 0, sizeof(double), s));
       return GP_OK;
     }
-#define GP_TV(D_, G_, T_) \
-  k_tv<D_, G_, T_><<<tb, TV_THREADS, 0, s>>>(G, b->brick_coord, b->n_bricks, tv_scale, grad_dev, b->acc, bv, b->partials, err)
+#define GP_TV(D_, G_, T_, L_)                                                                                  \
+  k_tv<D_, G_, T_, L_><<<tb, TV_THREADS, 0, s>>>(G, b->brick_coord, b->n_bricks, tv_scale, grad_dev, b->acc, bv, \
+                                                 b->partials, err, fa)
     gp_prof_pre(ctx);
-    if (det && grad_on) {
-      if (tv_on) GP_TV(true, true, true); else GP_TV(true, true, false);
+    if (tv_last) {
+      if (tv_on) GP_TV(true, true, true, true); else GP_TV(true, true, false, true);
     } else if (grad_on) {
-      if (tv_on) GP_TV(false, true, true); else GP_TV(false, true, false);
+      if (tv_on) GP_TV(false, true, true, false); else GP_TV(false, true, false, false);
     } else {
-      if (tv_on) GP_TV(false, false, true); else GP_TV(false, false, false);
+      if (tv_on) GP_TV(false, false, true, false); else GP_TV(false, false, false, false);
     }
 #undef GP_TV
     gp_prof_post(ctx, "k_tv");
@@ -505,31 +518,27 @@ extern "C" gp_status gp_step(gp_band* b, const float* rec_dev, int64_t B, const 
   auto launch_q = [&]() -> gp_status {
     gp_prof_pre(ctx);
     if (det && grad_on)
-      k_query<true, true><<<qb, Q_THREADS, 0, s>>>(G, rec_dev, B, nvalid_dev, bv, w->beta, w->gamma, grad_dev, b->acc,
-                                                   b->partials, err);
+      k_query<true, true, false><<<qb, Q_THREADS, 0, s>>>(G, rec_dev, B, bv, w->beta, w->gamma, grad_dev, b->acc,
+                                                          b->partials, err, fa);
     else if (grad_on)
-      k_query<false, true><<<qb, Q_THREADS, 0, s>>>(G, rec_dev, B, nvalid_dev, bv, w->beta, w->gamma, grad_dev, b->acc,
-                                                    b->partials, err);
+      k_query<false, true, true><<<qb, Q_THREADS, 0, s>>>(G, rec_dev, B, bv, w->beta, w->gamma, grad_dev, b->acc,
+                                                          b->partials, err, fa);
     else
-      k_query<false, false><<<qb, Q_THREADS, 0, s>>>(G, rec_dev, B, nvalid_dev, bv, w->beta, w->gamma, grad_dev,
-                                                     b->acc, b->partials, err);
+      k_query<false, false, true><<<qb, Q_THREADS, 0, s>>>(G, rec_dev, B, bv, w->beta, w->gamma, grad_dev, b->acc,
+                                                           b->partials, err, fa);
     gp_prof_post(ctx, "k_query");
     GP_LAUNCH_CHECK(ctx, "k_query");
     return GP_OK;
   };
   gp_status st;
-  // The TV sweep writes (overwrites) the gradient; the query pass adds to it.
-  // In deterministic mode the query pass fills the fixed-point sums first and
-  // the sweep folds them in.
-  if (det && grad_on) {
+  if (tv_last) {
     if ((st = launch_q())) return st;
+    if (b->n_bricks == 0) return gp_fail(ctx, GP_ERR_STATE, "gp_step: empty band");
     if ((st = launch_tv())) return st;
   } else {
     if ((st = launch_tv())) return st;
     if ((st = launch_q())) return st;
   }
-  GP_KERNEL(ctx, "k_finalize", k_finalize<<<1, 256, 0, s>>>(b->partials, (int)qb, b->n_bricks ? (int)tb : 1, bv, b->V_tv, w->alpha, w->beta,
-                               w->gamma, tv_on ? 1 : 0, loss_dev));
   return GP_OK;
 }
 

@@ -34,6 +34,7 @@ class FitStep:
         self.rec = torch.empty((self.B, 6), dtype=torch.float32, device=dev)
         self.grad = torch.empty(band.V_stored, dtype=torch.float32, device=dev)
         self.loss = torch.zeros(8, dtype=torch.float32, device=dev)
+        self.nvalid = torch.zeros(1, dtype=torch.int32, device=dev)
 
     def batch_of(self, t: int):
         epoch, b = divmod(int(t), self.batches_per_epoch)
@@ -50,7 +51,7 @@ class FitStep:
         band = self.band
         epoch, first, count = self.batch_of(t)
         gb.gp_sample(band, self.seed, epoch, self.Q, first, count, self.q, self.src)
-        gb.gp_nn(band, self.q[:count], None, self.rec, hint=self.src[:count])
-        gb.gp_step(band, self.rec, count, self.grad, self.loss, self.weights, flags=self.flags)
+        gb.gp_nn(band, self.q[:count], None, self.rec, hint=self.src[:count], nvalid_out=self.nvalid)
+        gb.gp_step(band, self.rec, count, self.grad, self.loss, self.weights, nvalid=self.nvalid, flags=self.flags)
         gb.gp_update(band, self.grad, self.lr_at(t), t + 1)
         return self.loss

@@ -138,13 +138,30 @@ def test_nn_matches_bruteforce_sphere(gb, ctx, sphere5k):
         assert np.array_equal(nn_h, want)
 
 
+def test_nn_counts_valid_records(gb, ctx, sphere5k):
+    import torch
+    R = 64
+    band = _band(gb, ctx, sphere5k, R, 2, 2, knn_k=0)
+    q1, _ = synth.gaussian_queries(sphere5k, 20000, 0.05, seed=12)
+    q = np.concatenate([q1, np.random.default_rng(2).uniform(-1.2, 1.2, (5000, 3)).astype(np.float32)])
+    nv = torch.zeros(1, dtype=torch.int32, device="cuda")
+    rec = torch.empty((len(q), 6), dtype=torch.float32, device="cuda")
+    gb.gp_nn(band, torch.from_numpy(q).cuda(), None, rec, nvalid_out=nv)
+    s = sphere5k[o.nearest_point(q, sphere5k)]
+    res = o.query_terms(np.zeros((R + 1) ** 3), R, o.band_sets(sphere5k, R, 2, 2)["pull_cells"], q, s, 1.0, 0.005,
+                        with_grad=False)
+    assert int(nv.item()) == res["Bv"]
+    assert 0 < res["Bv"] < len(q)
+
+
 def test_nn_non_finite_queries(gb, ctx, sphere5k):
     band = _band(gb, ctx, sphere5k, 32, 1, 1, knn_k=0)
-    q = np.array([[np.nan, 0, 0], [np.inf, 0, 0], [0, -np.inf, 0.1], [0.1, 0.2, 0.3]], np.float32)
+    q = np.array([[np.nan, 0, 0], [np.inf, 0, 0], [0, -np.inf, 0.1], [1e20, 0, 0], [0.1, 0.2, 0.3],
+                  [3.0, -2.5, 7.0]], np.float32)
     nn, rec = _nn_gpu(gb, band, q)
-    assert list(nn[:3]) == [-1, -1, -1]
-    assert np.all(np.isnan(rec[:3, 3:]))
-    assert nn[3] == o.nearest_point(q[3:], sphere5k)[0]
+    assert list(nn[:4]) == [-1, -1, -1, -1]
+    assert np.all(np.isnan(rec[:4, 3:]))
+    assert np.array_equal(nn[4:], o.nearest_point(q[4:], sphere5k))
 
 
 def test_nn_ties_go_to_lowest_index(gb, ctx):
@@ -305,7 +322,12 @@ def test_step_flags_and_override(gb, ctx, sphere5k):
     w = (1.0, 1.0, 0.005)
     _check_step(gb, band, R, sets, q, s, w, D, flags=gb.GP_STEP_NO_TV)
     _check_step(gb, band, R, sets, q, s, w, D, flags=gb.GP_STEP_LOSS_ONLY)
-    _check_step(gb, band, R, sets, q, s, w, D * 1.1 + 0.01, d_override=(vals * 1.1 + 0.01).astype(np.float32))
+    # Override values: the same float32 numbers on both sides.
+    ov = (vals.astype(np.float64) * 1.1 + 0.01).astype(np.float32)
+    D_ov = np.zeros_like(D)
+    req = sets["required"]
+    D_ov[req] = (D[req] * 1.1 + 0.01).astype(np.float32)
+    _check_step(gb, band, R, sets, q, s, w, D_ov, d_override=ov)
 
 
 def test_step_edge_cases(gb, ctx, sphere5k):
@@ -368,12 +390,12 @@ def test_update_matches_oracle(gb, ctx, sphere5k):
     R = 64
     band = _band(gb, ctx, sphere5k, R, 2, 2, knn_k=0)
     sets = o.band_sets(sphere5k, R, 2, 2)
-    D, _ = _set_field(gb, band, sets, R, 0.5, 0.01, seed=0)
+    D, vals = _set_field(gb, band, sets, R, 0.5, 0.01, seed=0)
     ijk, _, fl, exists = export_band(band)
     train = exists & ((fl & 2) != 0)
     keys = vertex_keys(ijk, R)
-    d0 = np.zeros(band.V_stored)
-    d0[exists] = D[keys[exists]]
+    d0 = vals.astype(np.float64)                      # what the band holds
+    assert np.array_equal(d0[train], D[keys[train]])  # the oracle sees the same trainable values
     rng = np.random.default_rng(0)
     d = d0.copy()
     m = np.zeros_like(d)
