@@ -187,18 +187,25 @@ gp_status gp_band_check(gp_band* band);
 
 /* --------------------------------------------------------------- sampling */
 
+#define GP_SAMPLE_SPATIAL 1u /* emit the batch grouped by source point, points in
+                                the order of the cloud's cell list            */
+
 /* Queries of the epoch-`epoch` pool of Q queries, pool positions
  * [first, first + count), written to q_dev (count x 3 float32).  Sec. 3: each
  * epoch visits the points in a fresh random order and draws a Gaussian query
  * around each visited point.  Position k visits point j = Pi_e(k mod J), where
  * Pi_e is a 4-round Feistel bijection of [0, J) keyed by (seed, epoch), and
  * q = s_j + sigma_j * z with z ~ N(0, I) from Philox4x32-10 at counter
- * (k, epoch, 0, 0), key (seed_lo, seed_hi), via Box-Muller.  If src_dev is
- * not NULL it receives j per query (count int32; a valid gp_nn hint).
- * Requires knn_k > 0 at build.  Errors: GP_ERR_ARG (Q > 2^31-1, first + count
- * > Q, null q_dev with count > 0), GP_ERR_STATE (no sigma). */
-gp_status gp_sample(gp_band* band, uint64_t seed, uint32_t epoch, int64_t Q, int64_t first,
-                    int64_t count, float* q_dev, int32_t* src_dev);
+ * (k, epoch, 0, 0), key (seed_lo, seed_hi), via Box-Muller.  Without flags the
+ * i-th output is position first + i; with GP_SAMPLE_SPATIAL the same set of
+ * queries is emitted grouped by source point, points in the cloud's cell-list
+ * order (replicas of a point in increasing k): neighbouring outputs are close
+ * in space.  Optional outputs (NULL to skip, count int32 each): src_dev = j
+ * (a valid gp_nn hint), pos_dev = k.  Requires knn_k > 0 at build.  Errors:
+ * GP_ERR_ARG (Q > 2^31-1, first + count > Q, null q_dev with count > 0),
+ * GP_ERR_STATE (no sigma). */
+gp_status gp_sample(gp_band* band, uint64_t seed, uint32_t epoch, int64_t Q, int64_t first, int64_t count,
+                    uint32_t flags, float* q_dev, int32_t* src_dev, int32_t* pos_dev);
 
 /* ---------------------------------------------------------- nearest point */
 

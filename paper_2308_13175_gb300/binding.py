@@ -20,6 +20,7 @@ GP_BAND_DETERMINISTIC = 1
 GP_STEP_DETERMINISTIC = 1
 GP_STEP_NO_TV = 2
 GP_STEP_LOSS_ONLY = 4
+GP_SAMPLE_SPATIAL = 1
 GP_LOSS_TOTAL, GP_LOSS_PULL, GP_LOSS_GRAD, GP_LOSS_SURF, GP_LOSS_TV, GP_LOSS_BV, GP_LOSS_T = range(7)
 
 STATUS_NAMES = {0: "GP_OK", 1: "GP_ERR_ARG", 2: "GP_ERR_OOM", 3: "GP_ERR_CUDA", 4: "GP_ERR_TIMEOUT",
@@ -75,7 +76,7 @@ SIGNATURES = {
     "gp_band_sigma": (ctypes.c_int, [_vp, _vp]),
     "gp_band_reset_adam": (ctypes.c_int, [_vp]),
     "gp_band_check": (ctypes.c_int, [_vp]),
-    "gp_sample": (ctypes.c_int, [_vp, _u64, _u32, _i64, _i64, _i64, _vp, _vp]),
+    "gp_sample": (ctypes.c_int, [_vp, _u64, _u32, _i64, _i64, _i64, _u32, _vp, _vp, _vp]),
     "gp_nn": (ctypes.c_int, [_vp, _vp, _i64, _vp, _vp, _vp, _vp]),
     "gp_step": (ctypes.c_int, [_vp, _vp, _i64, _vp, _vp, ctypes.POINTER(LossW), _vp, _vp, _u32]),
     "gp_update": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(Adam), _i64]),
@@ -292,15 +293,18 @@ def gp_band_check(band: Band):
     band.ctx.check(band.ctx.lib.gp_band_check(band.handle))
 
 
-def gp_sample(band: Band, seed: int, epoch: int, Q: int, first: int, count: int, out=None, src_out=None):
+def gp_sample(band: Band, seed: int, epoch: int, Q: int, first: int, count: int, out=None, src_out=None,
+              pos_out=None, spatial: bool = False):
     import torch
     if out is None:
         out = torch.empty((count, 3), dtype=torch.float32, device=torch.device("cuda", band.ctx.device))
     _need(out, torch.float32, 3 * count, "q")
     _need(src_out, torch.int32, count, "src")
+    _need(pos_out, torch.int32, count, "pos")
     band.ctx.sync_stream()
     band.ctx.check(band.ctx.lib.gp_sample(band.handle, int(seed), int(epoch), int(Q), int(first), int(count),
-                                          _ptr(out), _ptr(src_out)))
+                                          GP_SAMPLE_SPATIAL if spatial else 0, _ptr(out), _ptr(src_out),
+                                          _ptr(pos_out)))
     return out
 
 

@@ -81,6 +81,8 @@ struct gp_band {
   int32_t* cell_start = nullptr;   // G^3 + 1
   float* sigma = nullptr;          // J
   int32_t* perm = nullptr;         // J: Pi_e of the cached epoch
+  int32_t* inv_perm = nullptr;     // J: Pi_e^-1 (point -> pool slot within a replica)
+  int32_t* order_tiles = nullptr;  // per-tile counts / offsets of the spatial batch order
   bool perm_valid = false;
   uint64_t perm_seed = 0;
   uint32_t perm_epoch = 0;
@@ -138,8 +140,13 @@ inline unsigned gp_blocks(int64_t n, int threads, int64_t cap = 1 << 30) {
 // paths only).
 gp_status gp_exclusive_scan_i32(gp_ctx* ctx, int32_t* data, int64_t n, int64_t* total_host);
 
-// Feistel round-trip used by the sampler (also needed on the host for checks).
+// Pi_e and its inverse for (seed, epoch), recomputed only when they change.
 gp_status gp_build_permutation(gp_band* band, uint64_t seed, uint32_t epoch);
+
+// Tile of sorted points handled by one block of the spatial batch order.
+constexpr int GP_ORDER_THREADS = 512;
+constexpr int GP_ORDER_PER_THREAD = 8;
+constexpr int GP_ORDER_TILE = GP_ORDER_THREADS * GP_ORDER_PER_THREAD;
 
 // ------------------------------------------------------ device: geometry
 // Exact cell of one float32 coordinate: t = (x + 1) * R/2.  x + 1 is split

@@ -320,12 +320,21 @@ __global__ void __launch_bounds__(256) k_nn(NNGrid g, const float* __restrict__ 
       }
     }
   }
+  auto one = [&](float4 P) {
+    float dx = q[0] - P.x, dy = q[1] - P.y, dz = q[2] - P.z;
+    nn_update(st, dx * dx + dy * dy + dz * dz, __float_as_int(P.w));
+  };
+  // Points of a range, four loads in flight at a time (same visiting order).
   auto scan = [&](int a, int b) {
-    for (int p = a; p < b; ++p) {
-      float4 P = g.pts[p];
-      float dx = q[0] - P.x, dy = q[1] - P.y, dz = q[2] - P.z;
-      nn_update(st, dx * dx + dy * dy + dz * dz, __float_as_int(P.w));
+    int p = a;
+    for (; p + 4 <= b; p += 4) {
+      float4 P0 = __ldg(g.pts + p), P1 = __ldg(g.pts + p + 1), P2 = __ldg(g.pts + p + 2), P3 = __ldg(g.pts + p + 3);
+      one(P0);
+      one(P1);
+      one(P2);
+      one(P3);
     }
+    for (; p < b; ++p) one(__ldg(g.pts + p));
   };
   const int r_end = nn_ball_scan(q, c, g, margin, st.thr, st.b1, scan);
   if (st.j1 == 0x7fffffff) {  // cannot happen for J >= 1 and a finite query
@@ -431,6 +440,8 @@ gp_status gp_build_points(gp_band* b, const float* pts_dev) {
   if (b->knn_k > 0) {
     if ((st = gp_alloc(ctx, &b->sigma, J, "sigma"))) return st;
     if ((st = gp_alloc(ctx, &b->perm, J, "permutation"))) return st;
+    if ((st = gp_alloc(ctx, &b->inv_perm, J, "inverse permutation"))) return st;
+    if ((st = gp_alloc(ctx, &b->order_tiles, (J + GP_ORDER_TILE - 1) / GP_ORDER_TILE + 1, "order tiles"))) return st;
     int k = (int)std::min<int64_t>(b->knn_k, J - 1);
     GP_KERNEL(ctx, "k_knn_sigma", k_knn_sigma<<<gp_blocks(J, 128), 128, 0, s>>>(g, J, k, b->sigma));
   }

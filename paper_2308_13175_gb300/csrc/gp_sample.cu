@@ -4,14 +4,25 @@
 // [0, J) (cycle walking), keyed by (seed, epoch); z comes from Philox4x32-10
 // at counter (k, epoch, 0, 0) through Box-Muller.  Both are counter based, so
 // any pool position is generated on its own, in any order.
+//
+// A batch is the pool positions [first, first + count).  In position order the
+// queries of a batch are scattered over the whole surface.  In spatial order
+// (GP_SAMPLE_SPATIAL) the same queries are emitted grouped by their source
+// point, the points taken in the order of the cloud's cell list: position k
+// belongs to point Pi_e(k mod J), so point j owns positions Pi_e^-1(j) + r J,
+// and a three-kernel count / scan / emit pass lists them without a sort.
+// Neighbouring outputs then lie close together, which is what the nearest-point
+// search and the gather / scatter of the step profit from; the loss does not
+// depend on the order.
 #include "gp_internal.cuh"
 
 namespace {
 
 constexpr int WALK_LIMIT = 4096;  // cycle walks end in < 4 rounds on average
+constexpr int NW = GP_ORDER_THREADS / 32;
 
 __global__ void k_perm(int64_t J, int half, uint32_t epoch, uint32_t k0, uint32_t k1, int32_t* __restrict__ perm,
-                       int32_t* __restrict__ err) {
+                       int32_t* __restrict__ inv, int32_t* __restrict__ err) {
   int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= J) return;
   uint32_t x = (uint32_t)p;
@@ -24,21 +35,158 @@ __global__ void k_perm(int64_t J, int half, uint32_t epoch, uint32_t k0, uint32_
     x = (uint32_t)(x % (uint64_t)J);
   }
   perm[p] = (int32_t)x;
+  inv[x] = (int32_t)p;
+}
+
+__device__ __forceinline__ float3 draw_query(const float* __restrict__ pts, const float* __restrict__ sigma, int32_t j,
+                                             int64_t k, uint32_t epoch, uint32_t k0, uint32_t k1) {
+  float3 z = gp_box_muller3(gp_philox((uint32_t)k, epoch, 0u, 0u, k0, k1));
+  float sg = sigma[j];
+  return make_float3(pts[3 * (int64_t)j + 0] + sg * z.x, pts[3 * (int64_t)j + 1] + sg * z.y,
+                     pts[3 * (int64_t)j + 2] + sg * z.z);
+}
+
+__device__ __forceinline__ void put_query(int64_t i, float3 v, int32_t j, int64_t k, float* __restrict__ q,
+                                          int32_t* __restrict__ src, int32_t* __restrict__ pos) {
+  q[3 * i + 0] = v.x;
+  q[3 * i + 1] = v.y;
+  q[3 * i + 2] = v.z;
+  if (src) src[i] = j;
+  if (pos) pos[i] = (int32_t)k;
 }
 
 __global__ void k_sample(const float* __restrict__ pts, const float* __restrict__ sigma,
                          const int32_t* __restrict__ perm, int64_t J, int64_t first, int64_t count, uint32_t epoch,
-                         uint32_t k0, uint32_t k1, float* __restrict__ q, int32_t* __restrict__ src) {
+                         uint32_t k0, uint32_t k1, float* __restrict__ q, int32_t* __restrict__ src,
+                         int32_t* __restrict__ pos) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= count) return;
   int64_t k = first + i;
   int32_t j = perm[k % J];
-  float3 z = gp_box_muller3(gp_philox((uint32_t)k, epoch, 0u, 0u, k0, k1));
-  float sg = sigma[j];
-  q[3 * i + 0] = pts[3 * (int64_t)j + 0] + sg * z.x;
-  q[3 * i + 1] = pts[3 * (int64_t)j + 1] + sg * z.y;
-  q[3 * i + 2] = pts[3 * (int64_t)j + 2] + sg * z.z;
-  if (src) src[i] = j;
+  put_query(i, draw_query(pts, sigma, j, k, epoch, k0, k1), j, k, q, src, pos);
+}
+
+// Replicas r >= 0 of pool slot p whose position k = p + r J lies in
+// [first, last): r in [r0, r0 + n).
+__device__ __forceinline__ void owned_range(int64_t p, int64_t J, int64_t first, int64_t last, int64_t& r0, int& n) {
+  int64_t lo = first - p;
+  r0 = lo <= 0 ? 0 : (lo + J - 1) / J;
+  int64_t hi = last - 1 - p;
+  if (hi < 0) {
+    n = 0;
+    return;
+  }
+  int64_t r1 = hi / J;
+  n = r1 >= r0 ? (int)(r1 - r0 + 1) : 0;
+}
+
+// Exclusive scan of one int per thread over the block; returns the block total.
+__device__ __forceinline__ int block_exclusive_scan(int v, int* excl) {
+  __shared__ int wsum[NW];
+  __shared__ int total_s;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) wsum[wid] = incl;
+  __syncthreads();
+  if (wid == 0) {
+    int w = lane < NW ? wsum[lane] : 0;
+    int wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += y;
+    }
+    if (lane < NW) wsum[lane] = wi - w;
+    if (lane == NW - 1) total_s = wi;
+  }
+  __syncthreads();
+  *excl = wsum[wid] + incl - v;
+  int t = total_s;
+  __syncthreads();  // wsum and total_s may be reused by the next call
+  return t;
+}
+
+// Pass 1: queries owned by each tile of sorted points.
+__global__ void __launch_bounds__(GP_ORDER_THREADS) k_order_count(const float4* __restrict__ pts_sorted,
+                                                                  const int32_t* __restrict__ inv, int64_t J,
+                                                                  int64_t first, int64_t last,
+                                                                  int32_t* __restrict__ tiles) {
+  int64_t base = (int64_t)blockIdx.x * GP_ORDER_TILE + (int64_t)threadIdx.x * GP_ORDER_PER_THREAD;
+  int c = 0;
+#pragma unroll
+  for (int u = 0; u < GP_ORDER_PER_THREAD; ++u) {
+    int64_t t = base + u;
+    if (t < J) {
+      int j = __float_as_int(pts_sorted[t].w);
+      int64_t r0;
+      int n;
+      owned_range(inv[j], J, first, last, r0, n);
+      c += n;
+    }
+  }
+  int excl;
+  int total = block_exclusive_scan(c, &excl);
+  if (threadIdx.x == 0) tiles[blockIdx.x] = total;
+}
+
+// Pass 2: exclusive scan of the tile counts in place (one block, any length).
+__global__ void __launch_bounds__(GP_ORDER_THREADS) k_order_tiles(int32_t* __restrict__ tiles, int64_t ntiles) {
+  int carry = 0;
+  for (int64_t base = 0; base < ntiles; base += GP_ORDER_THREADS) {
+    int64_t i = base + threadIdx.x;
+    int v = i < ntiles ? tiles[i] : 0;
+    int excl;
+    int total = block_exclusive_scan(v, &excl);
+    if (i < ntiles) tiles[i] = carry + excl;
+    carry += total;
+  }
+}
+
+// Pass 3: every sorted point writes its queries at its offset.
+__global__ void __launch_bounds__(GP_ORDER_THREADS) k_order_emit(
+    const float4* __restrict__ pts_sorted, const int32_t* __restrict__ inv, const float* __restrict__ pts,
+    const float* __restrict__ sigma, int64_t J, int64_t first, int64_t last, const int32_t* __restrict__ tiles,
+    uint32_t epoch, uint32_t k0, uint32_t k1, float* __restrict__ q, int32_t* __restrict__ src,
+    int32_t* __restrict__ pos, int32_t* __restrict__ err) {
+  int64_t base = (int64_t)blockIdx.x * GP_ORDER_TILE + (int64_t)threadIdx.x * GP_ORDER_PER_THREAD;
+  const int64_t n_out = last - first;
+  int jj[GP_ORDER_PER_THREAD], nn[GP_ORDER_PER_THREAD];
+  int64_t rr[GP_ORDER_PER_THREAD], pp[GP_ORDER_PER_THREAD];
+  int c = 0;
+#pragma unroll
+  for (int u = 0; u < GP_ORDER_PER_THREAD; ++u) {
+    int64_t t = base + u;
+    nn[u] = 0;
+    jj[u] = 0;
+    pp[u] = 0;
+    rr[u] = 0;
+    if (t < J) {
+      jj[u] = __float_as_int(pts_sorted[t].w);
+      pp[u] = inv[jj[u]];
+      owned_range(pp[u], J, first, last, rr[u], nn[u]);
+      c += nn[u];
+    }
+  }
+  int excl;
+  block_exclusive_scan(c, &excl);
+  int64_t out = (int64_t)tiles[blockIdx.x] + excl;
+#pragma unroll
+  for (int u = 0; u < GP_ORDER_PER_THREAD; ++u) {
+    for (int r = 0; r < nn[u]; ++r) {
+      int64_t k = pp[u] + (rr[u] + r) * J;
+      int64_t i = out++;
+      if (i < 0 || i >= n_out) {  // only if Pi_e were not a bijection
+        atomicOr(err, GP_EF_RANGE);
+        continue;
+      }
+      put_query(i, draw_query(pts, sigma, jj[u], k, epoch, k0, k1), jj[u], k, q, src, pos);
+    }
+  }
 }
 
 }  // namespace
@@ -47,8 +195,10 @@ gp_status gp_build_permutation(gp_band* b, uint64_t seed, uint32_t epoch) {
   if (b->perm_valid && b->perm_seed == seed && b->perm_epoch == epoch) return GP_OK;
   gp_ctx* ctx = b->ctx;
   int half = gp_feistel_bits(b->J) / 2;
-  GP_KERNEL(ctx, "k_perm", k_perm<<<gp_blocks(b->J, 256), 256, 0, ctx->stream>>>(b->J, half, epoch, (uint32_t)seed, (uint32_t)(seed >> 32),
-                                                        b->perm, b->dev_ints + GP_DI_ERROR));
+  GP_KERNEL(ctx, "k_perm",
+            k_perm<<<gp_blocks(b->J, 256), 256, 0, ctx->stream>>>(b->J, half, epoch, (uint32_t)seed,
+                                                                  (uint32_t)(seed >> 32), b->perm, b->inv_perm,
+                                                                  b->dev_ints + GP_DI_ERROR));
   b->perm_valid = true;
   b->perm_seed = seed;
   b->perm_epoch = epoch;
@@ -56,7 +206,7 @@ gp_status gp_build_permutation(gp_band* b, uint64_t seed, uint32_t epoch) {
 }
 
 extern "C" gp_status gp_sample(gp_band* b, uint64_t seed, uint32_t epoch, int64_t Q, int64_t first, int64_t count,
-                               float* q_dev, int32_t* src_dev) {
+                               uint32_t flags, float* q_dev, int32_t* src_dev, int32_t* pos_dev) {
   if (!b) return GP_ERR_ARG;
   gp_ctx* ctx = b->ctx;
   if (Q < 0 || Q >= (int64_t(1) << 31) || first < 0 || count < 0 || first + count > Q)
@@ -66,8 +216,22 @@ extern "C" gp_status gp_sample(gp_band* b, uint64_t seed, uint32_t epoch, int64_
   if (!b->sigma) return gp_fail(ctx, GP_ERR_STATE, "gp_sample: band built with knn_k = 0 (no sigma)");
   gp_status st = gp_build_permutation(b, seed, epoch);
   if (st) return st;
-  GP_KERNEL(ctx, "k_sample", k_sample<<<gp_blocks(count, 256), 256, 0, ctx->stream>>>(
-                                 b->pts, b->sigma, b->perm, b->J, first, count, epoch, (uint32_t)seed,
-                                 (uint32_t)(seed >> 32), q_dev, src_dev));
+  const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  if (!(flags & GP_SAMPLE_SPATIAL)) {
+    GP_KERNEL(ctx, "k_sample",
+              k_sample<<<gp_blocks(count, 256), 256, 0, ctx->stream>>>(b->pts, b->sigma, b->perm, b->J, first, count,
+                                                                      epoch, k0, k1, q_dev, src_dev, pos_dev));
+    return GP_OK;
+  }
+  const int64_t J = b->J, last = first + count;
+  const int64_t ntiles = (J + GP_ORDER_TILE - 1) / GP_ORDER_TILE;
+  GP_KERNEL(ctx, "k_order_count",
+            k_order_count<<<(unsigned)ntiles, GP_ORDER_THREADS, 0, ctx->stream>>>(b->pts_sorted, b->inv_perm, J,
+                                                                                 first, last, b->order_tiles));
+  GP_KERNEL(ctx, "k_order_tiles", k_order_tiles<<<1, GP_ORDER_THREADS, 0, ctx->stream>>>(b->order_tiles, ntiles));
+  GP_KERNEL(ctx, "k_order_emit",
+            k_order_emit<<<(unsigned)ntiles, GP_ORDER_THREADS, 0, ctx->stream>>>(
+                b->pts_sorted, b->inv_perm, b->pts, b->sigma, J, first, last, b->order_tiles, epoch, k0, k1, q_dev,
+                src_dev, pos_dev, b->dev_ints + GP_DI_ERROR));
   return GP_OK;
 }

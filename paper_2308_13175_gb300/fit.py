@@ -2,7 +2,7 @@
 
 ``FitStep.run(t)`` performs step t of the fit over one batch of the epoch's
 query pool: gp_sample (Gaussian queries around points visited in the epoch's
-random order) -> gp_nn (NN(q), step records; each search seeded with the
+random order, emitted grouped by source point in the cloud's cell order) -> gp_nn (NN(q), step records; each search seeded with the
 query's own source point) -> gp_step (Eq. 8 forward and
 hand-written backward) -> gp_update (Adam).  All device buffers are allocated
 once here; the calls themselves never allocate."""
@@ -50,7 +50,7 @@ class FitStep:
         """Step t (0-based); returns the loss buffer (device, 8 floats)."""
         band = self.band
         epoch, first, count = self.batch_of(t)
-        gb.gp_sample(band, self.seed, epoch, self.Q, first, count, self.q, self.src)
+        gb.gp_sample(band, self.seed, epoch, self.Q, first, count, self.q, self.src, spatial=True)
         gb.gp_nn(band, self.q[:count], None, self.rec, hint=self.src[:count], nvalid_out=self.nvalid)
         gb.gp_step(band, self.rec, count, self.grad, self.loss, self.weights, nvalid=self.nvalid, flags=self.flags)
         gb.gp_update(band, self.grad, self.lr_at(t), t + 1)
