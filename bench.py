@@ -53,7 +53,9 @@ WORKLOADS = {
 def alg_bytes(name, n, J, Vs, Vt):
     return {
         "k_sample": 32 * n,
-        "k_perm": 4 * J,
+        "k_perm": 8 * J,
+        "k_order_count": 20 * J,
+        "k_order_emit": 20 * J + 32 * n,
         "k_nn": 36 * n + 16 * J,
         "k_count_valid": 24 * n,
         "k_tv": 8 * Vs,
