@@ -249,7 +249,7 @@ def run_ours(args, world, rank, local):
     pts = wl["cloud"]()
     R = wl["R"]
     ctx = gb.gp_create(local)
-    band = gb.gp_build_band(ctx, torch.from_numpy(pts).cuda(), R, wl["M1"], wl["M2"], 50)
+    band = gb.gp_build_band(ctx, torch.from_numpy(pts).cuda(), R, wl["M1"], wl["M2"], 50, nn_grid=args.nn_grid)
     c = 0.5 * (pts.min(0) + pts.max(0))
     gb.gp_band_init_sphere(band, c, 2.0 * 2.0 / R, 0.0, seed=0)
     fit = FitStep(band, wl["Q"], wl["B"], seed=rank, weights=PAPER_WEIGHTS, lr=wl["lr"])
@@ -357,7 +357,7 @@ def run_ours(args, world, rank, local):
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-               "config": {"workload": wl["desc"], "parallelism": f"replicas x{world}",
+               "config": {"workload": wl["desc"], "parallelism": f"replicas x{world}", "nn_grid": info["nn_grid"],
                           "l2": "flushed between timed steps (256 MB write outside the step events)",
                           "V_stored": Vs, "V_trainable": Vt, "V_tv": info["V_tv"], "J": J},
                "roofline": roofline, "cpu_baseline": cpu,
@@ -378,6 +378,7 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=4096)
     ap.add_argument("--ref-sample", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--nn-grid", type=int, default=0, help="cells per axis of the point cell list (0 = automatic)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
