@@ -80,6 +80,7 @@ SIGNATURES = {
     "gp_nn": (ctypes.c_int, [_vp, _vp, _i64, _vp, _vp, _vp, _vp]),
     "gp_step": (ctypes.c_int, [_vp, _vp, _i64, _vp, _vp, ctypes.POINTER(LossW), _vp, _vp, _u32]),
     "gp_update": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(Adam), _i64]),
+    "gp_step_dense_noalloc": (ctypes.c_int, [_vp, _i32, _vp, _vp, _i64, ctypes.POINTER(LossW), _vp, _vp]),
 }
 
 
@@ -341,3 +342,18 @@ def gp_update(band: Band, grad, lr: float, step: int, beta1: float = 0.9, beta2:
     hp = Adam(float(lr), float(beta1), float(beta2), float(eps))
     band.ctx.sync_stream()
     band.ctx.check(band.ctx.lib.gp_update(band.handle, _ptr(grad), ctypes.byref(hp), int(step)))
+
+
+def gp_step_dense_noalloc(ctx: Context, R: int, d, rec, B: int, grad, loss, weights=(1.0, 1.0, 0.005)):
+    """Query terms and gradient on a caller-owned dense grid; allocates nothing
+    (for callers that may not allocate device memory themselves)."""
+    import torch
+    n1 = R + 1
+    _need(d, torch.float32, n1 ** 3, "values")
+    _need(rec, torch.float32, 6 * B, "records")
+    _need(grad, torch.float32, n1 ** 3, "grad")
+    _need(loss, torch.float32, 8, "loss")
+    w = LossW(*[float(x) for x in weights])
+    ctx.sync_stream()
+    ctx.check(ctx.lib.gp_step_dense_noalloc(ctx.handle, int(R), _ptr(d), _ptr(rec), int(B), ctypes.byref(w),
+                                            _ptr(grad), _ptr(loss)))
