@@ -138,6 +138,26 @@ def test_nn_matches_bruteforce_sphere(gb, ctx, sphere5k):
         assert np.array_equal(nn_h, want)
 
 
+def test_nn_seeded_spatial_batch_full_size(gb, ctx, object100k):
+    """The fitting step's NN configuration at the bench size: 262,144 queries
+    around their source points, in spatial order, each seeded by its source
+    point (the warp-wide search); 4,000 sampled queries checked by brute force."""
+    R = 256
+    band = _band(gb, ctx, object100k, R, 2, 2, knn_k=0)
+    q, j = synth.gaussian_queries(object100k, 262_144, 0.02, seed=21)
+    cell = np.floor((object100k[j].astype(np.float64) + 1) * 64).astype(np.int64)
+    order = np.lexsort((cell[:, 0], cell[:, 1], cell[:, 2]))
+    q, j = q[order], j[order]
+    rng = np.random.default_rng(5)
+    j_hint = j.copy()
+    j_hint[rng.choice(len(j), 500, replace=False)] = -1       # a few unseeded lanes
+    nn, _ = _nn_gpu(gb, band, q, j_hint)
+    sel = rng.choice(len(q), 4000, replace=False)
+    assert np.array_equal(nn[sel], o.nearest_point(q[sel], object100k))
+    nn_plain, _ = _nn_gpu(gb, band, q[sel])                  # per-thread search, no seed
+    assert np.array_equal(nn_plain, nn[sel])
+
+
 def test_nn_counts_valid_records(gb, ctx, sphere5k):
     import torch
     R = 64
