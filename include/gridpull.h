@@ -188,7 +188,7 @@ gp_status gp_band_check(gp_band* band);
 /* --------------------------------------------------------------- sampling */
 
 #define GP_SAMPLE_SPATIAL 1u /* emit the batch grouped by source point, points in
-                                the order of the cloud's cell list            */
+                                Morton order of their cells                   */
 
 /* Queries of the epoch-`epoch` pool of Q queries, pool positions
  * [first, first + count), written to q_dev (count x 3 float32).  Sec. 3: each
@@ -198,8 +198,8 @@ gp_status gp_band_check(gp_band* band);
  * q = s_j + sigma_j * z with z ~ N(0, I) from Philox4x32-10 at counter
  * (k, epoch, 0, 0), key (seed_lo, seed_hi), via Box-Muller.  Without flags the
  * i-th output is position first + i; with GP_SAMPLE_SPATIAL the same set of
- * queries is emitted grouped by source point, points in the cloud's cell-list
- * order (replicas of a point in increasing k): neighbouring outputs are close
+ * queries is emitted grouped by source point, points in Morton order of their
+ * cell-list cells (replicas of a point in increasing k): neighbouring outputs are close
  * in space.  Optional outputs (NULL to skip, count int32 each): src_dev = j
  * (a valid gp_nn hint), pos_dev = k.  Requires knn_k > 0 at build.  Errors:
  * GP_ERR_ARG (Q > 2^31-1, first + count > Q, null q_dev with count > 0),

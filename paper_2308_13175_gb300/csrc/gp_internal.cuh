@@ -83,6 +83,7 @@ struct gp_band {
   int32_t* perm = nullptr;         // J: Pi_e of the cached epoch
   int32_t* inv_perm = nullptr;     // J: Pi_e^-1 (point -> pool slot within a replica)
   int32_t* order_tiles = nullptr;  // per-tile counts / offsets of the spatial batch order
+  int32_t* emit_order = nullptr;   // J: point indices in Morton order of their cell-list cells
   bool perm_valid = false;
   uint64_t perm_seed = 0;
   uint32_t perm_epoch = 0;

@@ -19,7 +19,9 @@
 // query's cell until the distance from q to the scanned box, less a rounding
 // margin of 1e-5 (1 + |q|_inf), exceeds sqrt(b1 (1 + 8 eps)), so no unscanned
 // point can enter the comparison.
+#include <algorithm>
 #include <cmath>
+#include <vector>
 
 #include "gp_internal.cuh"
 
@@ -544,6 +546,48 @@ NNGrid make_grid(const gp_band* b) {
 
 }  // namespace
 
+// Emission order of the spatial batches: point indices sorted by the Morton
+// code of their cell-list cell (ties by index), so that consecutive points, and
+// the queries drawn around them, stay close in all three directions.  Set-up
+// only: the sort runs once per cloud on the host.
+static uint64_t spread3(uint64_t x) {
+  x &= 0x1fffff;
+  x = (x | x << 32) & 0x1f00000000ffffull;
+  x = (x | x << 16) & 0x1f0000ff0000ffull;
+  x = (x | x << 8) & 0x100f00f00f00f00full;
+  x = (x | x << 4) & 0x10c30c30c30c30c3ull;
+  x = (x | x << 2) & 0x1249249249249249ull;
+  return x;
+}
+
+static gp_status build_emit_order(gp_band* b) {
+  gp_ctx* ctx = b->ctx;
+  const int64_t J = b->J;
+  std::vector<float> pts((size_t)(3 * J));
+  GP_CUDA(ctx, cudaMemcpyAsync(pts.data(), b->pts, 3 * J * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+  GP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  const float half_g = 0.5f * (float)b->G;
+  std::vector<uint64_t> key((size_t)J);
+  for (int64_t j = 0; j < J; ++j) {
+    uint64_t c[3];
+    for (int a = 0; a < 3; ++a) {
+      float t = (pts[3 * j + a] + 1.0f) * half_g;
+      int ci = (t < 0.f) ? 0 : (int)std::floor(std::fmin(t, 1.0e6f));
+      c[a] = (uint64_t)std::min(std::max(ci, 0), b->G - 1);
+    }
+    uint64_t m = spread3(c[0]) | (spread3(c[1]) << 1) | (spread3(c[2]) << 2);
+    key[(size_t)j] = (m << 31) | (uint64_t)j;  // Morton code (<= 30 bits), then index
+  }
+  std::sort(key.begin(), key.end());
+  std::vector<int32_t> order((size_t)J);
+  for (int64_t t = 0; t < J; ++t) order[(size_t)t] = (int32_t)(key[(size_t)t] & 0x7fffffffull);
+  gp_status st = gp_alloc(ctx, &b->emit_order, J, "emission order");
+  if (st) return st;
+  GP_CUDA(ctx, cudaMemcpyAsync(b->emit_order, order.data(), J * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
+  GP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return GP_OK;
+}
+
 // Point copy, cell list and sigma (called by gp_build_band).
 gp_status gp_build_points(gp_band* b, const float* pts_dev) {
   gp_ctx* ctx = b->ctx;
@@ -591,6 +635,7 @@ gp_status gp_build_points(gp_band* b, const float* pts_dev) {
     if ((st = gp_alloc(ctx, &b->perm, J, "permutation"))) return st;
     if ((st = gp_alloc(ctx, &b->inv_perm, J, "inverse permutation"))) return st;
     if ((st = gp_alloc(ctx, &b->order_tiles, (J + GP_ORDER_TILE - 1) / GP_ORDER_TILE + 1, "order tiles"))) return st;
+    if ((st = build_emit_order(b))) return st;
     int k = (int)std::min<int64_t>(b->knn_k, J - 1);
     GP_KERNEL(ctx, "k_knn_sigma", k_knn_sigma<<<gp_blocks(J, 128), 128, 0, s>>>(g, J, k, b->sigma));
   }

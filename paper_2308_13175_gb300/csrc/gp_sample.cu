@@ -8,7 +8,7 @@
 // A batch is the pool positions [first, first + count).  In position order the
 // queries of a batch are scattered over the whole surface.  In spatial order
 // (GP_SAMPLE_SPATIAL) the same queries are emitted grouped by their source
-// point, the points taken in the order of the cloud's cell list: position k
+// point, the points taken in Morton order of their cells: position k
 // belongs to point Pi_e(k mod J), so point j owns positions Pi_e^-1(j) + r J,
 // and a three-kernel count / scan / emit pass lists them without a sort.
 // Neighbouring outputs then lie close together, which is what the nearest-point
@@ -112,7 +112,7 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* excl) {
 }
 
 // Pass 1: queries owned by each tile of sorted points.
-__global__ void __launch_bounds__(GP_ORDER_THREADS) k_order_count(const float4* __restrict__ pts_sorted,
+__global__ void __launch_bounds__(GP_ORDER_THREADS) k_order_count(const int32_t* __restrict__ order,
                                                                   const int32_t* __restrict__ inv, int64_t J,
                                                                   int64_t first, int64_t last,
                                                                   int32_t* __restrict__ tiles) {
@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(GP_ORDER_THREADS) k_order_count(const float4* 
   for (int u = 0; u < GP_ORDER_PER_THREAD; ++u) {
     int64_t t = base + u;
     if (t < J) {
-      int j = __float_as_int(pts_sorted[t].w);
+      int j = order[t];
       int64_t r0;
       int n;
       owned_range(inv[j], J, first, last, r0, n);
@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(GP_ORDER_THREADS) k_order_tiles(int32_t* __res
 
 // Pass 3: every sorted point writes its queries at its offset.
 __global__ void __launch_bounds__(GP_ORDER_THREADS) k_order_emit(
-    const float4* __restrict__ pts_sorted, const int32_t* __restrict__ inv, const float* __restrict__ pts,
+    const int32_t* __restrict__ order, const int32_t* __restrict__ inv, const float* __restrict__ pts,
     const float* __restrict__ sigma, int64_t J, int64_t first, int64_t last, const int32_t* __restrict__ tiles,
     uint32_t epoch, uint32_t k0, uint32_t k1, float* __restrict__ q, int32_t* __restrict__ src,
     int32_t* __restrict__ pos, int32_t* __restrict__ err) {
@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(GP_ORDER_THREADS) k_order_emit(
     pp[u] = 0;
     rr[u] = 0;
     if (t < J) {
-      jj[u] = __float_as_int(pts_sorted[t].w);
+      jj[u] = order[t];
       pp[u] = inv[jj[u]];
       owned_range(pp[u], J, first, last, rr[u], nn[u]);
       c += nn[u];
@@ -226,12 +226,12 @@ extern "C" gp_status gp_sample(gp_band* b, uint64_t seed, uint32_t epoch, int64_
   const int64_t J = b->J, last = first + count;
   const int64_t ntiles = (J + GP_ORDER_TILE - 1) / GP_ORDER_TILE;
   GP_KERNEL(ctx, "k_order_count",
-            k_order_count<<<(unsigned)ntiles, GP_ORDER_THREADS, 0, ctx->stream>>>(b->pts_sorted, b->inv_perm, J,
+            k_order_count<<<(unsigned)ntiles, GP_ORDER_THREADS, 0, ctx->stream>>>(b->emit_order, b->inv_perm, J,
                                                                                  first, last, b->order_tiles));
   GP_KERNEL(ctx, "k_order_tiles", k_order_tiles<<<1, GP_ORDER_THREADS, 0, ctx->stream>>>(b->order_tiles, ntiles));
   GP_KERNEL(ctx, "k_order_emit",
             k_order_emit<<<(unsigned)ntiles, GP_ORDER_THREADS, 0, ctx->stream>>>(
-                b->pts_sorted, b->inv_perm, b->pts, b->sigma, J, first, last, b->order_tiles, epoch, k0, k1, q_dev,
+                b->emit_order, b->inv_perm, b->pts, b->sigma, J, first, last, b->order_tiles, epoch, k0, k1, q_dev,
                 src_dev, pos_dev, b->dev_ints + GP_DI_ERROR));
   return GP_OK;
 }
