@@ -409,131 +409,6 @@ __global__ void __launch_bounds__(256) k_nn(NNGrid g, const float* __restrict__ 
   nn_finish(i, q, best, pts_orig, nn_out, rec, band, nvalid);
 }
 
-__device__ __forceinline__ int warp_min_i(int v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
-}
-
-__device__ __forceinline__ int warp_max_i(int v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
-}
-
-// Largest union of the 32 lanes' search boxes (in cells) scanned warp-wide;
-// beyond it every lane searches on its own.
-constexpr int64_t NN_UNION_CAP = 8192;
-
-// One warp per 32 consecutive queries, each seeded by a known point.  The lanes'
-// balls (radius from the seed) are covered by the union of their boxes of
-// cells; the warp walks that union row by row, in lockstep, with the row's
-// point range loaded once for all lanes (broadcast loads), and every lane keeps
-// its own best, runner-up and pruning radius.  A row is read only if some lane
-// still needs it, over the union of the x-ranges those lanes need.  Every point
-// within a lane's radius lies in a row of the union, so each lane's result is
-// the one its own search would find.  Queries given in spatial order keep the
-// union small; lanes without a usable seed, and warps whose union exceeds
-// NN_UNION_CAP cells, fall back to the per-thread search.
-__global__ void __launch_bounds__(256) k_nn_warp(NNGrid g, const float* __restrict__ qin, int64_t n,
-                                                 const int32_t* __restrict__ hint, int64_t J,
-                                                 const float* __restrict__ pts_orig, int32_t* __restrict__ nn_out,
-                                                 float* __restrict__ rec, Grid band, int32_t* __restrict__ nvalid) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const bool active = i < n;
-  float q[3] = {0.f, 0.f, 0.f};
-  if (active) {
-    q[0] = qin[3 * i];
-    q[1] = qin[3 * i + 1];
-    q[2] = qin[3 * i + 2];
-  }
-  const bool ok = active && nn_query_ok(q);
-  int c[3] = {0, 0, 0};
-  float margin = 0.f;
-  NNState st{INFINITY, INFINITY, INFINITY, 0x7fffffff};
-  if (ok) {
-    c[0] = nn_cell(q[0], g);
-    c[1] = nn_cell(q[1], g);
-    c[2] = nn_cell(q[2], g);
-    margin = nn_margin(q);
-    nn_seed(st, q, hint, i, J, pts_orig);
-  }
-  const bool seeded = ok && st.b1 < INFINITY;
-  int lo[3] = {0x7fffffff, 0x7fffffff, 0x7fffffff}, hi[3] = {-1, -1, -1};
-  float rad0 = 0.f;
-  if (seeded) {
-    rad0 = sqrtf(st.thr) * 1.000001f + margin;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      lo[a] = nn_cell(q[a] - rad0, g);
-      hi[a] = nn_cell(q[a] + rad0, g);
-    }
-  }
-  int ulo[3], uhi[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    ulo[a] = warp_min_i(lo[a]);
-    uhi[a] = warp_max_i(hi[a]);
-  }
-  const bool any_seeded = __any_sync(0xffffffffu, seeded);
-  int64_t vol = 0;
-  if (any_seeded)
-    vol = (int64_t)(uhi[0] - ulo[0] + 1) * (int64_t)(uhi[1] - ulo[1] + 1) * (int64_t)(uhi[2] - ulo[2] + 1);
-  const bool warp_mode = any_seeded && vol <= NN_UNION_CAP;
-  if (warp_mode) {
-    const int G = g.G;
-    for (int cz = ulo[2]; cz <= uhi[2]; ++cz) {
-      float lz = seeded ? nn_axis_gap(q[2], cz, g, margin) : 0.f;
-      float lz2 = lz * lz;
-      for (int cy = ulo[1]; cy <= uhi[1]; ++cy) {
-        bool need = false;
-        int xa = 0x7fffffff, xb = -1;
-        if (seeded) {
-          float ly = nn_axis_gap(q[1], cy, g, margin);
-          float lyz2 = fmaf(ly, ly, lz2);
-          if (lyz2 <= st.thr) {
-            need = true;
-            float rad = sqrtf(st.thr - lyz2) * 1.000001f + margin;
-            xa = nn_cell(q[0] - rad, g);
-            xb = nn_cell(q[0] + rad, g);
-          }
-        }
-        if (!__any_sync(0xffffffffu, need)) continue;
-        xa = warp_min_i(xa);
-        xb = warp_max_i(xb);
-        const int64_t row = ((int64_t)cz * G + cy) * G;
-        const int a = __ldg(g.start + row + xa), b = __ldg(g.start + row + xb + 1);
-        int p = a;
-        for (; p + 4 <= b; p += 4) {
-          float4 P[4] = {__ldg(g.pts + p), __ldg(g.pts + p + 1), __ldg(g.pts + p + 2), __ldg(g.pts + p + 3)};
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            float dx = q[0] - P[u].x, dy = q[1] - P[u].y, dz = q[2] - P[u].z;
-            float d = dx * dx + dy * dy + dz * dz;
-            if (seeded) nn_update(st, d, __float_as_int(P[u].w));
-          }
-        }
-        for (; p < b; ++p) {
-          float4 P = __ldg(g.pts + p);
-          float dx = q[0] - P.x, dy = q[1] - P.y, dz = q[2] - P.z;
-          float d = dx * dx + dy * dy + dz * dz;
-          if (seeded) nn_update(st, d, __float_as_int(P.w));
-        }
-      }
-    }
-  }
-  int best = -1;
-  if (ok) {
-    if (warp_mode && seeded) {
-      const int r_end = (int)(rad0 / g.cs) + 2;
-      best = nn_break_tie(q, c, g, margin, st, r_end);
-    } else {
-      best = nn_thread_search(q, c, g, margin, st);
-    }
-  }
-  if (active) nn_finish(i, q, best, pts_orig, nn_out, rec, band, nvalid);
-}
-
 NNGrid make_grid(const gp_band* b) {
   NNGrid g;
   g.pts = b->pts_sorted;
@@ -667,12 +542,7 @@ extern "C" gp_status gp_nn(gp_band* b, const float* q_dev, int64_t n, const int3
   band.nb = b->nb;
   band.R = b->R;
   band.half_r = 0.5f * (float)b->R;
-  if (hint_dev)
-    GP_KERNEL(ctx, "k_nn_warp",
-              k_nn_warp<<<gp_blocks(n, 256), 256, 0, ctx->stream>>>(g, q_dev, n, hint_dev, b->J, b->pts, nn_dev,
-                                                                    rec_dev, band, nvalid_dev));
-  else
-    GP_KERNEL(ctx, "k_nn", k_nn<<<gp_blocks(n, 256), 256, 0, ctx->stream>>>(g, q_dev, n, hint_dev, b->J, b->pts,
-                                                                             nn_dev, rec_dev, band, nvalid_dev));
+  GP_KERNEL(ctx, "k_nn", k_nn<<<gp_blocks(n, 256), 256, 0, ctx->stream>>>(g, q_dev, n, hint_dev, b->J, b->pts,
+                                                                           nn_dev, rec_dev, band, nvalid_dev));
   return GP_OK;
 }

@@ -141,7 +141,7 @@ def test_nn_matches_bruteforce_sphere(gb, ctx, sphere5k):
 def test_nn_seeded_spatial_batch_full_size(gb, ctx, object100k):
     """The fitting step's NN configuration at the bench size: 262,144 queries
     around their source points, in spatial order, each seeded by its source
-    point (the warp-wide search); 4,000 sampled queries checked by brute force."""
+    point; 4,000 sampled queries checked by brute force."""
     R = 256
     band = _band(gb, ctx, object100k, R, 2, 2, knn_k=0)
     q, j = synth.gaussian_queries(object100k, 262_144, 0.02, seed=21)
@@ -150,7 +150,7 @@ def test_nn_seeded_spatial_batch_full_size(gb, ctx, object100k):
     q, j = q[order], j[order]
     rng = np.random.default_rng(5)
     j_hint = j.copy()
-    j_hint[rng.choice(len(j), 500, replace=False)] = -1       # a few unseeded lanes
+    j_hint[rng.choice(len(j), 500, replace=False)] = -1       # a few unseeded queries
     nn, _ = _nn_gpu(gb, band, q, j_hint)
     sel = rng.choice(len(q), 4000, replace=False)
     assert np.array_equal(nn[sel], o.nearest_point(q[sel], object100k))
