@@ -346,6 +346,43 @@ def run_ours(args, world, rank, local):
     e2e_value = reduce_sum(float(K * B), world) / (e2e_ms / 1e3)
     loss_final = float(hloss[K - 1][gb.GP_LOSS_TOTAL])
 
+    # Plain PyTorch autograd on the same GPU and the same records: Eq. 8 in torch
+    # ops (index gathers), loss.backward(), torch.optim.Adam with the frozen
+    # vertices masked; beside it our gp_step + gp_update on those records.
+    torch_cmp = None
+    if not args.no_torch:
+        from paper_2308_13175_gb300.torch_reference import from_band
+        ts = from_band(band, device="cuda", dtype=torch.float32)
+        Dt = gb.gp_band_values(band)[0].clone().requires_grad_(True)
+        opt = torch.optim.Adam([Dt], lr=wl["lr"])
+        rec = fit.rec.clone()
+        nv = fit.nvalid.clone()
+        for _ in range(3):
+            ts.step(Dt, opt, rec, PAPER_WEIGHTS)
+        Kt = max(3, min(args.steps, 10))
+        t_ms, o_ms = [], []
+        for k in range(Kt):
+            flush.fill_(float(k))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ts.step(Dt, opt, rec, PAPER_WEIGHTS)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t_ms.append(e0.elapsed_time(e1))
+            flush.fill_(float(k))
+            e0.record(stream)
+            gb.gp_step(band, rec, B, fit.grad, fit.loss, PAPER_WEIGHTS, nvalid=nv)
+            gb.gp_update(band, fit.grad, wl["lr"], step_t + K + k + 1)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            o_ms.append(e0.elapsed_time(e1))
+        tq = B / (float(np.median(t_ms)) / 1e3)
+        oq = B / (float(np.median(o_ms)) / 1e3)
+        torch_cmp = {"value": tq, "unit": UNIT, "scope": f"loss + backward + Adam over the same {B} step records",
+                     "ours_same_scope": oq, "speedup_same_scope": oq / tq, "speedup_full_step": value / tq,
+                     "torch_ms": float(np.median(t_ms)), "ours_ms": float(np.median(o_ms))}
+        del ts, Dt, opt
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, cinfo = oracle_rate(pts, wl, args.cpu_sample)
@@ -362,7 +399,7 @@ def run_ours(args, world, rank, local):
                           "V_stored": Vs, "V_trainable": Vt, "V_tv": info["V_tv"], "J": J},
                "roofline": roofline, "cpu_baseline": cpu,
                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 12 * B, "d2h_bytes_per_step": 32},
-               "gpu_launches": int(launches), "clocks": clk, "kernels": per_kernel,
+               "gpu_launches": int(launches), "clocks": clk, "kernels": per_kernel, "torch_autograd": torch_cmp,
                "loss_last": loss_final}
         print(json.dumps(out), flush=True)
     gb.gp_band_check(band)
@@ -378,6 +415,7 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=4096)
     ap.add_argument("--ref-sample", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-torch", action="store_true", help="skip the plain PyTorch autograd comparison")
     ap.add_argument("--nn-grid", type=int, default=0, help="cells per axis of the point cell list (0 = automatic)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":

@@ -8,7 +8,7 @@ device memory and the stream); ``fit`` strings the calls into a fitting step.
 The library is built with ``build.build()``; nothing here falls back to a CPU
 path when it is missing.
 """
-__all__ = ["binding", "build", "fit", "synth"]
+__all__ = ["autograd", "binding", "build", "fit", "synth", "torch_reference"]
 
 
 def __getattr__(name):

@@ -383,3 +383,34 @@ def test_sphere_init_formula():
     d1 = o.sphere_init(keys, R, (0.1, 0, 0), 0.25, 0.1, 3)
     z = (d1 - d0) / 0.1
     assert abs(z.mean()) < 0.05 and abs(z.std() - 1) < 0.05
+
+
+# -------------------------------------------- plain torch autograd (FP64)
+@pytest.mark.parametrize("M", [1, -1])
+def test_oracle_matches_plain_torch_autograd(M):
+    """Eq. 8 written with torch ops and differentiated by autograd agrees with
+    the oracle's Eq. 3 solve and explicit adjoints."""
+    import torch
+    from paper_2308_13175_gb300.torch_reference import TorchStep
+    R = 16
+    pts = synth.sphere_cloud(300, 0.45, seed=2)
+    sets = o.band_sets(pts, R, M, M)
+    n = (R + 1) ** 3
+    keys = np.arange(n)
+    D = synth.sphere_field(synth.all_vertices(R), R, 0.45, 0.05, seed=3).astype(np.float64)
+    q, j = synth.gaussian_queries(pts, 2000, 0.08, seed=4)
+    s = pts[j]
+    w = (1.5, 0.7, 0.2)
+    ref = o.step_loss_grad(D, R, sets, q, s, w)
+    pull = np.zeros(R ** 3, bool)
+    pull[sets["pull_cells"]] = True
+    ts = TorchStep(R, keys, np.isin(keys, sets["tv"]), np.isin(keys, sets["trainable"]), pull)
+    Dt = torch.tensor(D, requires_grad=True)
+    rec = torch.from_numpy(np.concatenate([q, s], axis=1))
+    L, parts = ts.loss(Dt, rec, w)
+    L.backward()
+    assert parts["Bv"] == ref["Bv"]
+    for k in ("l_pull", "l_grad", "l_surf", "l_tv", "loss"):
+        assert abs(float(parts[k]) - ref[k]) <= 1e-12 * max(1.0, abs(ref[k])), k
+    g = Dt.grad.numpy()
+    assert np.max(np.abs(g - ref["grad"])) <= 1e-11 * np.max(np.abs(ref["grad"]))
