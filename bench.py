@@ -93,7 +93,7 @@ class ClockSampler:
         try:
             self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=self.file, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -219,9 +219,16 @@ def run_reference(args, world, rank):
         return
     wl = WORKLOADS[args.workload]
     pts = wl["cloud"]()
-    sample_q = args.ref_sample
     t_start = time.perf_counter()
-    oracle_rate(pts, wl, sample_q, repeats=max(1, args.warmup))
+    # Size each step's sample so that the W + K steps take about 150 s of CPU.
+    _, cal = oracle_rate(pts, wl, 256, repeats=1)
+    budget = 150.0 / max(1, args.steps + args.warmup)
+    per_q = cal["t_query_s"] / 256
+    sample_q = int(min(8192, max(64, (budget - cal["t_vertex_s"]) / max(per_q, 1e-9))))
+    if args.ref_sample > 0:
+        sample_q = args.ref_sample
+    if args.warmup > 1:
+        oracle_rate(pts, wl, sample_q, repeats=args.warmup - 1)
     rate, info = oracle_rate(pts, wl, sample_q, repeats=max(1, args.steps))
     elapsed = time.perf_counter() - t_start
     sample = (f"each step: sampler + brute-force NN + query terms for {sample_q} queries and the full vertex "
@@ -318,11 +325,12 @@ def run_ours(args, world, rank, local):
     # NN + step + update, loss back to the host, every step.
     B = wl["B"]
     K = args.steps
+    NH = min(K, 8)  # distinct host batches, reused in turn
     rng = np.random.default_rng(rank + 7)
-    jj = rng.integers(0, len(pts), size=(K, B))
+    jj = rng.integers(0, len(pts), size=(NH, B))
     sig = gb.gp_band_sigma(band).cpu().numpy()
-    hq = torch.empty((K, B, 3), dtype=torch.float32).pin_memory()
-    hq.copy_(torch.from_numpy((pts[jj] + sig[jj][..., None] * rng.normal(size=(K, B, 3))).astype(np.float32)))
+    hq = torch.empty((NH, B, 3), dtype=torch.float32).pin_memory()
+    hq.copy_(torch.from_numpy((pts[jj] + sig[jj][..., None] * rng.normal(size=(NH, B, 3))).astype(np.float32)))
     hloss = torch.empty((K, 8), dtype=torch.float32).pin_memory()
     dq = torch.empty((B, 3), dtype=torch.float32, device="cuda")
     barrier(world)
@@ -334,7 +342,7 @@ def run_ours(args, world, rank, local):
     for k in range(K):
         flush.fill_(float(k))
         e_start.record(stream)
-        dq.copy_(hq[k], non_blocking=True)
+        dq.copy_(hq[k % NH], non_blocking=True)
         gb.gp_nn(band, dq, None, fit.rec, nvalid_out=fit.nvalid)
         gb.gp_step(band, fit.rec, B, fit.grad, fit.loss, PAPER_WEIGHTS, nvalid=fit.nvalid)
         gb.gp_update(band, fit.grad, wl["lr"], step_t + k + 1)
@@ -408,12 +416,12 @@ def run_ours(args, world, rank, local):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="object", choices=sorted(WORKLOADS))
     ap.add_argument("--cpu-sample", type=int, default=4096)
-    ap.add_argument("--ref-sample", type=int, default=1024)
+    ap.add_argument("--ref-sample", type=int, default=0, help="queries per oracle step (0 = sized to ~150 s total)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-torch", action="store_true", help="skip the plain PyTorch autograd comparison")
     ap.add_argument("--nn-grid", type=int, default=0, help="cells per axis of the point cell list (0 = automatic)")

@@ -78,13 +78,15 @@ def test_function_matches_finite_differences(setup):
     import torch
     from paper_2308_13175_gb300.autograd import gridpull_loss
     gb, ctx, band, R, vals, rec, pts, q, j = setup
-    w = (1.0, 1.0, 0.005)
+    # beta = 0: |f(s)| has a kink at f(s) = 0 that a finite step straddles; its
+    # gradient is checked against the oracle and the autograd form instead.
+    w = (1.0, 0.0, 0.005)
     rec = rec[:2000].contiguous()  # few records: gradients well above the float32 noise of L
     D = torch.from_numpy(vals).cuda().requires_grad_(True)
     gridpull_loss(D, band, rec, weights=w).backward()
     g = D.grad.cpu().numpy().astype(np.float64)
     top = np.argsort(-np.abs(g))[:12]
-    eps = 5e-3
+    eps = 1e-3
     for k in top:
         dp = vals.copy()
         dm = vals.copy()
