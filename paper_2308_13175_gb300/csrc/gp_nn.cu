@@ -309,9 +309,61 @@ __device__ __forceinline__ void nn_seed(NNState& st, const float q[3], const int
   }
 }
 
+// Seeded search (thr finite from the start): walk the slabs (fixed z) and, in
+// each, the rows (fixed y) closest first, alternating sides, each clipped to
+// the cells within the current radius; a side stops at its first slab or row
+// whose lower bound exceeds thr, since bounds only grow outwards and thr only
+// shrinks.  Every point with squared distance <= the final thr lies in a row
+// that was visited, within the x-range read.
+template <typename F>
+__device__ __forceinline__ void nn_ball_walk(const float q[3], const int c[3], const NNGrid& g, float margin,
+                                             const float& thr, F&& visit) {
+  const int G = g.G;
+  bool z_done[2] = {false, false};
+  for (int kz = 0; !(z_done[0] && z_done[1]); ++kz) {
+#pragma unroll
+    for (int sz = 0; sz < 2; ++sz) {
+      if (z_done[sz] || (kz == 0 && sz == 1)) continue;
+      const int cz = c[2] + (sz ? -kz : kz);
+      if (cz < 0 || cz >= G) {
+        z_done[sz] = true;
+        continue;
+      }
+      const float lz = nn_axis_gap(q[2], cz, g, margin);
+      const float lz2 = lz * lz;
+      if (lz2 > thr) {
+        z_done[sz] = true;
+        continue;
+      }
+      bool y_done[2] = {false, false};
+      for (int ky = 0; !(y_done[0] && y_done[1]); ++ky) {
+#pragma unroll
+        for (int sy = 0; sy < 2; ++sy) {
+          if (y_done[sy] || (ky == 0 && sy == 1)) continue;
+          const int cy = c[1] + (sy ? -ky : ky);
+          if (cy < 0 || cy >= G) {
+            y_done[sy] = true;
+            continue;
+          }
+          const float ly = nn_axis_gap(q[1], cy, g, margin);
+          const float lyz2 = fmaf(ly, ly, lz2);
+          if (lyz2 > thr) {
+            y_done[sy] = true;
+            continue;
+          }
+          const float rad = sqrtf(thr - lyz2) * 1.000001f + margin;
+          const int xa = nn_cell(q[0] - rad, g), xb = nn_cell(q[0] + rad, g);
+          const int64_t row = ((int64_t)cz * G + cy) * G;
+          visit(__ldg(g.start + row + xa), __ldg(g.start + row + xb + 1));
+        }
+      }
+    }
+  }
+}
+
 // Near tie (another point within the float32 margin of the best): rank every
 // point within the margin by its float64 distance and index.  Rings 0..r_end
-// cover every row within the pruning radius.
+// (or, for r_end < 0, the ball walk) cover every row within the pruning radius.
 __device__ __forceinline__ int nn_break_tie(const float q[3], const int c[3], const NNGrid& g, float margin,
                                             const NNState& st, int r_end) {
   const float tie = st.b1 * (1.0f + 2.0f * NN_EPS) + NN_TINY;
@@ -333,7 +385,10 @@ __device__ __forceinline__ int nn_break_tie(const float q[3], const int c[3], co
       }
     }
   };
-  for (int r = 0; r <= r_end; ++r) nn_row_ring(q, c, r, g, margin, thr, rank);
+  if (r_end < 0)
+    nn_ball_walk(q, c, g, margin, thr, rank);
+  else
+    for (int r = 0; r <= r_end; ++r) nn_row_ring(q, c, r, g, margin, thr, rank);
   return bj != 0x7fffffff ? bj : st.j1;
 }
 
@@ -357,7 +412,11 @@ __device__ __forceinline__ int nn_thread_search(const float q[3], const int c[3]
     }
     for (; p < b; ++p) one(__ldg(g.pts + p));
   };
-  const int r_end = nn_ball_scan(q, c, g, margin, st.thr, st.b1, scan);
+  int r_end = -1;
+  if (st.b1 < INFINITY)
+    nn_ball_walk(q, c, g, margin, st.thr, scan);  // seeded: closest-first walk of the ball
+  else
+    r_end = nn_ball_scan(q, c, g, margin, st.thr, st.b1, scan);
   if (st.j1 == 0x7fffffff) return -1;
   return nn_break_tie(q, c, g, margin, st, r_end);
 }
