@@ -361,6 +361,84 @@ __device__ __forceinline__ void nn_ball_walk(const float q[3], const int c[3], c
   }
 }
 
+// The same ball walk for the seeded lanes of a warp, run in lockstep: every
+// lane goes through the same slab / row / point loop trips (the warp's maxima),
+// doing its own work where it still has some and idling where it has none.  A
+// divergent walk would serialise the lanes' chains of dependent loads; in
+// lockstep each load instruction carries all the lanes that need one.  Must be
+// called by all 32 lanes; lanes with part == false only keep the others company.
+__device__ __forceinline__ void nn_walk_warp(const float q[3], const int c[3], const NNGrid& g, float margin,
+                                             NNState& st, bool part) {
+  const unsigned FULL = 0xffffffffu;
+  const int G = g.G;
+  bool zd[2] = {!part, !part};
+  for (int kz = 0; __any_sync(FULL, !(zd[0] && zd[1])); ++kz) {
+#pragma unroll
+    for (int sz = 0; sz < 2; ++sz) {
+      bool on = false;
+      int cz = 0;
+      float lz2 = 0.f;
+      if (!zd[sz]) {
+        if (kz == 0 && sz == 1) {
+          // offset 0 is visited once, as the positive side
+        } else {
+          cz = c[2] + (sz ? -kz : kz);
+          if (cz < 0 || cz >= G) {
+            zd[sz] = true;
+          } else {
+            const float lz = nn_axis_gap(q[2], cz, g, margin);
+            lz2 = lz * lz;
+            if (lz2 > st.thr)
+              zd[sz] = true;
+            else
+              on = true;
+          }
+        }
+      }
+      if (!__any_sync(FULL, on)) continue;
+      bool yd[2] = {!on, !on};
+      for (int ky = 0; __any_sync(FULL, !(yd[0] && yd[1])); ++ky) {
+#pragma unroll
+        for (int sy = 0; sy < 2; ++sy) {
+          int a = 0, b = 0;
+          if (!yd[sy] && !(ky == 0 && sy == 1)) {
+            const int cy = c[1] + (sy ? -ky : ky);
+            if (cy < 0 || cy >= G) {
+              yd[sy] = true;
+            } else {
+              const float ly = nn_axis_gap(q[1], cy, g, margin);
+              const float lyz2 = fmaf(ly, ly, lz2);
+              if (lyz2 > st.thr) {
+                yd[sy] = true;
+              } else {
+                const float rad = sqrtf(st.thr - lyz2) * 1.000001f + margin;
+                const int xa = nn_cell(q[0] - rad, g), xb = nn_cell(q[0] + rad, g);
+                const int64_t row = ((int64_t)cz * G + cy) * G;
+                a = __ldg(g.start + row + xa);
+                b = __ldg(g.start + row + xb + 1);
+              }
+            }
+          }
+          const int lmax = (int)__reduce_max_sync(FULL, (unsigned)(b - a));
+          for (int t = 0; t < lmax; t += 4) {
+            float4 P[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+              P[u] = (a + t + u < b) ? __ldg(g.pts + a + t + u) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              if (a + t + u < b) {
+                const float dx = q[0] - P[u].x, dy = q[1] - P[u].y, dz = q[2] - P[u].z;
+                nn_update(st, dx * dx + dy * dy + dz * dz, __float_as_int(P[u].w));
+              }
+            }
+          }
+        }
+      }
+    }
+  }
+}
+
 // Near tie (another point within the float32 margin of the best): rank every
 // point within the margin by its float64 distance and index.  Rings 0..r_end
 // (or, for r_end < 0, the ball walk) cover every row within the pruning radius.
@@ -451,21 +529,39 @@ __device__ __forceinline__ bool nn_query_ok(const float q[3]) {
 
 // One thread per query.  Queries with a NaN, infinite or huge coordinate (whose
 // squared distances would overflow float32) get -1 and a NaN surface point.
+// Seeded queries walk their ball in warp lockstep; the others search alone.
 __global__ void __launch_bounds__(256) k_nn(NNGrid g, const float* __restrict__ qin, int64_t n,
                                             const int32_t* __restrict__ hint, int64_t J,
                                             const float* __restrict__ pts_orig, int32_t* __restrict__ nn_out,
                                             float* __restrict__ rec, Grid band, int32_t* __restrict__ nvalid) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  float q[3] = {qin[3 * i], qin[3 * i + 1], qin[3 * i + 2]};
-  int best = -1;
-  if (nn_query_ok(q)) {
-    int c[3] = {nn_cell(q[0], g), nn_cell(q[1], g), nn_cell(q[2], g)};
-    NNState st{INFINITY, INFINITY, INFINITY, 0x7fffffff};
-    nn_seed(st, q, hint, i, J, pts_orig);
-    best = nn_thread_search(q, c, g, nn_margin(q), st);
+  // All lanes stay until the lockstep walk is over (tail lanes just idle).
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool active = i < n;
+  float q[3] = {0.f, 0.f, 0.f};
+  if (active) {
+    q[0] = qin[3 * i];
+    q[1] = qin[3 * i + 1];
+    q[2] = qin[3 * i + 2];
   }
-  nn_finish(i, q, best, pts_orig, nn_out, rec, band, nvalid);
+  const bool ok = active && nn_query_ok(q);
+  int c[3] = {0, 0, 0};
+  float margin = 0.f;
+  NNState st{INFINITY, INFINITY, INFINITY, 0x7fffffff};
+  if (ok) {
+    c[0] = nn_cell(q[0], g);
+    c[1] = nn_cell(q[1], g);
+    c[2] = nn_cell(q[2], g);
+    margin = nn_margin(q);
+    nn_seed(st, q, hint, i, J, pts_orig);
+  }
+  const bool seeded = ok && st.b1 < INFINITY;
+  if (__any_sync(0xffffffffu, seeded)) nn_walk_warp(q, c, g, margin, st, seeded);
+  int best = -1;
+  if (seeded)
+    best = nn_break_tie(q, c, g, margin, st, -1);
+  else if (ok)
+    best = nn_thread_search(q, c, g, margin, st);
+  if (active) nn_finish(i, q, best, pts_orig, nn_out, rec, band, nvalid);
 }
 
 NNGrid make_grid(const gp_band* b) {
