@@ -246,6 +246,7 @@ void band_free(gp_band* b) {
   gp_free(b->pts_sorted);
   gp_free(b->cell_start);
   gp_free(b->sigma);
+  gp_free(b->normals);
   gp_free(b->perm);
   gp_free(b->inv_perm);
   gp_free(b->order_tiles);

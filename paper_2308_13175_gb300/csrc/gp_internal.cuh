@@ -80,6 +80,7 @@ struct gp_band {
   float4* pts_sorted = nullptr;    // J: x, y, z, original index (int bits)
   int32_t* cell_start = nullptr;   // G^3 + 1
   float* sigma = nullptr;          // J
+  float* normals = nullptr;        // J x 3: unit normal estimate (PCA of the sigma-ball), seeds gp_nn
   int32_t* perm = nullptr;         // J: Pi_e of the cached epoch
   int32_t* inv_perm = nullptr;     // J: Pi_e^-1 (point -> pool slot within a replica)
   int32_t* order_tiles = nullptr;  // per-tile counts / offsets of the spatial batch order

@@ -361,84 +361,6 @@ __device__ __forceinline__ void nn_ball_walk(const float q[3], const int c[3], c
   }
 }
 
-// The same ball walk for the seeded lanes of a warp, run in lockstep: every
-// lane goes through the same slab / row / point loop trips (the warp's maxima),
-// doing its own work where it still has some and idling where it has none.  A
-// divergent walk would serialise the lanes' chains of dependent loads; in
-// lockstep each load instruction carries all the lanes that need one.  Must be
-// called by all 32 lanes; lanes with part == false only keep the others company.
-__device__ __forceinline__ void nn_walk_warp(const float q[3], const int c[3], const NNGrid& g, float margin,
-                                             NNState& st, bool part) {
-  const unsigned FULL = 0xffffffffu;
-  const int G = g.G;
-  bool zd[2] = {!part, !part};
-  for (int kz = 0; __any_sync(FULL, !(zd[0] && zd[1])); ++kz) {
-#pragma unroll
-    for (int sz = 0; sz < 2; ++sz) {
-      bool on = false;
-      int cz = 0;
-      float lz2 = 0.f;
-      if (!zd[sz]) {
-        if (kz == 0 && sz == 1) {
-          // offset 0 is visited once, as the positive side
-        } else {
-          cz = c[2] + (sz ? -kz : kz);
-          if (cz < 0 || cz >= G) {
-            zd[sz] = true;
-          } else {
-            const float lz = nn_axis_gap(q[2], cz, g, margin);
-            lz2 = lz * lz;
-            if (lz2 > st.thr)
-              zd[sz] = true;
-            else
-              on = true;
-          }
-        }
-      }
-      if (!__any_sync(FULL, on)) continue;
-      bool yd[2] = {!on, !on};
-      for (int ky = 0; __any_sync(FULL, !(yd[0] && yd[1])); ++ky) {
-#pragma unroll
-        for (int sy = 0; sy < 2; ++sy) {
-          int a = 0, b = 0;
-          if (!yd[sy] && !(ky == 0 && sy == 1)) {
-            const int cy = c[1] + (sy ? -ky : ky);
-            if (cy < 0 || cy >= G) {
-              yd[sy] = true;
-            } else {
-              const float ly = nn_axis_gap(q[1], cy, g, margin);
-              const float lyz2 = fmaf(ly, ly, lz2);
-              if (lyz2 > st.thr) {
-                yd[sy] = true;
-              } else {
-                const float rad = sqrtf(st.thr - lyz2) * 1.000001f + margin;
-                const int xa = nn_cell(q[0] - rad, g), xb = nn_cell(q[0] + rad, g);
-                const int64_t row = ((int64_t)cz * G + cy) * G;
-                a = __ldg(g.start + row + xa);
-                b = __ldg(g.start + row + xb + 1);
-              }
-            }
-          }
-          const int lmax = (int)__reduce_max_sync(FULL, (unsigned)(b - a));
-          for (int t = 0; t < lmax; t += 4) {
-            float4 P[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-              P[u] = (a + t + u < b) ? __ldg(g.pts + a + t + u) : make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              if (a + t + u < b) {
-                const float dx = q[0] - P[u].x, dy = q[1] - P[u].y, dz = q[2] - P[u].z;
-                nn_update(st, dx * dx + dy * dy + dz * dz, __float_as_int(P[u].w));
-              }
-            }
-          }
-        }
-      }
-    }
-  }
-}
-
 // Near tie (another point within the float32 margin of the best): rank every
 // point within the margin by its float64 distance and index.  Rings 0..r_end
 // (or, for r_end < 0, the ball walk) cover every row within the pruning radius.
@@ -529,12 +451,125 @@ __device__ __forceinline__ bool nn_query_ok(const float q[3]) {
 
 // One thread per query.  Queries with a NaN, infinite or huge coordinate (whose
 // squared distances would overflow float32) get -1 and a NaN surface point.
-// Seeded queries walk their ball in warp lockstep; the others search alone.
+// Smallest-eigenvalue eigenvector of a symmetric 3x3 matrix (Smith, "Eigenvalues
+// of a symmetric 3x3 matrix", CACM 1961: the characteristic cubic solved by
+// trigonometry), then a null vector of A - l I from the largest cross product
+// of its rows.  Returns false when the matrix is (nearly) isotropic.
+__device__ bool smallest_eigvec(const double A[6], double v[3]) {
+  // A = [a00 a01 a02; . a11 a12; . . a22] packed as a00, a01, a02, a11, a12, a22
+  const double a00 = A[0], a01 = A[1], a02 = A[2], a11 = A[3], a12 = A[4], a22 = A[5];
+  const double p1 = a01 * a01 + a02 * a02 + a12 * a12;
+  const double qm = (a00 + a11 + a22) / 3.0;
+  const double p2 = (a00 - qm) * (a00 - qm) + (a11 - qm) * (a11 - qm) + (a22 - qm) * (a22 - qm) + 2.0 * p1;
+  if (!(p2 > 1e-300)) return false;
+  const double p = sqrt(p2 / 6.0);
+  const double b00 = (a00 - qm) / p, b11 = (a11 - qm) / p, b22 = (a22 - qm) / p;
+  const double b01 = a01 / p, b02 = a02 / p, b12 = a12 / p;
+  double r = 0.5 * (b00 * (b11 * b22 - b12 * b12) - b01 * (b01 * b22 - b12 * b02) + b02 * (b01 * b12 - b11 * b02));
+  r = fmin(1.0, fmax(-1.0, r));
+  const double phi = acos(r) / 3.0;
+  const double lmin = qm + 2.0 * p * cos(phi + 2.0943951023931954923);  // + 2 pi / 3
+  const double r0[3] = {a00 - lmin, a01, a02}, r1[3] = {a01, a11 - lmin, a12}, r2[3] = {a02, a12, a22 - lmin};
+  double c[3][3] = {{r0[1] * r1[2] - r0[2] * r1[1], r0[2] * r1[0] - r0[0] * r1[2], r0[0] * r1[1] - r0[1] * r1[0]},
+                    {r0[1] * r2[2] - r0[2] * r2[1], r0[2] * r2[0] - r0[0] * r2[2], r0[0] * r2[1] - r0[1] * r2[0]},
+                    {r1[1] * r2[2] - r1[2] * r2[1], r1[2] * r2[0] - r1[0] * r2[2], r1[0] * r2[1] - r1[1] * r2[0]}};
+  int best = 0;
+  double bn = -1.0;
+  for (int k = 0; k < 3; ++k) {
+    double nk = c[k][0] * c[k][0] + c[k][1] * c[k][1] + c[k][2] * c[k][2];
+    if (nk > bn) {
+      bn = nk;
+      best = k;
+    }
+  }
+  if (!(bn > 1e-300)) return false;
+  const double inv = 1.0 / sqrt(bn);
+  v[0] = c[best][0] * inv;
+  v[1] = c[best][1] * inv;
+  v[2] = c[best][2] * inv;
+  return true;
+}
+
+// Normal of each point: direction of least spread of the points within
+// sigma_j (its k-nearest-neighbour ball), by PCA.  Used only to seed gp_nn.
+__global__ void __launch_bounds__(128) k_normals(NNGrid g, int64_t J, const float* __restrict__ sigma,
+                                                 float* __restrict__ normals) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= J) return;
+  const float4 me = g.pts[t];
+  const int self = __float_as_int(me.w);
+  const float q[3] = {me.x, me.y, me.z};
+  const int c[3] = {nn_cell(q[0], g), nn_cell(q[1], g), nn_cell(q[2], g)};
+  const float rad = sigma[self];
+  const float r2 = rad * rad * 1.000001f;
+  const float margin = nn_margin(q);
+  double m[3] = {0, 0, 0}, S[6] = {0, 0, 0, 0, 0, 0};
+  int cnt = 0;
+  for (int r = 0; r <= g.G; ++r) {
+    nn_ring(c, r, g, [&](int a, int b) {
+      for (int p = a; p < b; ++p) {
+        float4 P = g.pts[p];
+        float dx = P.x - q[0], dy = P.y - q[1], dz = P.z - q[2];
+        if (dx * dx + dy * dy + dz * dz > r2) continue;
+        m[0] += dx;
+        m[1] += dy;
+        m[2] += dz;
+        S[0] += (double)dx * dx;
+        S[1] += (double)dx * dy;
+        S[2] += (double)dx * dz;
+        S[3] += (double)dy * dy;
+        S[4] += (double)dy * dz;
+        S[5] += (double)dz * dz;
+        ++cnt;
+      }
+    });
+    float gap = nn_gap(q, c, r, g);
+    if (gap == INFINITY || gap - margin > rad) break;
+  }
+  float nv[3] = {0.f, 0.f, 0.f};
+  if (cnt >= 3) {
+    for (int a = 0; a < 3; ++a) m[a] /= cnt;
+    double C[6] = {S[0] / cnt - m[0] * m[0], S[1] / cnt - m[0] * m[1], S[2] / cnt - m[0] * m[2],
+                   S[3] / cnt - m[1] * m[1], S[4] / cnt - m[1] * m[2], S[5] / cnt - m[2] * m[2]};
+    double v[3];
+    if (smallest_eigvec(C, v)) {
+      nv[0] = (float)v[0];
+      nv[1] = (float)v[1];
+      nv[2] = (float)v[2];
+    }
+  }
+  normals[3 * (int64_t)self + 0] = nv[0];
+  normals[3 * (int64_t)self + 1] = nv[1];
+  normals[3 * (int64_t)self + 2] = nv[2];
+}
+
+// Extra seeds: the points of the cell holding the foot of q on the tangent
+// plane of its source point, f = q - ((q - s) . n) n.  The nearest point tends
+// to lie near f, much closer to q than s is, which shrinks the ball to walk.
+__device__ __forceinline__ void nn_seed_foot(NNState& st, const float q[3], const int32_t* __restrict__ hint,
+                                             int64_t i, int64_t J, const float* __restrict__ pts_orig,
+                                             const float* __restrict__ normals, const NNGrid& g) {
+  if (!hint || !normals) return;
+  const int j = hint[i];
+  if (j < 0 || j >= J) return;
+  const float n0 = normals[3 * (int64_t)j], n1 = normals[3 * (int64_t)j + 1], n2 = normals[3 * (int64_t)j + 2];
+  const float s0 = pts_orig[3 * (int64_t)j], s1 = pts_orig[3 * (int64_t)j + 1], s2 = pts_orig[3 * (int64_t)j + 2];
+  const float h = (q[0] - s0) * n0 + (q[1] - s1) * n1 + (q[2] - s2) * n2;
+  const int cx = nn_cell(q[0] - h * n0, g), cy = nn_cell(q[1] - h * n1, g), cz = nn_cell(q[2] - h * n2, g);
+  const int64_t cell = ((int64_t)cz * g.G + cy) * g.G + cx;
+  const int a = __ldg(g.start + cell), b = __ldg(g.start + cell + 1);
+  for (int p = a; p < b; ++p) {
+    float4 P = __ldg(g.pts + p);
+    float dx = q[0] - P.x, dy = q[1] - P.y, dz = q[2] - P.z;
+    nn_update(st, dx * dx + dy * dy + dz * dz, __float_as_int(P.w));
+  }
+}
+
 __global__ void __launch_bounds__(256) k_nn(NNGrid g, const float* __restrict__ qin, int64_t n,
                                             const int32_t* __restrict__ hint, int64_t J,
                                             const float* __restrict__ pts_orig, int32_t* __restrict__ nn_out,
-                                            float* __restrict__ rec, Grid band, int32_t* __restrict__ nvalid) {
-  // All lanes stay until the lockstep walk is over (tail lanes just idle).
+                                            float* __restrict__ rec, Grid band, int32_t* __restrict__ nvalid,
+                                            const float* __restrict__ normals) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const bool active = i < n;
   float q[3] = {0.f, 0.f, 0.f};
@@ -553,14 +588,10 @@ __global__ void __launch_bounds__(256) k_nn(NNGrid g, const float* __restrict__ 
     c[2] = nn_cell(q[2], g);
     margin = nn_margin(q);
     nn_seed(st, q, hint, i, J, pts_orig);
+    if (st.b1 < INFINITY) nn_seed_foot(st, q, hint, i, J, pts_orig, normals, g);
   }
-  const bool seeded = ok && st.b1 < INFINITY;
-  if (__any_sync(0xffffffffu, seeded)) nn_walk_warp(q, c, g, margin, st, seeded);
   int best = -1;
-  if (seeded)
-    best = nn_break_tie(q, c, g, margin, st, -1);
-  else if (ok)
-    best = nn_thread_search(q, c, g, margin, st);
+  if (ok) best = nn_thread_search(q, c, g, margin, st);
   if (active) nn_finish(i, q, best, pts_orig, nn_out, rec, band, nvalid);
 }
 
@@ -668,6 +699,8 @@ gp_status gp_build_points(gp_band* b, const float* pts_dev) {
     if ((st = build_emit_order(b))) return st;
     int k = (int)std::min<int64_t>(b->knn_k, J - 1);
     GP_KERNEL(ctx, "k_knn_sigma", k_knn_sigma<<<gp_blocks(J, 128), 128, 0, s>>>(g, J, k, b->sigma));
+    if ((st = gp_alloc(ctx, &b->normals, 3 * J, "normals"))) return st;
+    GP_KERNEL(ctx, "k_normals", k_normals<<<gp_blocks(J, 128), 128, 0, s>>>(g, J, b->sigma, b->normals));
   }
   return GP_OK;
 }
@@ -698,6 +731,7 @@ extern "C" gp_status gp_nn(gp_band* b, const float* q_dev, int64_t n, const int3
   band.R = b->R;
   band.half_r = 0.5f * (float)b->R;
   GP_KERNEL(ctx, "k_nn", k_nn<<<gp_blocks(n, 256), 256, 0, ctx->stream>>>(g, q_dev, n, hint_dev, b->J, b->pts,
-                                                                           nn_dev, rec_dev, band, nvalid_dev));
+                                                                           nn_dev, rec_dev, band, nvalid_dev,
+                                                                           b->normals));
   return GP_OK;
 }
