@@ -133,9 +133,11 @@ __device__ void finalize_loss(const double* __restrict__ partials, const FinalAr
 // writes the loss slots and re-arms the counter for the next call.
 __device__ void finish_if_last(const double* __restrict__ partials, const FinalArgs& fa) {
   __shared__ int am_last;
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) am_last = (atomicAdd(fa.done, 1) == (int)gridDim.x - 1);
+  __syncthreads();  // thread 0 has written this block's partials
+  if (threadIdx.x == 0) {
+    __threadfence();
+    am_last = (atomicAdd(fa.done, 1) == (int)gridDim.x - 1);
+  }
   __syncthreads();
   if (!am_last) return;
   __threadfence();
@@ -221,7 +223,7 @@ __device__ __forceinline__ void block_store3(double* __restrict__ partials, floa
 }
 
 template <bool DET, bool GRAD, bool LAST>
-__global__ void __launch_bounds__(Q_THREADS) k_query(Grid G, const float* __restrict__ rec, int64_t B,
+__global__ void __launch_bounds__(Q_THREADS, 4) k_query(Grid G, const float* __restrict__ rec, int64_t B,
                                                      const int32_t* __restrict__ bv, float beta, float gamma,
                                                      float* __restrict__ grad, unsigned long long* __restrict__ acc,
                                                      double* __restrict__ partials, int32_t* __restrict__ err,
@@ -314,6 +316,8 @@ __global__ void __launch_bounds__(TV_THREADS) k_tv(Grid G, const int32_t* __rest
   __shared__ float sD[HN];
   __shared__ uint8_t sF[HN];  // bit0: stored and inside [0,R]^3, bit1: in T
   __shared__ float sInv[IN];  // 1/TV of T vertices of the inner region, else 0
+  __shared__ int sSlot[27];   // slots of the 3x3x3 bricks around the current one (-1: absent)
+  __shared__ uint32_t sT[27 * 16];  // their T masks
   float tsum = 0.f;
   double qscale = 0.0;
   if (DET) {
@@ -327,17 +331,29 @@ __global__ void __launch_bounds__(TV_THREADS) k_tv(Grid G, const int32_t* __rest
     const int64_t addr = slot * 512 + l;
     if (TV) {
       __syncthreads();  // previous brick done with the shared arrays
+      // The 27 bricks around this one: slots and T masks, once per brick.
+      if (l < 27) {
+        int bx = (ox >> 3) + l % 3 - 1, by = (oy >> 3) + (l / 3) % 3 - 1, bz = (oz >> 3) + l / 9 - 1;
+        sSlot[l] = gp_brick_slot(G.table, G.nb, bx * 8, by * 8, bz * 8);
+      }
+      __syncthreads();
+      for (int w = l; w < 27 * 16; w += TV_THREADS) {
+        int sl = sSlot[w >> 4];
+        sT[w] = sl >= 0 ? __ldg(G.masks + (int64_t)sl * 48 + (w & 15)) : 0u;
+      }
+      __syncthreads();
       for (int h = l; h < HN; h += TV_THREADS) {
         int hx = h % HS - 2, hy = (h / HS) % HS - 2, hz = h / (HS * HS) - 2;
         int i = ox + hx, j = oy + hy, k = oz + hz;
         float v = 0.f;
         uint8_t f = 0;
         if (i >= 0 && j >= 0 && k >= 0 && i <= G.R && j <= G.R && k <= G.R) {
-          int s = gp_brick_slot(G.table, G.nb, i, j, k);
-          if (s >= 0) {
+          int nbi = ((hz >> 3) + 1) * 9 + ((hy >> 3) + 1) * 3 + ((hx >> 3) + 1);  // hx in [-2, 9]
+          int sl = sSlot[nbi];
+          if (sl >= 0) {
             int loc = gp_local(i, j, k);
-            v = __ldg(G.D + (int64_t)s * 512 + loc);
-            f = 1 | (gp_mask_bit(G.masks, s, 0, loc) ? 2 : 0);
+            v = __ldg(G.D + (int64_t)sl * 512 + loc);
+            f = 1 | (((sT[nbi * 16 + (loc >> 5)] >> (loc & 31)) & 1u) ? 2 : 0);
           }
         }
         sD[h] = v;
