@@ -261,6 +261,16 @@ __device__ __forceinline__ uint32_t gp_feistel(uint32_t x, int half, uint32_t ep
   return (left << half) | right;
 }
 
+// Query at pool position k of an epoch: q = s_j + sigma_j * z, z the three
+// Box-Muller normals of Philox4x32-10 at counter (k, epoch, 0, 0).
+__device__ __forceinline__ float3 gp_draw_query(const float* __restrict__ pts, const float* __restrict__ sigma, int32_t j,
+                                             int64_t k, uint32_t epoch, uint32_t k0, uint32_t k1) {
+  float3 z = gp_box_muller3(gp_philox((uint32_t)k, epoch, 0u, 0u, k0, k1));
+  float sg = sigma[j];
+  return make_float3(pts[3 * (int64_t)j + 0] + sg * z.x, pts[3 * (int64_t)j + 1] + sg * z.y,
+                     pts[3 * (int64_t)j + 2] + sg * z.z);
+}
+
 __host__ __device__ inline int gp_feistel_bits(int64_t J) {
   int m = 2;
   while ((int64_t(1) << m) < J) ++m;

@@ -38,14 +38,6 @@ __global__ void k_perm(int64_t J, int half, uint32_t epoch, uint32_t k0, uint32_
   inv[x] = (int32_t)p;
 }
 
-__device__ __forceinline__ float3 draw_query(const float* __restrict__ pts, const float* __restrict__ sigma, int32_t j,
-                                             int64_t k, uint32_t epoch, uint32_t k0, uint32_t k1) {
-  float3 z = gp_box_muller3(gp_philox((uint32_t)k, epoch, 0u, 0u, k0, k1));
-  float sg = sigma[j];
-  return make_float3(pts[3 * (int64_t)j + 0] + sg * z.x, pts[3 * (int64_t)j + 1] + sg * z.y,
-                     pts[3 * (int64_t)j + 2] + sg * z.z);
-}
-
 __device__ __forceinline__ void put_query(int64_t i, float3 v, int32_t j, int64_t k, float* __restrict__ q,
                                           int32_t* __restrict__ src, int32_t* __restrict__ pos) {
   q[3 * i + 0] = v.x;
@@ -63,7 +55,7 @@ __global__ void k_sample(const float* __restrict__ pts, const float* __restrict_
   if (i >= count) return;
   int64_t k = first + i;
   int32_t j = perm[k % J];
-  put_query(i, draw_query(pts, sigma, j, k, epoch, k0, k1), j, k, q, src, pos);
+  put_query(i, gp_draw_query(pts, sigma, j, k, epoch, k0, k1), j, k, q, src, pos);
 }
 
 // Replicas r >= 0 of pool slot p whose position k = p + r J lies in
@@ -184,7 +176,7 @@ __global__ void __launch_bounds__(GP_ORDER_THREADS) k_order_emit(
         atomicOr(err, GP_EF_RANGE);
         continue;
       }
-      put_query(i, draw_query(pts, sigma, jj[u], k, epoch, k0, k1), jj[u], k, q, src, pos);
+      put_query(i, gp_draw_query(pts, sigma, jj[u], k, epoch, k0, k1), jj[u], k, q, src, pos);
     }
   }
 }
