@@ -283,6 +283,78 @@ typedef struct gp_adam {
  * optimised).  Errors: GP_ERR_ARG (step < 1, null pointers). */
 gp_status gp_update(gp_band* band, const float* grad_dev, const gp_adam* hp, int64_t step);
 
+/* ------------------------------------------------------------- many clouds */
+
+/* Several clouds of uneven size fitted together: the whole step of Sec. 3
+ * (sampling, NN, Eq. 3-8 forward and backward, L_TV, Adam) for every cloud in
+ * one launch per stage, each a persistent kernel over a work list that mixes
+ * the clouds' tiles.  Each cloud keeps its own band (its values and Adam
+ * moments are the band's own D, m, v, which gp_band_values and gp_band_export
+ * read); the multi owns the records, the per-cloud orders Pi_e, the gradient
+ * buffer and a step counter t kept on the device.
+ *
+ * Cloud k at step t takes batch t mod nb_k of epoch t / nb_k, nb_k =
+ * ceil(Q_k / B_k): pool positions [b B_k, min((b+1) B_k, Q_k)), the queries
+ * gp_sample draws with key seed + k; with GP_SAMPLE_SPATIAL they are emitted in
+ * the spatial order (the same set).  Adam runs as step t + 1 with learning
+ * rate lr * lr_decay^floor(t / lr_every) (lr_every = 0: constant lr). */
+typedef struct gp_multi gp_multi;
+
+typedef struct gp_multi_info {
+  int32_t n;                    /* clouds                                      */
+  uint32_t flags;               /* creation flags                              */
+  int32_t records_per_tile;     /* also the block size of the record kernels   */
+  int32_t blocks_per_sm_nn;     /* persistent blocks per SM, NN stage          */
+  int32_t blocks_per_sm_tv;     /* ... L_TV sweep                              */
+  int32_t blocks_per_sm_query;  /* ... fused query forward + backward          */
+  int32_t error_bits;           /* kernel error flags raised so far (0 = none) */
+  int32_t reserved;
+  int64_t total_B;              /* sum of the batch sizes (record slots)       */
+  int64_t V_total;              /* sum of the bands' V_stored (gradient size)  */
+  int64_t step;                 /* t, the next step to run                     */
+} gp_multi_info;
+
+/* Bands: n distinct bands of ctx, built with knn_k > 0 and without
+ * GP_BAND_DETERMINISTIC; they must outlive the multi.  Q[k], B[k]: pool size
+ * and batch size of cloud k, 1 <= B[k] <= Q[k] < 2^31, sum of B[k] < 2^31.
+ * flags: 0 or GP_SAMPLE_SPATIAL.  Allocates the multi's buffers (the
+ * dominant ones: 36 bytes per record slot, 4 bytes per stored vertex, 8 bytes
+ * per point) and synchronises.  t starts at 0.  Errors: GP_ERR_ARG,
+ * GP_ERR_OOM, GP_ERR_CUDA. */
+gp_status gp_multi_create(gp_ctx* ctx, gp_band* const* bands, int32_t n, const int64_t* Q, const int64_t* B,
+                          uint64_t seed, uint32_t flags, gp_multi** out);
+
+/* Step t of every cloud, then t += 1 on the device.  Stream-ordered on the
+ * context's stream; allocates nothing and does not synchronise, so a call can
+ * be captured into a CUDA graph and replayed: the weights, hyper-parameters
+ * and loss_dev of the captured call then stay fixed while t advances.  Writes
+ * 8 loss slots per cloud to loss_dev (n x 8 floats, the gp_step layout).
+ * Errors: GP_ERR_ARG (null pointers, lr_every < 0), GP_ERR_CUDA. */
+gp_status gp_multi_step(gp_multi* m, const gp_loss_w* w, const gp_adam* hp, float lr_decay, int64_t lr_every,
+                        float* loss_dev);
+
+/* Chooses the records per tile (128, 256 or 512) and the persistent blocks
+ * per SM of the NN, L_TV and query stages by timing each candidate with CUDA
+ * events on the current step's data.  Leaves D, m, v and t as they were;
+ * synchronises.  Call it before capturing a graph of gp_multi_step. */
+gp_status gp_multi_autotune(gp_multi* m, const gp_loss_w* w);
+
+/* Configuration, step counter and error flags (synchronises). */
+gp_status gp_multi_get_info(gp_multi* m, gp_multi_info* out);
+
+/* Sets t (to resume a fit; synchronises).  Errors: GP_ERR_ARG (step < 0). */
+gp_status gp_multi_set_step(gp_multi* m, int64_t step);
+
+/* Device views of cloud k's slices of the multi's buffers, as the last step
+ * left them: its B_k records (B_k x 6 floats; slots past a short batch hold
+ * NaN queries), their source points (B_k ints, -1 for those slots) and its
+ * gradient (V_stored floats).  Any pointer may be NULL.  Valid until
+ * gp_multi_destroy; gp_multi_autotune rewrites them. */
+gp_status gp_multi_buffers(gp_multi* m, int32_t k, float** rec_dev, int32_t** src_dev, float** grad_dev);
+
+/* Waits for the context's stream and frees the multi (not the bands). */
+void gp_multi_destroy(gp_multi* m);
+
 /* ------------------------------------------------------- no allocation */
 
 /* The query part of gp_step (Eq. 4, 6, 7: L_Pull + beta L_Surface +

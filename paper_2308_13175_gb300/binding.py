@@ -56,6 +56,15 @@ class Adam(ctypes.Structure):
     _fields_ = [("lr", _f), ("beta1", _f), ("beta2", _f), ("eps", _f)]
 
 
+class MultiInfo(ctypes.Structure):
+    _fields_ = [("n", _i32), ("flags", _u32), ("records_per_tile", _i32), ("blocks_per_sm_nn", _i32),
+                ("blocks_per_sm_tv", _i32), ("blocks_per_sm_query", _i32), ("error_bits", _i32),
+                ("reserved", _i32), ("total_B", _i64), ("V_total", _i64), ("step", _i64)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_ if name != "reserved"}
+
+
 SIGNATURES = {
     "gp_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, _vp]),
     "gp_set_stream": (ctypes.c_int, [_vp, _vp]),
@@ -80,6 +89,14 @@ SIGNATURES = {
     "gp_nn": (ctypes.c_int, [_vp, _vp, _i64, _vp, _vp, _vp, _vp]),
     "gp_step": (ctypes.c_int, [_vp, _vp, _i64, _vp, _vp, ctypes.POINTER(LossW), _vp, _vp, _u32]),
     "gp_update": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(Adam), _i64]),
+    "gp_multi_create": (ctypes.c_int, [_vp, ctypes.POINTER(_vp), _i32, ctypes.POINTER(_i64), ctypes.POINTER(_i64),
+                                       _u64, _u32, ctypes.POINTER(_vp)]),
+    "gp_multi_step": (ctypes.c_int, [_vp, ctypes.POINTER(LossW), ctypes.POINTER(Adam), _f, _i64, _vp]),
+    "gp_multi_autotune": (ctypes.c_int, [_vp, ctypes.POINTER(LossW)]),
+    "gp_multi_get_info": (ctypes.c_int, [_vp, ctypes.POINTER(MultiInfo)]),
+    "gp_multi_set_step": (ctypes.c_int, [_vp, _i64]),
+    "gp_multi_buffers": (ctypes.c_int, [_vp, _i32, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp)]),
+    "gp_multi_destroy": (None, [_vp]),
     "gp_step_dense_noalloc": (ctypes.c_int, [_vp, _i32, _vp, _vp, _i64, ctypes.POINTER(LossW), _vp, _vp]),
 }
 
@@ -265,12 +282,12 @@ def gp_band_values(band: Band):
     return tuple(_wrap_device(p.value, band.V_stored, band) for p in (pd, pm, pv))
 
 
-def _wrap_device(addr: int, n: int, owner):
+def _wrap_device(addr: int, n: int, owner, typestr: str = "<f4"):
     import torch
 
     class _CAI:
         def __init__(self):
-            self.__cuda_array_interface__ = {"shape": (n,), "typestr": "<f4", "data": (addr, False), "version": 3,
+            self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (addr, False), "version": 3,
                                              "strides": None}
     t = torch.as_tensor(_CAI(), device=torch.device("cuda", owner.ctx.device))
     return t
@@ -357,3 +374,85 @@ def gp_step_dense_noalloc(ctx: Context, R: int, d, rec, B: int, grad, loss, weig
     ctx.sync_stream()
     ctx.check(ctx.lib.gp_step_dense_noalloc(ctx.handle, int(R), _ptr(d), _ptr(rec), int(B), ctypes.byref(w),
                                             _ptr(grad), _ptr(loss)))
+
+
+# ----------------------------------------------------------- many clouds
+class Multi:
+    """A gp_multi: several bands stepped together, one launch per stage.  Holds
+    references to its bands, which the C side needs alive."""
+
+    def __init__(self, ctx: Context, handle, bands, Q, B):
+        self.ctx = ctx
+        self.handle = handle
+        self.bands = list(bands)
+        self.Q = [int(x) for x in Q]
+        self.B = [int(x) for x in B]
+
+    @property
+    def n(self) -> int:
+        return len(self.bands)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.ctx.lib.gp_multi_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def gp_multi_create(ctx: Context, bands, Q, B, seed: int = 0, spatial: bool = True) -> Multi:
+    n = len(bands)
+    arr = (_vp * n)(*[b.handle for b in bands])
+    qa = (_i64 * n)(*[int(x) for x in Q])
+    ba = (_i64 * n)(*[int(x) for x in B])
+    out = _vp()
+    ctx.sync_stream()
+    ctx.check(ctx.lib.gp_multi_create(ctx.handle, arr, n, qa, ba, int(seed), GP_SAMPLE_SPATIAL if spatial else 0,
+                                      ctypes.byref(out)))
+    return Multi(ctx, out, bands, Q, B)
+
+
+def gp_multi_step(m: Multi, loss, weights=(1.0, 1.0, 0.005), lr: float = 1e-3, beta1: float = 0.9,
+                  beta2: float = 0.999, eps: float = 1e-8, lr_decay: float = 1.0, lr_every: int = 0):
+    import torch
+    _need(loss, torch.float32, 8 * m.n, "loss")
+    w = LossW(*[float(x) for x in weights])
+    hp = Adam(float(lr), float(beta1), float(beta2), float(eps))
+    m.ctx.sync_stream()
+    m.ctx.check(m.ctx.lib.gp_multi_step(m.handle, ctypes.byref(w), ctypes.byref(hp), float(lr_decay), int(lr_every),
+                                        _ptr(loss)))
+
+
+def gp_multi_autotune(m: Multi, weights=(1.0, 1.0, 0.005)):
+    w = LossW(*[float(x) for x in weights])
+    m.ctx.sync_stream()
+    m.ctx.check(m.ctx.lib.gp_multi_autotune(m.handle, ctypes.byref(w)))
+    return gp_multi_get_info(m)
+
+
+def gp_multi_get_info(m: Multi) -> dict:
+    info = MultiInfo()
+    m.ctx.sync_stream()
+    m.ctx.check(m.ctx.lib.gp_multi_get_info(m.handle, ctypes.byref(info)))
+    return info.as_dict()
+
+
+def gp_multi_set_step(m: Multi, step: int):
+    m.ctx.sync_stream()
+    m.ctx.check(m.ctx.lib.gp_multi_set_step(m.handle, int(step)))
+
+
+def gp_multi_buffers(m: Multi, k: int):
+    """Zero-copy views of cloud k's records (B_k, 6), sources (B_k,) and
+    gradient (V_stored,) as the last step left them."""
+    pr, ps, pg = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+    m.ctx.check(m.ctx.lib.gp_multi_buffers(m.handle, int(k), ctypes.byref(pr), ctypes.byref(ps), ctypes.byref(pg)))
+    Bk = m.B[k]
+    rec = _wrap_device(pr.value, 6 * Bk, m).view(Bk, 6)
+    src = _wrap_device(ps.value, Bk, m, "<i4")
+    grad = _wrap_device(pg.value, m.bands[k].V_stored, m)
+    return rec, src, grad

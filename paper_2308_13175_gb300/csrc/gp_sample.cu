@@ -19,7 +19,6 @@
 namespace {
 
 constexpr int WALK_LIMIT = 4096;  // cycle walks end in < 4 rounds on average
-constexpr int NW = GP_ORDER_THREADS / 32;
 
 __global__ void k_perm(int64_t J, int half, uint32_t epoch, uint32_t k0, uint32_t k1, int32_t* __restrict__ perm,
                        int32_t* __restrict__ inv, int32_t* __restrict__ err) {
@@ -56,51 +55,6 @@ __global__ void k_sample(const float* __restrict__ pts, const float* __restrict_
   int64_t k = first + i;
   int32_t j = perm[k % J];
   put_query(i, gp_draw_query(pts, sigma, j, k, epoch, k0, k1), j, k, q, src, pos);
-}
-
-// Replicas r >= 0 of pool slot p whose position k = p + r J lies in
-// [first, last): r in [r0, r0 + n).
-__device__ __forceinline__ void owned_range(int64_t p, int64_t J, int64_t first, int64_t last, int64_t& r0, int& n) {
-  int64_t lo = first - p;
-  r0 = lo <= 0 ? 0 : (lo + J - 1) / J;
-  int64_t hi = last - 1 - p;
-  if (hi < 0) {
-    n = 0;
-    return;
-  }
-  int64_t r1 = hi / J;
-  n = r1 >= r0 ? (int)(r1 - r0 + 1) : 0;
-}
-
-// Exclusive scan of one int per thread over the block; returns the block total.
-__device__ __forceinline__ int block_exclusive_scan(int v, int* excl) {
-  __shared__ int wsum[NW];
-  __shared__ int total_s;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  int incl = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    int y = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += y;
-  }
-  if (lane == 31) wsum[wid] = incl;
-  __syncthreads();
-  if (wid == 0) {
-    int w = lane < NW ? wsum[lane] : 0;
-    int wi = w;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      int y = __shfl_up_sync(0xffffffffu, wi, o);
-      if (lane >= o) wi += y;
-    }
-    if (lane < NW) wsum[lane] = wi - w;
-    if (lane == NW - 1) total_s = wi;
-  }
-  __syncthreads();
-  *excl = wsum[wid] + incl - v;
-  int t = total_s;
-  __syncthreads();  // wsum and total_s may be reused by the next call
-  return t;
 }
 
 // Pass 1: queries owned by each tile of sorted points.
