@@ -45,6 +45,16 @@ WORKLOADS = {
                         "(10 per point), full batch",
                    cloud=lambda: __import__("paper_2308_13175_gb300.synth", fromlist=["x"]).sphere_cloud(5000, 0.5, 0),
                    R=64, M1=-1, M2=-1, Q=50_000, B=50_000, lr=1e-3),
+    "scene": dict(desc="indoor scene: 10 x 8 x 3 m room (floor, ceiling, 4 walls) + 60 boxes / cylinders, "
+                       "10,000,000 points + N(0, 0.002 m^2) noise, normalised to [-1,1]^3; 1024^3 grid, band of "
+                       "8^3 float32 bricks; pool 50,000,000 queries/epoch, batch 2,097,152",
+                  cloud=lambda: __import__("paper_2308_13175_gb300.synth", fromlist=["x"]).room_cloud(10_000_000, seed=2),
+                  R=1024, M1=2, M2=2, Q=50_000_000, B=2_097_152, lr=1e-3),
+    "superquadric": dict(desc="large object: union of 10 superquadrics (exponents U[0.3,3]), 2,000,000 points + "
+                              "N(0,0.001^2) noise; 512^3 grid, band of 8^3 float32 bricks; pool 20,000,000 "
+                              "queries/epoch, batch 4,194,304",
+                         cloud=lambda: __import__("paper_2308_13175_gb300.synth", fromlist=["x"]).superquadric_cloud(2_000_000, seed=4),
+                         R=512, M1=2, M2=2, Q=20_000_000, B=4_194_304, lr=1e-3),
     "collection": dict(desc="batched fitting: 64 shapes, each a union of 1-5 ellipsoids / boxes / tori, point "
                             "counts log-uniform in [5,000, 500,000], grids drawn from {128, 256, 512}^3 with a "
                             "2-voxel band of 8^3 float32 bricks; pool 10 queries per point, batch = pool / 8 per "
@@ -261,10 +271,12 @@ def run_ours(args, world, rank, local):
     pts = wl["cloud"]()
     R = wl["R"]
     ctx = gb.gp_create(local)
-    band = gb.gp_build_band(ctx, torch.from_numpy(pts).cuda(), R, wl["M1"], wl["M2"], 50, nn_grid=args.nn_grid)
+    band = gb.gp_build_band(ctx, torch.from_numpy(pts).cuda(), R, wl["M1"], wl["M2"], 50, nn_grid=args.nn_grid,
+                            deterministic=args.deterministic)
     c = 0.5 * (pts.min(0) + pts.max(0))
     gb.gp_band_init_sphere(band, c, 2.0 * 2.0 / R, 0.0, seed=0)
-    fit = FitStep(band, wl["Q"], wl["B"], seed=rank, weights=PAPER_WEIGHTS, lr=wl["lr"])
+    fit = FitStep(band, wl["Q"], wl["B"], seed=rank, weights=PAPER_WEIGHTS, lr=wl["lr"],
+                  deterministic=args.deterministic)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
     info = band.info
@@ -349,7 +361,7 @@ def run_ours(args, world, rank, local):
         e_start.record(stream)
         dq.copy_(hq[k % NH], non_blocking=True)
         gb.gp_nn(band, dq, None, fit.rec, nvalid_out=fit.nvalid)
-        gb.gp_step(band, fit.rec, B, fit.grad, fit.loss, PAPER_WEIGHTS, nvalid=fit.nvalid)
+        gb.gp_step(band, fit.rec, B, fit.grad, fit.loss, PAPER_WEIGHTS, nvalid=fit.nvalid, flags=fit.flags)
         gb.gp_update(band, fit.grad, wl["lr"], step_t + k + 1)
         hloss[k].copy_(fit.loss, non_blocking=True)
         e_end.record(stream)
@@ -384,7 +396,7 @@ def run_ours(args, world, rank, local):
             t_ms.append(e0.elapsed_time(e1))
             flush.fill_(float(k))
             e0.record(stream)
-            gb.gp_step(band, rec, B, fit.grad, fit.loss, PAPER_WEIGHTS, nvalid=nv)
+            gb.gp_step(band, rec, B, fit.grad, fit.loss, PAPER_WEIGHTS, nvalid=nv, flags=fit.flags)
             gb.gp_update(band, fit.grad, wl["lr"], step_t + K + k + 1)
             e1.record(stream)
             torch.cuda.synchronize()
@@ -409,7 +421,9 @@ def run_ours(args, world, rank, local):
                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                "config": {"workload": wl["desc"], "parallelism": f"replicas x{world}", "nn_grid": info["nn_grid"],
                           "l2": "flushed between timed steps (256 MB write outside the step events)",
-                          "V_stored": Vs, "V_trainable": Vt, "V_tv": info["V_tv"], "J": J},
+                          "V_stored": Vs, "V_trainable": Vt, "V_tv": info["V_tv"], "J": J,
+                          "gradient_sum": "deterministic two-word fixed point" if args.deterministic
+                          else "float atomics"},
                "roofline": roofline, "cpu_baseline": cpu,
                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 12 * B, "d2h_bytes_per_step": 32},
                "gpu_launches": int(launches), "clocks": clk, "kernels": per_kernel, "torch_autograd": torch_cmp,
@@ -572,6 +586,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-torch", action="store_true", help="skip the plain PyTorch autograd comparison")
     ap.add_argument("--nn-grid", type=int, default=0, help="cells per axis of the point cell list (0 = automatic)")
+    ap.add_argument("--deterministic", action="store_true",
+                    help="bit-reproducible gradient sums (fixed point) instead of float atomics")
     args = ap.parse_args()
     if args.impl == "reference" and args.workload == "collection":
         ap.error("the oracle arm times the single-cloud workloads")

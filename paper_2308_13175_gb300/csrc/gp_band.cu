@@ -150,6 +150,20 @@ __global__ void k_assign_slots(const uint8_t* __restrict__ need, const int32_t* 
   coord[3 * slot + 2] = bz;
 }
 
+// Slots of the 27 bricks around each brick (itself included), x fastest.
+__global__ void k_brick_nbr(const int32_t* __restrict__ table, const int32_t* __restrict__ coord, int nb,
+                            int64_t n_bricks, int32_t* __restrict__ nbr) {
+  int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= n_bricks * 27) return;
+  int64_t slot = a / 27;
+  int t = (int)(a - slot * 27);
+  int bx = coord[3 * slot] + t % 3 - 1, by = coord[3 * slot + 1] + (t / 3) % 3 - 1, bz = coord[3 * slot + 2] + t / 9 - 1;
+  int32_t v = -1;
+  if ((unsigned)bx < (unsigned)nb && (unsigned)by < (unsigned)nb && (unsigned)bz < (unsigned)nb)
+    v = table[((int64_t)bz * nb + by) * nb + bx];
+  nbr[a] = v;
+}
+
 // One block of 512 threads per brick: masks by warp ballots, counts, active flag.
 __global__ void k_brick_masks(const uint8_t* __restrict__ verts, int R, const int32_t* __restrict__ coord,
                               uint32_t* __restrict__ masks, int32_t* __restrict__ active_flag,
@@ -236,6 +250,7 @@ void band_free(gp_band* b) {
   if (!b) return;
   gp_free(b->brick_table);
   gp_free(b->brick_coord);
+  gp_free(b->brick_nbr);
   gp_free(b->masks);
   gp_free(b->active);
   gp_free(b->D);
@@ -326,6 +341,9 @@ gp_status build_band_sets(gp_band* b, const float* pts_dev) {
   GP_CUDA(ctx, cudaMemsetAsync(b->brick_table, 0xFF, nbr * sizeof(int32_t), s));
   if ((st = gp_alloc(ctx, &b->brick_coord, 3 * n_bricks, "brick coords"))) return st;
   GP_KERNEL(ctx, "k_assign_slots", k_assign_slots<<<gp_blocks(nm, 256), 256, 0, s>>>(need, mflags, nb, nm, b->brick_table, b->brick_coord));
+  if ((st = gp_alloc(ctx, &b->brick_nbr, 27 * n_bricks, "brick neighbours"))) return st;
+  if (n_bricks > 0)
+    GP_KERNEL(ctx, "k_brick_nbr", k_brick_nbr<<<gp_blocks(27 * n_bricks, 256), 256, 0, s>>>(b->brick_table, b->brick_coord, nb, n_bricks, b->brick_nbr));
 
   if ((st = gp_alloc(ctx, &b->masks, 48 * n_bricks, "brick masks"))) return st;
   int32_t *aflag = nullptr, *aoffs = nullptr;

@@ -68,6 +68,7 @@ struct gp_band {
   // Brick storage: brick_table[(bz*nb + by)*nb + bx] = slot or -1.
   int32_t* brick_table = nullptr;
   int32_t* brick_coord = nullptr;  // n_bricks x 3 (bx, by, bz)
+  int32_t* brick_nbr = nullptr;    // n_bricks x 27: slots of the 3x3x3 bricks around each (x fastest, -1 absent)
   uint32_t* masks = nullptr;       // n_bricks x 48 words: [T 16][trainable 16][pull 16]
   int32_t* active = nullptr;       // slots of bricks with a trainable vertex
   float* D = nullptr;              // values, V_stored

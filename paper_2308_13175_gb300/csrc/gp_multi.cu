@@ -48,6 +48,7 @@ struct MShape {
   int32_t* perm;         // this cloud's slice of the multi's Pi_e
   int32_t* inv;          // and of Pi_e^-1
   const int32_t* coord;
+  const int32_t* nbr;  // 27 neighbour slots per brick
   const int32_t* active;
   int64_t J, Q, B, nb_epoch, V_tv;
   int64_t rec_off;  // first record slot of this cloud
@@ -287,22 +288,49 @@ __device__ __forceinline__ float block_sum(float v, float* red) {
   return s;
 }
 
-// L_TV sweep: one brick per tile, 512 threads; the gradient is overwritten
-// (every stored slot of every brick), the TV sums go to the cloud's slot 3.
-__global__ void __launch_bounds__(512) k_m_tv(const MShape* __restrict__ shapes, const MTile* __restrict__ tiles,
-                                              int64_t ntiles, float alpha, double* __restrict__ sums) {
-  __shared__ TvShared sh;
-  __shared__ float red[32];
-  for (int64_t ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
+struct MultiTvSrc {
+  const MShape* shapes;
+  const MTile* tiles;
+  __device__ __forceinline__ TvBrick brick(int64_t ti) const {
     const MTile tl = tiles[ti];
     const MShape& S = shapes[tl.shape];
-    const float tv_scale = S.V_tv > 0 ? alpha / (float)S.V_tv : 0.f;
-    float tsum = 0.f;
-    const float gv = tv_brick<true>(S.G, S.coord + 3 * (int64_t)tl.first, tv_scale, sh, tsum);
-    S.grad[(int64_t)tl.first * 512 + threadIdx.x] = gv;
-    const float bs = block_sum(tsum, red);
-    if (threadIdx.x == 0 && bs != 0.f) atomicAdd(sums + 4 * tl.shape + 3, (double)bs);
+    const int32_t* c = S.coord + 3 * (int64_t)tl.first;
+    return TvBrick{S.G.D, S.G.masks, S.nbr + 27 * (int64_t)tl.first, S.G.R, __ldg(c) * 8, __ldg(c + 1) * 8,
+                   __ldg(c + 2) * 8};
   }
+};
+
+// L_TV sweep: one brick per tile (TV_SWEEP_THREADS threads, pipelined across
+// the block's tiles); the gradient is overwritten at every slot of every
+// brick; the TV sums go to each cloud's slot 3, one atomic per run of tiles of
+// the same cloud.
+__global__ void __launch_bounds__(TV_SWEEP_THREADS) k_m_tv(const MShape* __restrict__ shapes,
+                                                           const MTile* __restrict__ tiles, int64_t ntiles,
+                                                           float alpha, double* __restrict__ sums) {
+  __shared__ TvShared sh;
+  __shared__ float red[32];
+  int cur = -1;
+  float acc = 0.f;
+  auto flush = [&]() {
+    const float bs = block_sum(acc, red);
+    if (threadIdx.x == 0 && bs != 0.f) atomicAdd(sums + 4 * cur + 3, (double)bs);
+    acc = 0.f;
+  };
+  tv_sweep(MultiTvSrc{shapes, tiles}, blockIdx.x, gridDim.x, ntiles, sh,
+           [&](int64_t ti, float g0, float g1, float ts) {
+             const MTile tl = tiles[ti];
+             const MShape& S = shapes[tl.shape];
+             if (tl.shape != cur) {
+               if (cur >= 0) flush();
+               cur = tl.shape;
+             }
+             acc += ts;
+             const float tv_scale = S.V_tv > 0 ? alpha / (float)S.V_tv : 0.f;
+             float* gp = S.grad + (int64_t)tl.first * 512 + threadIdx.x;
+             gp[0] = tv_scale * g0;
+             gp[256] = tv_scale * g1;
+           });
+  if (cur >= 0) flush();
 }
 
 // Fused forward + hand-written backward of every valid record (the gp_step
@@ -456,7 +484,7 @@ gp_status launch_nn(gp_multi* m) {
 gp_status launch_tv(gp_multi* m, const gp_loss_w* w) {
   gp_ctx* ctx = m->ctx;
   GP_KERNEL(ctx, "k_m_tv",
-            k_m_tv<<<persistent_grid(m, m->bpsm[ST_TV], m->n_brick_tiles), 512, 0, ctx->stream>>>(
+            k_m_tv<<<persistent_grid(m, m->bpsm[ST_TV], m->n_brick_tiles), TV_SWEEP_THREADS, 0, ctx->stream>>>(
                 m->shapes, m->brick_tiles, m->n_brick_tiles, w->alpha, m->sums));
   return GP_OK;
 }
@@ -607,6 +635,7 @@ extern "C" gp_status gp_multi_create(gp_ctx* ctx, gp_band* const* bands, int32_t
     S.perm = m->perm + joff;
     S.inv = m->inv + joff;
     S.coord = b->brick_coord;
+    S.nbr = b->brick_nbr;
     S.active = b->active;
     S.J = b->J;
     S.Q = Q[k];

@@ -24,7 +24,7 @@
 namespace {
 
 constexpr int Q_THREADS = 256;
-constexpr int TV_THREADS = 512;
+constexpr int TV_THREADS = TV_SWEEP_THREADS;
 // Loss slots from the per-block partial sums, in a fixed order (run by one
 // whole block).
 struct FinalArgs {
@@ -153,8 +153,19 @@ __global__ void __launch_bounds__(Q_THREADS, 4) k_query(Grid G, const float* __r
 // memory.  Writes the gradient of every stored slot: alpha/|T| * dTV/dd_i (+ the
 // fixed-point query sums in deterministic mode, which are cleared for the next
 // step).  Each TV_i enters the loss sum once, from the brick that stores i.
+struct BandTvSrc {
+  Grid G;
+  const int32_t* coord;
+  const int32_t* nbrs;
+  __device__ __forceinline__ TvBrick brick(int64_t s) const {
+    return TvBrick{G.D, G.masks, nbrs + 27 * s, G.R, __ldg(coord + 3 * s) * 8, __ldg(coord + 3 * s + 1) * 8,
+                   __ldg(coord + 3 * s + 2) * 8};
+  }
+};
+
 template <bool DET, bool GRAD, bool TV, bool LAST>
-__global__ void __launch_bounds__(TV_THREADS) k_tv(Grid G, const int32_t* __restrict__ coord, int64_t n_bricks,
+__global__ void __launch_bounds__(TV_THREADS) k_tv(Grid G, const int32_t* __restrict__ coord,
+                                                   const int32_t* __restrict__ nbrs, int64_t n_bricks,
                                                    float tv_scale, float* __restrict__ grad,
                                                    unsigned long long* __restrict__ acc,
                                                    const int32_t* __restrict__ bv, double* __restrict__ partials,
@@ -167,19 +178,28 @@ __global__ void __launch_bounds__(TV_THREADS) k_tv(Grid G, const int32_t* __rest
     qscale = b > 0 ? 1.0 / (double)b : 0.0;
   }
   const int l = threadIdx.x;
-  for (int64_t slot = blockIdx.x; slot < n_bricks; slot += gridDim.x) {
-    const int64_t addr = slot * 512 + l;
-    float gv = 0.f;
-    if (TV) gv = tv_brick<GRAD>(G, coord + 3 * slot, tv_scale, sh, tsum);
-    if (GRAD) {
-      if (DET) {
-        long long hi = (long long)acc[2 * addr], lo = (long long)acc[2 * addr + 1];
-        acc[2 * addr] = 0ull;
-        acc[2 * addr + 1] = 0ull;
-        double q = ((double)hi / FIX_HI + (double)lo / FIX_LO) * qscale;
-        gv = (float)((double)gv + q);
-      }
-      grad[addr] = gv;
+  auto emit = [&](int64_t addr, float gv) {
+    if (!GRAD) return;
+    if (DET) {
+      long long hi = (long long)acc[2 * addr], lo = (long long)acc[2 * addr + 1];
+      acc[2 * addr] = 0ull;
+      acc[2 * addr + 1] = 0ull;
+      double q = ((double)hi / FIX_HI + (double)lo / FIX_LO) * qscale;
+      gv = (float)((double)gv + q);
+    }
+    grad[addr] = gv;
+  };
+  if (TV) {
+    tv_sweep(BandTvSrc{G, coord, nbrs}, blockIdx.x, gridDim.x, n_bricks, sh,
+             [&](int64_t slot, float g0, float g1, float ts) {
+               tsum += ts;
+               emit(slot * 512 + l, tv_scale * g0);
+               emit(slot * 512 + l + 256, tv_scale * g1);
+             });
+  } else {
+    for (int64_t slot = blockIdx.x; slot < n_bricks; slot += gridDim.x) {
+      emit(slot * 512 + l, 0.f);
+      emit(slot * 512 + l + 256, 0.f);
     }
   }
   // block reduction of the TV sum into partials[block*8 + 3]
@@ -209,7 +229,7 @@ unsigned q_grid(const gp_ctx* ctx, int64_t B) {
 }
 
 unsigned tv_grid(const gp_ctx* ctx, int64_t n_bricks) {
-  int64_t cap = (int64_t)ctx->num_sms * 4;
+  int64_t cap = (int64_t)ctx->num_sms * 8;
   if (cap > GP_MAX_PARTIAL_BLOCKS) cap = GP_MAX_PARTIAL_BLOCKS;
   return gp_blocks(n_bricks, 1, cap);
 }
@@ -273,7 +293,8 @@ extern "C" gp_status gp_step(gp_band* b, const float* rec_dev, int64_t B, const 
       return GP_OK;
     }
 #define GP_TV(D_, G_, T_, L_)                                                                                  \
-  k_tv<D_, G_, T_, L_><<<tb, TV_THREADS, 0, s>>>(G, b->brick_coord, b->n_bricks, tv_scale, grad_dev, b->acc, bv, \
+  k_tv<D_, G_, T_, L_><<<tb, TV_THREADS, 0, s>>>(G, b->brick_coord, b->brick_nbr, b->n_bricks, tv_scale, grad_dev, \
+                                                 b->acc, bv, \
                                                  b->partials, err, fa)
     gp_prof_pre(ctx);
     if (tv_last) {

@@ -174,94 +174,170 @@ __device__ __forceinline__ int hidx(int x, int y, int z) { return ((z + 2) * HS 
 __device__ __forceinline__ int iidx(int x, int y, int z) { return ((z + 1) * IS + (y + 1)) * IS + (x + 1); }
 
 
-// One brick of the L_TV sweep, run by a block of 512 threads (one per
-// vertex): stage the brick plus a two-vertex halo (12^3 values with stored /
-// in-grid / T flags) in shared memory, compute 1/TV_n on the brick plus a
-// one-vertex halo (10^3), then gather each vertex's dTV/dd.  Returns tv_scale *
-// dTV/dd_i for this thread's vertex (0 for padding) and adds this brick's own
-// TV_i to tsum.  Each TV_i enters the sum once, from the brick that stores i.
-struct TvShared {
-  float D[HN];
-  uint8_t F[HN];      // bit0: stored and inside [0,R]^3, bit1: in T
-  float inv[IN];      // 1/TV of T vertices of the inner region, else 0
-  int slot[27];       // slots of the 3x3x3 bricks around the current one (-1: absent)
-  uint32_t T[27 * 16];  // their T masks
+// The L_TV sweep, one brick at a time per block of TV_SWEEP_THREADS threads
+// (each owns vertex l and vertex l + 256 of the brick).  For each brick: stage
+// the brick plus a two-vertex halo (12^3 values) and the T masks of its 27
+// neighbour bricks in shared memory, compute 1/TV_n on the brick plus a
+// one-vertex halo (10^3), then gather every vertex's
+//   dTV/dd_i = [i in T] sum_n (d_i - d_n) / TV_i + sum_{n in T} (d_i - d_n) / TV_n
+// over the stored in-grid axis neighbours n.  Each TV_i enters the sum once,
+// from the brick that stores i.
+//
+// Pipeline: the halo of the next brick is copied by cp.async (zero-filled
+// where absent) into the other of two buffers while the current brick is
+// computed; the neighbour slots of the brick after that are fetched in two
+// steps spread over the current brick's phases.  No halo value is held in
+// registers, so several blocks fit on an SM.
+constexpr int TV_SWEEP_THREADS = 256;
+
+// Brick b as the sweep sees it: values, masks, its row of the 27-neighbour
+// table (3x3x3, x fastest, -1 absent), grid size and origin vertex.
+struct TvBrick {
+  const float* D;
+  const uint32_t* masks;
+  const int32_t* nbr;
+  int R, ox, oy, oz;
 };
 
-template <bool GRAD>
-__device__ __forceinline__ float tv_brick(const Grid& G, const int32_t* __restrict__ bcoord, float tv_scale,
-                                          TvShared& sh, float& tsum) {
-  const int l = threadIdx.x;
-  const int lx = l & 7, ly = (l >> 3) & 7, lz = l >> 6;
-  const int ox = bcoord[0] * 8, oy = bcoord[1] * 8, oz = bcoord[2] * 8;
-  __syncthreads();  // previous brick done with the shared arrays
-  if (l < 27) {
-    int bx = (ox >> 3) + l % 3 - 1, by = (oy >> 3) + (l / 3) % 3 - 1, bz = (oz >> 3) + l / 9 - 1;
-    sh.slot[l] = gp_brick_slot(G.table, G.nb, bx * 8, by * 8, bz * 8);
+struct TvShared {
+  float D[2][HN];          // staged values (0 where not stored)
+  uint32_t T[2][27 * 16];  // T-mask words of the 27 neighbour bricks (0 where absent)
+  uint8_t S[2][HN];        // 1: stored and inside [0, R]^3
+  float inv[IN];           // 1/TV of T vertices of the inner region, else 0
+  int slot[2][27];
+  TvBrick bk[2];
+};
+
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem, int src_bytes) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(gmem), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Neighbour-brick index (0..26) of halo offset (hx, hy, hz), each in [-2, 9].
+__device__ __forceinline__ int tv_region(int hx, int hy, int hz) {
+  return ((hz >> 3) + 1) * 9 + ((hy >> 3) + 1) * 3 + ((hx >> 3) + 1);
+}
+
+// Issue the copies of brick bk[q]'s halo and neighbour T masks into buffer q
+// and write its stored flags (plain stores).
+__device__ __forceinline__ void tv_issue(TvShared& sh, int q) {
+  const TvBrick bk = sh.bk[q];
+  for (int h = threadIdx.x; h < HN; h += TV_SWEEP_THREADS) {
+    const int hx = h % HS - 2, hy = (h / HS) % HS - 2, hz = h / (HS * HS) - 2;
+    const int i = bk.ox + hx, j = bk.oy + hy, k = bk.oz + hz;
+    const int sl = sh.slot[q][tv_region(hx, hy, hz)];
+    const bool ok = sl >= 0 && i <= bk.R && j <= bk.R && k <= bk.R;  // negative i lies in an absent brick
+    const float* src = ok ? bk.D + (int64_t)sl * 512 + gp_local(i, j, k) : bk.D;
+    cp_async4(&sh.D[q][h], src, ok ? 4 : 0);
+    sh.S[q][h] = ok ? 1 : 0;
   }
-  __syncthreads();
-  for (int w = l; w < 27 * 16; w += blockDim.x) {
-    int sl = sh.slot[w >> 4];
-    sh.T[w] = sl >= 0 ? __ldg(G.masks + (int64_t)sl * 48 + (w & 15)) : 0u;
+  for (int w = threadIdx.x; w < 27 * 16; w += TV_SWEEP_THREADS) {
+    const int sl = sh.slot[q][w >> 4];
+    const uint32_t* src = sl >= 0 ? bk.masks + (int64_t)sl * 48 + (w & 15) : bk.masks;
+    cp_async4(&sh.T[q][w], src, sl >= 0 ? 4 : 0);
   }
-  __syncthreads();
-  for (int h = l; h < HN; h += blockDim.x) {
-    int hx = h % HS - 2, hy = (h / HS) % HS - 2, hz = h / (HS * HS) - 2;
-    int i = ox + hx, j = oy + hy, k = oz + hz;
-    float v = 0.f;
-    uint8_t f = 0;
-    if (i >= 0 && j >= 0 && k >= 0 && i <= G.R && j <= G.R && k <= G.R) {
-      int nbi = ((hz >> 3) + 1) * 9 + ((hy >> 3) + 1) * 3 + ((hx >> 3) + 1);  // hx in [-2, 9]
-      int sl = sh.slot[nbi];
-      if (sl >= 0) {
-        int loc = gp_local(i, j, k);
-        v = __ldg(G.D + (int64_t)sl * 512 + loc);
-        f = 1 | (((sh.T[nbi * 16 + (loc >> 5)] >> (loc & 31)) & 1u) ? 2 : 0);
-      }
-    }
-    sh.D[h] = v;
-    sh.F[h] = f;
-  }
-  __syncthreads();
-  for (int h = l; h < IN; h += blockDim.x) {
-    int x = h % IS - 1, y = (h / IS) % IS - 1, z = h / (IS * IS) - 1;
-    int c = hidx(x, y, z);
+}
+
+// 1/TV over the inner region of buffer p; adds this thread's share of the
+// brick's own TV_i to tsum.
+__device__ __forceinline__ void tv_inverse(TvShared& sh, int p, float& tsum) {
+  const float* D = sh.D[p];
+  const uint8_t* S = sh.S[p];
+  for (int h = threadIdx.x; h < IN; h += TV_SWEEP_THREADS) {
+    const int x = h % IS - 1, y = (h / IS) % IS - 1, z = h / (IS * IS) - 1;
+    const int c = hidx(x, y, z);
     float inv = 0.f;
-    if ((sh.F[c] & 3) == 3) {
-      float dc = sh.D[c], acc2 = 0.f;
-      const int nb6[6] = {hidx(x - 1, y, z), hidx(x + 1, y, z), hidx(x, y - 1, z),
-                          hidx(x, y + 1, z), hidx(x, y, z - 1), hidx(x, y, z + 1)};
+    if (S[c]) {
+      const int loc = ((z & 7) << 6) | ((y & 7) << 3) | (x & 7);
+      const uint32_t tw = sh.T[p][tv_region(x, y, z) * 16 + (loc >> 5)];
+      if ((tw >> (loc & 31)) & 1u) {
+        const float dc = D[c];
+        float acc2 = 0.f;
+        const int nb6[6] = {c - 1, c + 1, c - HS, c + HS, c - HS * HS, c + HS * HS};
 #pragma unroll
-      for (int t = 0; t < 6; ++t) {
-        if (sh.F[nb6[t]] & 1) {
-          float e = dc - sh.D[nb6[t]];
-          acc2 = fmaf(e, e, acc2);
+        for (int t = 0; t < 6; ++t) {
+          if (S[nb6[t]]) {
+            const float e = dc - D[nb6[t]];
+            acc2 = fmaf(e, e, acc2);
+          }
         }
+        const float tv = sqrtf(acc2);
+        if (x >= 0 && y >= 0 && z >= 0 && x < 8 && y < 8 && z < 8) tsum += tv;
+        inv = tv > 0.f ? 1.0f / tv : 0.f;
       }
-      float tv = sqrtf(acc2);
-      if (x >= 0 && y >= 0 && z >= 0 && x < 8 && y < 8 && z < 8) tsum += tv;
-      inv = tv > 0.f ? 1.0f / tv : 0.f;
     }
     sh.inv[h] = inv;
   }
-  __syncthreads();
-  if (!GRAD) return 0.f;
-  int c = hidx(lx, ly, lz);
-  if (!(sh.F[c] & 1)) return 0.f;
-  float di = sh.D[c];
-  float own = sh.inv[iidx(lx, ly, lz)];
-  const int hn[6] = {hidx(lx - 1, ly, lz), hidx(lx + 1, ly, lz), hidx(lx, ly - 1, lz),
-                     hidx(lx, ly + 1, lz), hidx(lx, ly, lz - 1), hidx(lx, ly, lz + 1)};
-  const int in6[6] = {iidx(lx - 1, ly, lz), iidx(lx + 1, ly, lz), iidx(lx, ly - 1, lz),
-                      iidx(lx, ly + 1, lz), iidx(lx, ly, lz - 1), iidx(lx, ly, lz + 1)};
+}
+
+// dTV/dd of vertex l of the brick in buffer p (0 for padding).
+__device__ __forceinline__ float tv_gather(const TvShared& sh, int p, int l) {
+  const int lx = l & 7, ly = (l >> 3) & 7, lz = l >> 6;
+  const int c = hidx(lx, ly, lz);
+  const float* D = sh.D[p];
+  const uint8_t* S = sh.S[p];
+  if (!S[c]) return 0.f;
+  const float di = D[c];
+  const int ci = iidx(lx, ly, lz);
+  const float own = sh.inv[ci];
+  const int hn[6] = {c - 1, c + 1, c - HS, c + HS, c - HS * HS, c + HS * HS};
+  const int in6[6] = {ci - 1, ci + 1, ci - IS, ci + IS, ci - IS * IS, ci + IS * IS};
   float gsum = 0.f;
 #pragma unroll
   for (int t = 0; t < 6; ++t) {
-    if (!(sh.F[hn[t]] & 1)) continue;  // outside the grid or not stored
-    float e = di - sh.D[hn[t]];
+    if (!S[hn[t]]) continue;  // outside the grid or not stored
+    const float e = di - D[hn[t]];
     gsum += e * own + e * sh.inv[in6[t]];
   }
-  return tv_scale * gsum;
+  return gsum;
+}
+
+// The sweep over work items first, first + stride, ... < n of this block.
+// src.brick(i) gives item i's TvBrick.  out(i, g0, g1, tsum) is called by
+// every thread once per item, in order, with the unscaled dTV/dd of vertices
+// l and l + 256 and the thread's share of the item's sum of TV_i; it may
+// synchronise the block.
+template <class Src, class Out>
+__device__ __forceinline__ void tv_sweep(const Src& src, int64_t first, int64_t stride, int64_t n, TvShared& sh,
+                                         Out&& out) {
+  const int l = threadIdx.x;
+  if (first >= n) return;
+  if (l == 0) sh.bk[0] = src.brick(first);
+  __syncthreads();
+  if (l < 27) sh.slot[0][l] = __ldg(sh.bk[0].nbr + l);
+  __syncthreads();
+  tv_issue(sh, 0);
+  cp_async_commit();
+  if (first + stride < n) {
+    if (l == 0) sh.bk[1] = src.brick(first + stride);
+    __syncthreads();
+    if (l < 27) sh.slot[1][l] = __ldg(sh.bk[1].nbr + l);
+  }
+  int p = 0;
+  for (int64_t i = first; i < n; i += stride) {
+    __syncthreads();  // the previous item is done with buffer p ^ 1 and inv; bk / slot[p ^ 1] written
+    const int64_t next = i + stride, after = next + stride;
+    if (next < n) tv_issue(sh, p ^ 1);
+    cp_async_commit();
+    TvBrick ab;
+    if (l == 0 && after < n) ab = src.brick(after);
+    cp_async_wait1();  // this thread's copies of item i have landed
+    __syncthreads();   // ... and everyone's
+    float tsum = 0.f;
+    tv_inverse(sh, p, tsum);
+    if (l == 0 && after < n) sh.bk[p] = ab;  // item i's own TvBrick was last read by tv_issue
+    __syncthreads();  // inv ready, bk[p] published
+    int rs = -1;
+    if (l < 27 && after < n) rs = __ldg(sh.bk[p].nbr + l);
+    const float g0 = tv_gather(sh, p, l), g1 = tv_gather(sh, p, l + 256);
+    if (l < 27 && after < n) sh.slot[p][l] = rs;  // slot[p] was last read by tv_issue of item i
+    out(i, g0, g1, tsum);
+    p ^= 1;
+  }
+  cp_async_wait0();
 }
 
 // Adam (Kingma and Ba) on vertex `l` of brick `slot`, if it is trainable.

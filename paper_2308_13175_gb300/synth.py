@@ -106,6 +106,15 @@ class Primitive:
     def sample_surface(self, n: int, rng: np.random.Generator) -> np.ndarray:
         if self.kind in ("box", "cylinder"):
             return self._sample_flat(n, rng)
+        if self.kind == "superquadric":
+            # Its area element is too peaked for rejection: draw 3n parameter
+            # pairs and resample n of them in proportion to the area element.
+            eps = 1e-4
+            m = max(3 * n, 4096)
+            u, v = rng.random(m), rng.random(m)
+            dens = self._area_element(u, v, eps)
+            idx = rng.choice(m, size=n, p=dens / dens.sum())
+            return self._param(np.clip(u[idx], eps, 1 - eps), np.clip(v[idx], eps, 1 - eps)) @ self.rot.T + self.center
         out = []
         got = 0
         eps = 1e-4
@@ -156,6 +165,19 @@ class Primitive:
             p[part == 2, 2] = half_h
         return p @ self.rot.T + self.center
 
+    def bound(self) -> float:
+        """Radius of a ball around the centre that holds the whole primitive
+        (inside() is False beyond it); infinite when there is none."""
+        if self.kind == "ellipsoid":
+            return float(max(self.params))
+        if self.kind == "torus":
+            return float(self.params[0] + self.params[1])
+        if self.kind in ("box", "superquadric"):
+            return float(np.linalg.norm(self.params[:3]))
+        if self.kind == "cylinder":
+            return float(math.hypot(self.params[0], self.params[1]))
+        return math.inf
+
     def area(self, rng: np.random.Generator) -> float:
         if self.kind == "box":
             hx, hy, hz = self.params
@@ -183,7 +205,10 @@ def union_surface(prims: list, n: int, rng: np.random.Generator,
             keep = np.ones(len(pts), dtype=bool)
             for k, other in enumerate(prims):
                 if k != i and other.kind != "room":
-                    keep &= ~other.inside(pts)
+                    # Only points within the other primitive's bounding ball can lie inside it.
+                    near = np.flatnonzero(np.sum((pts - other.center) ** 2, axis=1) < other.bound() ** 2)
+                    if len(near):
+                        keep[near] &= ~other.inside(pts[near])
             chunks.append(pts[keep])
             got += int(keep.sum())
     pts = np.concatenate(chunks)
