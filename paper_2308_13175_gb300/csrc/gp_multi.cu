@@ -304,7 +304,7 @@ struct MultiTvSrc {
 // the block's tiles); the gradient is overwritten at every slot of every
 // brick; the TV sums go to each cloud's slot 3, one atomic per run of tiles of
 // the same cloud.
-__global__ void __launch_bounds__(TV_SWEEP_THREADS) k_m_tv(const MShape* __restrict__ shapes,
+__global__ void __launch_bounds__(TV_SWEEP_THREADS, TV_BLOCKS_PER_SM) k_m_tv(const MShape* __restrict__ shapes,
                                                            const MTile* __restrict__ tiles, int64_t ntiles,
                                                            float alpha, double* __restrict__ sums) {
   __shared__ TvShared sh;
@@ -365,18 +365,21 @@ __global__ void __launch_bounds__(256) k_m_query(const MShape* __restrict__ shap
 }
 
 // Adam on every active brick of every cloud, as step t + 1, learning rate
-// lr * decay^floor(t / every) (every = 0: constant).
-__global__ void __launch_bounds__(512) k_m_adam(const MShape* __restrict__ shapes, const MTile* __restrict__ tiles,
+// lr * decay^floor(t / every) (every = 0: constant); one thread per 4
+// consecutive vertices (128 per active-brick tile).
+__global__ void __launch_bounds__(256) k_m_adam(const MShape* __restrict__ shapes, const MTile* __restrict__ tiles,
                                                 int64_t ntiles, const int64_t* __restrict__ t_dev, float lr,
                                                 float decay, int64_t every, float b1, float b2, float eps) {
   const int64_t t = *t_dev;
   const float bc1 = (float)(1.0 - pow((double)b1, (double)(t + 1)));
   const float bc2 = (float)(1.0 - pow((double)b2, (double)(t + 1)));
   const float lr_t = every > 0 ? (float)((double)lr * pow((double)decay, (double)(t / every))) : lr;
-  for (int64_t ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
-    const MTile tl = tiles[ti];
+  const int64_t n = ntiles * 128;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const MTile tl = tiles[i >> 7];
     const MShape& S = shapes[tl.shape];
-    adam_vertex(S.active[tl.first], threadIdx.x, S.G.masks, S.grad, S.D, S.m, S.v, lr_t, b1, b2, eps, bc1, bc2);
+    adam_quad(__ldg(S.active + tl.first), (int)(i & 127), S.G.masks, S.grad, S.D, S.m, S.v, lr_t, b1, b2, eps,
+              bc1, bc2);
   }
 }
 
@@ -423,7 +426,7 @@ struct gp_multi {
   std::vector<int64_t> B, rec_off, grad_off;
   int64_t total_B = 0, V_total = 0, J_total = 0;
   int tq = 256;                    // records per tile = block size of the record kernels
-  int bpsm[ST_TUNED] = {4, 2, 4};  // persistent blocks per SM of the tuned stages
+  int bpsm[ST_TUNED] = {4, TV_BLOCKS_PER_SM, 4};  // persistent blocks per SM of the tuned stages
   MShape* shapes = nullptr;
   MTile *rec_tiles = nullptr, *pt_tiles = nullptr, *brick_tiles = nullptr, *active_tiles = nullptr;
   int64_t n_rec_tiles = 0, n_pt_tiles = 0, n_brick_tiles = 0, n_active_tiles = 0;
@@ -528,7 +531,7 @@ gp_status launch_adam_finish(gp_multi* m, const gp_loss_w* w, const gp_adam* hp,
   cudaStream_t s = ctx->stream;
   if (m->n_active_tiles > 0)
     GP_KERNEL(ctx, "k_m_adam",
-              k_m_adam<<<persistent_grid(m, 4, m->n_active_tiles), 512, 0, s>>>(
+              k_m_adam<<<persistent_grid(m, 8, m->n_active_tiles * 128 / 256 + 1), 256, 0, s>>>(
                   m->shapes, m->active_tiles, m->n_active_tiles, m->t, hp->lr, decay, every, hp->beta1, hp->beta2,
                   hp->eps));
   GP_KERNEL(ctx, "k_m_finish",
@@ -735,7 +738,12 @@ extern "C" gp_status gp_multi_autotune(gp_multi* m, const gp_loss_w* w) {
   for (int stage : {ST_NN, ST_TV, ST_QUERY}) {
     int best_b = m->bpsm[stage];
     float bm = INFINITY;
-    for (int c : {1, 2, 4, 8, 16}) {
+    const int tv_c[3] = {TV_BLOCKS_PER_SM, 2 * TV_BLOCKS_PER_SM, 3 * TV_BLOCKS_PER_SM};
+    const int gen_c[5] = {1, 2, 4, 8, 16};
+    const int* cand = stage == ST_TV ? tv_c : gen_c;
+    const int ncand = stage == ST_TV ? 3 : 5;
+    for (int ci = 0; ci < ncand; ++ci) {
+      const int c = cand[ci];
       if (st) break;
       m->bpsm[stage] = c;
       float ms = INFINITY;

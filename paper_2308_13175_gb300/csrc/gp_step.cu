@@ -164,7 +164,7 @@ struct BandTvSrc {
 };
 
 template <bool DET, bool GRAD, bool TV, bool LAST>
-__global__ void __launch_bounds__(TV_THREADS) k_tv(Grid G, const int32_t* __restrict__ coord,
+__global__ void __launch_bounds__(TV_THREADS, TV_BLOCKS_PER_SM) k_tv(Grid G, const int32_t* __restrict__ coord,
                                                    const int32_t* __restrict__ nbrs, int64_t n_bricks,
                                                    float tv_scale, float* __restrict__ grad,
                                                    unsigned long long* __restrict__ acc,
@@ -216,12 +216,14 @@ __global__ void __launch_bounds__(TV_THREADS) k_tv(Grid G, const int32_t* __rest
   (void)err;
 }
 
-__global__ void __launch_bounds__(512) k_adam(const int32_t* __restrict__ active, int64_t n_active,
+// One thread per 4 consecutive vertices of an active brick (128 per brick).
+__global__ void __launch_bounds__(256) k_adam(const int32_t* __restrict__ active, int64_t n_active,
                                               const uint32_t* __restrict__ masks, const float* __restrict__ grad,
                                               float* __restrict__ D, float* __restrict__ m, float* __restrict__ v,
                                               float lr, float b1, float b2, float eps, float bc1, float bc2) {
-  for (int64_t a = blockIdx.x; a < n_active; a += gridDim.x)
-    adam_vertex(active[a], threadIdx.x, masks, grad, D, m, v, lr, b1, b2, eps, bc1, bc2);
+  const int64_t n = n_active * 128;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    adam_quad(__ldg(active + (i >> 7)), (int)(i & 127), masks, grad, D, m, v, lr, b1, b2, eps, bc1, bc2);
 }
 
 unsigned q_grid(const gp_ctx* ctx, int64_t B) {
@@ -229,7 +231,7 @@ unsigned q_grid(const gp_ctx* ctx, int64_t B) {
 }
 
 unsigned tv_grid(const gp_ctx* ctx, int64_t n_bricks) {
-  int64_t cap = (int64_t)ctx->num_sms * 8;
+  int64_t cap = (int64_t)ctx->num_sms * TV_BLOCKS_PER_SM;  // persistent: one wave
   if (cap > GP_MAX_PARTIAL_BLOCKS) cap = GP_MAX_PARTIAL_BLOCKS;
   return gp_blocks(n_bricks, 1, cap);
 }
@@ -344,8 +346,8 @@ extern "C" gp_status gp_update(gp_band* b, const float* grad_dev, const gp_adam*
   if (b->n_active == 0) return GP_OK;
   double bc1 = 1.0 - std::pow((double)hp->beta1, (double)step);
   double bc2 = 1.0 - std::pow((double)hp->beta2, (double)step);
-  int64_t cap = (int64_t)ctx->num_sms * 4;
-  GP_KERNEL(ctx, "k_adam", k_adam<<<gp_blocks(b->n_active, 1, cap), 512, 0, ctx->stream>>>(b->active, b->n_active, b->masks, grad_dev, b->D,
+  int64_t cap = (int64_t)ctx->num_sms * 8;
+  GP_KERNEL(ctx, "k_adam", k_adam<<<gp_blocks(b->n_active * 128, 256, cap), 256, 0, ctx->stream>>>(b->active, b->n_active, b->masks, grad_dev, b->D,
                                                                   b->m, b->v, hp->lr, hp->beta1, hp->beta2, hp->eps,
                                                                   (float)bc1, (float)bc2));
   return GP_OK;

@@ -180,15 +180,22 @@ __device__ __forceinline__ int iidx(int x, int y, int z) { return ((z + 1) * IS 
 // neighbour bricks in shared memory, compute 1/TV_n on the brick plus a
 // one-vertex halo (10^3), then gather every vertex's
 //   dTV/dd_i = [i in T] sum_n (d_i - d_n) / TV_i + sum_{n in T} (d_i - d_n) / TV_n
-// over the stored in-grid axis neighbours n.  Each TV_i enters the sum once,
-// from the brick that stores i.
+// over the in-grid axis neighbours n.  Each TV_i enters the sum once, from the
+// brick that stores i.
 //
-// Pipeline: the halo of the next brick is copied by cp.async (zero-filled
-// where absent) into the other of two buffers while the current brick is
-// computed; the neighbour slots of the brick after that are fetched in two
-// steps spread over the current brick's phases.  No halo value is held in
-// registers, so several blocks fit on an SM.
+// The band stores every in-grid axis neighbour of a T vertex, so a value the
+// sums use is always present: absent bricks are staged as zeros and only the
+// grid boundary needs checks (bricks within two vertices of it take a checked
+// path).  Staging copies rows: each halo row (fixed y, z) is four cp.async
+// pieces (x = -2..-1 from the brick below in x, 0..3 and 4..7 from the centre
+// column, 8..9 from the brick above), into rows padded to 16 floats.  The next
+// brick's halo is copied into the other of two buffers while the current one
+// is computed; the neighbour slots of the brick after that are fetched in two
+// steps spread over the current brick's phases.
 constexpr int TV_SWEEP_THREADS = 256;
+constexpr int TV_BLOCKS_PER_SM = 5;  // resident blocks per SM at the register cap below (48 per thread)
+constexpr int TV_ROW = 20;        // floats per staged row: x = -2..9 at columns 2..13 (20: fewer bank conflicts)
+constexpr int TV_ROWS = HS * HS;  // 144 rows: y, z = -2..9
 
 // Brick b as the sweep sees it: values, masks, its row of the 27-neighbour
 // table (3x3x3, x fastest, -1 absent), grid size and origin vertex.
@@ -200,97 +207,165 @@ struct TvBrick {
 };
 
 struct TvShared {
-  float D[2][HN];          // staged values (0 where not stored)
-  uint32_t T[2][27 * 16];  // T-mask words of the 27 neighbour bricks (0 where absent)
-  uint8_t S[2][HN];        // 1: stored and inside [0, R]^3
-  float inv[IN];           // 1/TV of T vertices of the inner region, else 0
+  __align__(16) float D[2][TV_ROWS * TV_ROW];   // staged values (0 in absent bricks)
+  __align__(16) uint32_t T[2][27 * 16];         // T-mask words of the 27 neighbour bricks (0 if absent)
+  float inv[IN];                                // 1/TV of T vertices of the inner region, else 0
   int slot[2][27];
   TvBrick bk[2];
 };
 
-__device__ __forceinline__ void cp_async4(void* smem, const void* gmem, int src_bytes) {
+__device__ __forceinline__ int tv_hc(int x, int y, int z) { return ((z + 2) * HS + (y + 2)) * TV_ROW + (x + 4); }
+
+__device__ __forceinline__ void cp_async_ca8(void* smem, const void* gmem, int src_bytes) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(gmem), "r"(src_bytes) : "memory");
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(sa), "l"(gmem), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_cg16(void* smem, const void* gmem, int src_bytes) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(src_bytes) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
-// Neighbour-brick index (0..26) of halo offset (hx, hy, hz), each in [-2, 9].
-__device__ __forceinline__ int tv_region(int hx, int hy, int hz) {
-  return ((hz >> 3) + 1) * 9 + ((hy >> 3) + 1) * 3 + ((hx >> 3) + 1);
+// This thread's fixed share of every brick's work, decoded once: its row
+// pieces to copy and its inner-region entries.
+constexpr int TV_TASKS = (TV_ROWS * 4 + TV_SWEEP_THREADS - 1) / TV_SWEEP_THREADS;  // 3
+constexpr int TV_INNER = (IN + TV_SWEEP_THREADS - 1) / TV_SWEEP_THREADS;          // 4
+struct TvPlan {
+  uint32_t task[TV_TASKS];   // region | local << 5 | destination << 14 | 16-byte piece << 26 | valid << 27
+  uint32_t entry[TV_INNER];  // halo index | region << 12 | local << 17 | inner << 26 | valid << 27
+};
+
+__device__ __forceinline__ TvPlan tv_plan() {
+  TvPlan pl;
+#pragma unroll
+  for (int k = 0; k < TV_TASKS; ++k) {
+    const int r = threadIdx.x + k * TV_SWEEP_THREADS;
+    pl.task[k] = 0;
+    if (r >= TV_ROWS * 4) continue;
+    const int row = r >> 2, seg = r & 3;
+    const int hy = row % HS - 2, hz = row / HS - 2;
+    const int dx = seg == 0 ? 0 : (seg == 3 ? 2 : 1);  // brick column: below / centre / above
+    const int lx0 = seg == 0 ? 6 : (seg == 2 ? 4 : 0);
+    const int col = seg == 0 ? 2 : (seg == 1 ? 4 : (seg == 2 ? 8 : 12));
+    const uint32_t reg = ((hz >> 3) + 1) * 9 + ((hy >> 3) + 1) * 3 + dx;
+    const uint32_t loc = ((hz & 7) << 6) | ((hy & 7) << 3) | lx0;
+    const uint32_t dst = row * TV_ROW + col;
+    const uint32_t big = (seg == 1 || seg == 2) ? 1u : 0u;
+    pl.task[k] = reg | (loc << 5) | (dst << 14) | (big << 26) | (1u << 27);
+  }
+#pragma unroll
+  for (int k = 0; k < TV_INNER; ++k) {
+    const int h = threadIdx.x + k * TV_SWEEP_THREADS;
+    pl.entry[k] = 0;
+    if (h >= IN) continue;
+    const int x = h % IS - 1, y = (h / IS) % IS - 1, z = h / (IS * IS) - 1;
+    const uint32_t reg = ((z >> 3) + 1) * 9 + ((y >> 3) + 1) * 3 + ((x >> 3) + 1);
+    const uint32_t loc = ((z & 7) << 6) | ((y & 7) << 3) | (x & 7);
+    const uint32_t inner = (x >= 0 && y >= 0 && z >= 0 && x < 8 && y < 8 && z < 8) ? 1u : 0u;
+    pl.entry[k] = (uint32_t)tv_hc(x, y, z) | (reg << 12) | (loc << 17) | (inner << 26) | (1u << 27);
+  }
+  return pl;
 }
 
-// Issue the copies of brick bk[q]'s halo and neighbour T masks into buffer q
-// and write its stored flags (plain stores).
-__device__ __forceinline__ void tv_issue(TvShared& sh, int q) {
-  const TvBrick bk = sh.bk[q];
-  for (int h = threadIdx.x; h < HN; h += TV_SWEEP_THREADS) {
-    const int hx = h % HS - 2, hy = (h / HS) % HS - 2, hz = h / (HS * HS) - 2;
-    const int i = bk.ox + hx, j = bk.oy + hy, k = bk.oz + hz;
-    const int sl = sh.slot[q][tv_region(hx, hy, hz)];
-    const bool ok = sl >= 0 && i <= bk.R && j <= bk.R && k <= bk.R;  // negative i lies in an absent brick
-    const float* src = ok ? bk.D + (int64_t)sl * 512 + gp_local(i, j, k) : bk.D;
-    cp_async4(&sh.D[q][h], src, ok ? 4 : 0);
-    sh.S[q][h] = ok ? 1 : 0;
+// Issue the copies of brick bk[q]'s halo rows and neighbour T masks into
+// buffer q (zero-filled where the brick is absent).
+__device__ __forceinline__ void tv_issue(TvShared& sh, int q, const TvPlan& pl) {
+  const float* D = sh.bk[q].D;
+#pragma unroll
+  for (int k = 0; k < TV_TASKS; ++k) {
+    const uint32_t t = pl.task[k];
+    if (!(t >> 27)) continue;
+    const int sl = sh.slot[q][t & 31];
+    const float* src = sl >= 0 ? D + (size_t)sl * 512u + ((t >> 5) & 511) : D;
+    float* dst = &sh.D[q][(t >> 14) & 4095];
+    if ((t >> 26) & 1)
+      cp_async_cg16(dst, src, sl >= 0 ? 16 : 0);
+    else
+      cp_async_ca8(dst, src, sl >= 0 ? 8 : 0);
   }
-  for (int w = threadIdx.x; w < 27 * 16; w += TV_SWEEP_THREADS) {
-    const int sl = sh.slot[q][w >> 4];
-    const uint32_t* src = sl >= 0 ? bk.masks + (int64_t)sl * 48 + (w & 15) : bk.masks;
-    cp_async4(&sh.T[q][w], src, sl >= 0 ? 4 : 0);
+  if (threadIdx.x < 27 * 4) {
+    const int w = threadIdx.x;
+    const int sl = sh.slot[q][w >> 2];
+    const uint32_t* masks = sh.bk[q].masks;
+    const uint32_t* src = sl >= 0 ? masks + (size_t)sl * 48u + 4u * (w & 3) : masks;
+    cp_async_cg16(&sh.T[q][4 * w], src, sl >= 0 ? 16 : 0);
   }
+}
+
+// Is every vertex of the halo inside [0, R]^3?
+__device__ __forceinline__ bool tv_interior(const TvBrick& bk) {
+  return bk.ox >= 2 && bk.oy >= 2 && bk.oz >= 2 && bk.ox + 9 <= bk.R && bk.oy + 9 <= bk.R && bk.oz + 9 <= bk.R;
 }
 
 // 1/TV over the inner region of buffer p; adds this thread's share of the
-// brick's own TV_i to tsum.
-__device__ __forceinline__ void tv_inverse(TvShared& sh, int p, float& tsum) {
+// brick's own TV_i to tsum.  CHECK: skip out-of-grid neighbours.
+template <bool CHECK>
+__device__ __forceinline__ void tv_inverse(TvShared& sh, int p, const TvBrick& bk, const TvPlan& pl, float& tsum) {
   const float* D = sh.D[p];
-  const uint8_t* S = sh.S[p];
-  for (int h = threadIdx.x; h < IN; h += TV_SWEEP_THREADS) {
-    const int x = h % IS - 1, y = (h / IS) % IS - 1, z = h / (IS * IS) - 1;
-    const int c = hidx(x, y, z);
-    float inv = 0.f;
-    if (S[c]) {
-      const int loc = ((z & 7) << 6) | ((y & 7) << 3) | (x & 7);
-      const uint32_t tw = sh.T[p][tv_region(x, y, z) * 16 + (loc >> 5)];
-      if ((tw >> (loc & 31)) & 1u) {
-        const float dc = D[c];
-        float acc2 = 0.f;
-        const int nb6[6] = {c - 1, c + 1, c - HS, c + HS, c - HS * HS, c + HS * HS};
+  const uint32_t* T = sh.T[p];
 #pragma unroll
-        for (int t = 0; t < 6; ++t) {
-          if (S[nb6[t]]) {
-            const float e = dc - D[nb6[t]];
-            acc2 = fmaf(e, e, acc2);
-          }
-        }
-        const float tv = sqrtf(acc2);
-        if (x >= 0 && y >= 0 && z >= 0 && x < 8 && y < 8 && z < 8) tsum += tv;
-        inv = tv > 0.f ? 1.0f / tv : 0.f;
+  for (int k = 0; k < TV_INNER; ++k) {
+    const uint32_t e = pl.entry[k];
+    if (!(e >> 27)) continue;
+    const int h = threadIdx.x + k * TV_SWEEP_THREADS;
+    const int c = e & 4095, reg = (e >> 12) & 31, loc = (e >> 17) & 511;
+    float inv = 0.f;
+    if ((T[reg * 16 + (loc >> 5)] >> (loc & 31)) & 1u) {
+      const float dc = D[c];
+      const int nb6[6] = {c - 1, c + 1, c - TV_ROW, c + TV_ROW, c - TV_ROW * HS, c + TV_ROW * HS};
+      bool ok[6] = {true, true, true, true, true, true};
+      if (CHECK) {
+        const int x = h % IS - 1 + bk.ox, y = (h / IS) % IS - 1 + bk.oy, z = h / (IS * IS) - 1 + bk.oz;
+        ok[0] = x > 0;
+        ok[1] = x < bk.R;
+        ok[2] = y > 0;
+        ok[3] = y < bk.R;
+        ok[4] = z > 0;
+        ok[5] = z < bk.R;
       }
+      float acc2 = 0.f;
+#pragma unroll
+      for (int t = 0; t < 6; ++t) {
+        const float d = dc - D[nb6[t]];
+        if (ok[t]) acc2 = fmaf(d, d, acc2);
+      }
+      inv = acc2 > 0.f ? rsqrtf(acc2) : 0.f;  // 1/TV_n
+      if ((e >> 26) & 1) tsum += acc2 * inv;  // TV_n
     }
     sh.inv[h] = inv;
   }
 }
 
-// dTV/dd of vertex l of the brick in buffer p (0 for padding).
-__device__ __forceinline__ float tv_gather(const TvShared& sh, int p, int l) {
+// dTV/dd of vertex l of the brick in buffer p (0 outside the grid).
+template <bool CHECK>
+__device__ __forceinline__ float tv_gather(const TvShared& sh, int p, const TvBrick& bk, int l) {
   const int lx = l & 7, ly = (l >> 3) & 7, lz = l >> 6;
-  const int c = hidx(lx, ly, lz);
+  bool ok[6] = {true, true, true, true, true, true};
+  if (CHECK) {
+    const int x = bk.ox + lx, y = bk.oy + ly, z = bk.oz + lz;
+    if (x > bk.R || y > bk.R || z > bk.R) return 0.f;  // padding slot
+    ok[0] = x > 0;
+    ok[1] = x < bk.R;
+    ok[2] = y > 0;
+    ok[3] = y < bk.R;
+    ok[4] = z > 0;
+    ok[5] = z < bk.R;
+  }
   const float* D = sh.D[p];
-  const uint8_t* S = sh.S[p];
-  if (!S[c]) return 0.f;
+  const int c = tv_hc(lx, ly, lz);
   const float di = D[c];
   const int ci = iidx(lx, ly, lz);
   const float own = sh.inv[ci];
-  const int hn[6] = {c - 1, c + 1, c - HS, c + HS, c - HS * HS, c + HS * HS};
+  const int hn[6] = {c - 1, c + 1, c - TV_ROW, c + TV_ROW, c - TV_ROW * HS, c + TV_ROW * HS};
   const int in6[6] = {ci - 1, ci + 1, ci - IS, ci + IS, ci - IS * IS, ci + IS * IS};
   float gsum = 0.f;
 #pragma unroll
   for (int t = 0; t < 6; ++t) {
-    if (!S[hn[t]]) continue;  // outside the grid or not stored
-    const float e = di - D[hn[t]];
-    gsum += e * own + e * sh.inv[in6[t]];
+    // own != 0 only for i in T, whose in-grid neighbours are all stored;
+    // inv[n] != 0 only for n in T (inside the grid and stored).
+    if (ok[t]) gsum = fmaf(di - D[hn[t]], own + sh.inv[in6[t]], gsum);
   }
   return gsum;
 }
@@ -305,11 +380,12 @@ __device__ __forceinline__ void tv_sweep(const Src& src, int64_t first, int64_t 
                                          Out&& out) {
   const int l = threadIdx.x;
   if (first >= n) return;
+  const TvPlan pl = tv_plan();
   if (l == 0) sh.bk[0] = src.brick(first);
   __syncthreads();
   if (l < 27) sh.slot[0][l] = __ldg(sh.bk[0].nbr + l);
   __syncthreads();
-  tv_issue(sh, 0);
+  tv_issue(sh, 0, pl);
   cp_async_commit();
   if (first + stride < n) {
     if (l == 0) sh.bk[1] = src.brick(first + stride);
@@ -320,38 +396,68 @@ __device__ __forceinline__ void tv_sweep(const Src& src, int64_t first, int64_t 
   for (int64_t i = first; i < n; i += stride) {
     __syncthreads();  // the previous item is done with buffer p ^ 1 and inv; bk / slot[p ^ 1] written
     const int64_t next = i + stride, after = next + stride;
-    if (next < n) tv_issue(sh, p ^ 1);
+    if (next < n) tv_issue(sh, p ^ 1, pl);
     cp_async_commit();
     TvBrick ab;
-    if (l == 0 && after < n) ab = src.brick(after);
+    if (l < 27 && after < n) ab = src.brick(after);  // warp 0: one broadcast load per field
+    const TvBrick bk = sh.bk[p];
+    const bool check = !tv_interior(bk);
     cp_async_wait1();  // this thread's copies of item i have landed
     __syncthreads();   // ... and everyone's
     float tsum = 0.f;
-    tv_inverse(sh, p, tsum);
-    if (l == 0 && after < n) sh.bk[p] = ab;  // item i's own TvBrick was last read by tv_issue
-    __syncthreads();  // inv ready, bk[p] published
+    if (check)
+      tv_inverse<true>(sh, p, bk, pl, tsum);
+    else
+      tv_inverse<false>(sh, p, bk, pl, tsum);
+    __syncthreads();  // inv ready; bk[p] and slot[p] are free
+    if (l == 0 && after < n) sh.bk[p] = ab;
     int rs = -1;
-    if (l < 27 && after < n) rs = __ldg(sh.bk[p].nbr + l);
-    const float g0 = tv_gather(sh, p, l), g1 = tv_gather(sh, p, l + 256);
-    if (l < 27 && after < n) sh.slot[p][l] = rs;  // slot[p] was last read by tv_issue of item i
+    if (l < 27 && after < n) rs = __ldg(ab.nbr + l);
+    float g0, g1;
+    if (check) {
+      g0 = tv_gather<true>(sh, p, bk, l);
+      g1 = tv_gather<true>(sh, p, bk, l + 256);
+    } else {
+      g0 = tv_gather<false>(sh, p, bk, l);
+      g1 = tv_gather<false>(sh, p, bk, l + 256);
+    }
+    if (l < 27 && after < n) sh.slot[p][l] = rs;
     out(i, g0, g1, tsum);
     p ^= 1;
   }
   cp_async_wait0();
 }
 
-// Adam (Kingma and Ba) on vertex `l` of brick `slot`, if it is trainable.
-__device__ __forceinline__ void adam_vertex(int slot, int l, const uint32_t* __restrict__ masks,
-                                            const float* __restrict__ grad, float* __restrict__ D,
-                                            float* __restrict__ m, float* __restrict__ v, float lr, float b1, float b2,
-                                            float eps, float bc1, float bc2) {
-  if (!gp_mask_bit(masks, slot, 1, l)) return;
-  int64_t addr = (int64_t)slot * 512 + l;
-  float g = grad[addr];
-  float mm = fmaf(b1, m[addr], (1.0f - b1) * g);
-  float vv = fmaf(b2, v[addr], (1.0f - b2) * g * g);
-  m[addr] = mm;
-  v[addr] = vv;
-  float mh = mm / bc1, vh = vv / bc2;
-  D[addr] -= lr * mh / (sqrtf(vh) + eps);
+// Adam (Kingma and Ba) on the trainable vertices among 4q .. 4q + 3 of brick
+// `slot` (q in [0, 128)): one 16-byte load and store per array.  Vertices of
+// the quad that are not trainable are written back unchanged.
+__device__ __forceinline__ void adam_quad(int slot, int q, const uint32_t* __restrict__ masks,
+                                          const float* __restrict__ grad, float* __restrict__ D,
+                                          float* __restrict__ m, float* __restrict__ v, float lr, float b1, float b2,
+                                          float eps, float bc1, float bc2) {
+  const uint32_t bits = (__ldg(masks + (int64_t)slot * 48 + 16 + (q >> 3)) >> ((4 * q) & 31)) & 15u;
+  if (!bits) return;
+  const int64_t a = (int64_t)slot * 512 + 4 * q;
+  const float4 g4 = __ldg(reinterpret_cast<const float4*>(grad + a));
+  float4 m4 = *reinterpret_cast<const float4*>(m + a);
+  float4 v4 = *reinterpret_cast<const float4*>(v + a);
+  float4 d4 = *reinterpret_cast<const float4*>(D + a);
+  float* gp = reinterpret_cast<float*>(const_cast<float4*>(&g4));
+  float* mp = reinterpret_cast<float*>(&m4);
+  float* vp = reinterpret_cast<float*>(&v4);
+  float* dp = reinterpret_cast<float*>(&d4);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    if (!((bits >> k) & 1u)) continue;
+    const float g = gp[k];
+    const float mm = fmaf(b1, mp[k], (1.0f - b1) * g);
+    const float vv = fmaf(b2, vp[k], (1.0f - b2) * g * g);
+    mp[k] = mm;
+    vp[k] = vv;
+    const float mh = mm / bc1, vh = vv / bc2;
+    dp[k] -= lr * mh / (sqrtf(vh) + eps);
+  }
+  *reinterpret_cast<float4*>(m + a) = m4;
+  *reinterpret_cast<float4*>(v + a) = v4;
+  *reinterpret_cast<float4*>(D + a) = d4;
 }

@@ -181,8 +181,9 @@ def test_multi_autotune_keeps_state_and_graph_replay_matches_eager(gb, ctx, clou
     d_before = [export_band(b)[1].copy() for b in bands]
     info = gb.gp_multi_autotune(multi, W)
     assert info["records_per_tile"] in (128, 256, 512)
-    for key in ("blocks_per_sm_nn", "blocks_per_sm_tv", "blocks_per_sm_query"):
+    for key in ("blocks_per_sm_nn", "blocks_per_sm_query"):
         assert info[key] in (1, 2, 4, 8, 16)
+    assert info["blocks_per_sm_tv"] in (5, 10, 15)
     assert info["step"] == 0 and info["error_bits"] == 0
     for b, d0 in zip(bands, d_before):
         assert np.array_equal(export_band(b)[1], d0)
