@@ -361,9 +361,10 @@ struct Cells {
   int slot_q, slot_s;
 };
 
-// Validity of a record (Sec. 3 pull band; readings in the header): q inside
-// the domain, cell(q) and cell(s) in the M1 band.
-__device__ __forceinline__ bool classify(const Grid& G, const float q[3], const float s[3], Cells& C) {
+// The arithmetic half of classify(): q inside the domain, s finite; the cells
+// and local coordinates of q and s (cell(s) clamped to the grid, its local
+// coordinate extended accordingly).
+__device__ __forceinline__ bool classify_cells(const Grid& G, const float q[3], const float s[3], Cells& C) {
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     gp_cell1 g = gp_cell_exact(q[a], G.half_r);
@@ -376,6 +377,13 @@ __device__ __forceinline__ bool classify(const Grid& G, const float q[3], const 
     C.cs[a] = cc;
     C.ts[a] = h.t + (float)(h.c - cc);
   }
+  return true;
+}
+
+// Validity of a record (Sec. 3 pull band; readings in the header): q inside
+// the domain, cell(q) and cell(s) in the M1 band.
+__device__ __forceinline__ bool classify(const Grid& G, const float q[3], const float s[3], Cells& C) {
+  if (!classify_cells(G, q, s, C)) return false;
   C.slot_q = gp_brick_slot(G.table, G.nb, C.cq[0], C.cq[1], C.cq[2]);
   if (C.slot_q < 0 || !gp_mask_bit(G.masks, C.slot_q, 2, gp_local(C.cq[0], C.cq[1], C.cq[2]))) return false;
   C.slot_s = gp_brick_slot(G.table, G.nb, C.cs[0], C.cs[1], C.cs[2]);

@@ -127,7 +127,7 @@ __device__ __forceinline__ void block_store3(double* __restrict__ partials, floa
 }
 
 template <bool DET, bool GRAD, bool LAST>
-__global__ void __launch_bounds__(Q_THREADS, 4) k_query(Grid G, const float* __restrict__ rec, int64_t B,
+__global__ void __launch_bounds__(Q_THREADS, 3) k_query(Grid G, const float* __restrict__ rec, int64_t B,
                                                      const int32_t* __restrict__ bv, float beta, float gamma,
                                                      float* __restrict__ grad, unsigned long long* __restrict__ acc,
                                                      double* __restrict__ partials, int32_t* __restrict__ err,

@@ -107,17 +107,29 @@ __device__ __forceinline__ void scatter8(const Grid& G, float* __restrict__ grad
 // One step record: classify it, evaluate Eq. 3 at q and at s, add its loss
 // terms to sp / sg / ss and (GRAD) scatter its gradient to the 8 + 8 corners,
 // scaled by w (1/B_v; 1 for the fixed-point sums, scaled at the end).
+//
+// The validity test is the one of classify(), with its memory reads arranged
+// for latency: both brick slots are read together, then both pull-mask words
+// and all 16 corner values together (the corners of a record that turns out
+// invalid are read for nothing).
 template <bool DET, bool GRAD>
 __device__ __forceinline__ bool query_record(const Grid& G, const float q[3], const float s[3], float w, float beta,
                                              float gamma, float* __restrict__ grad,
                                              unsigned long long* __restrict__ acc, int32_t* __restrict__ err,
                                              float& sp, float& sg, float& ss) {
   Cells C;
-  if (!classify(G, q, s, C)) return false;
+  if (!classify_cells(G, q, s, C)) return false;
+  C.slot_q = gp_brick_slot(G.table, G.nb, C.cq[0], C.cq[1], C.cq[2]);
+  C.slot_s = gp_brick_slot(G.table, G.nb, C.cs[0], C.cs[1], C.cs[2]);
+  if (C.slot_q < 0 || C.slot_s < 0) return false;
+  const int lq = gp_local(C.cq[0], C.cq[1], C.cq[2]), ls = gp_local(C.cs[0], C.cs[1], C.cs[2]);
+  const uint32_t wq = __ldg(G.masks + (int64_t)C.slot_q * 48 + 32 + (lq >> 5));
+  const uint32_t ws = __ldg(G.masks + (int64_t)C.slot_s * 48 + 32 + (ls >> 5));
   bool ok = true;
   float dq[8], ds[8];
   load_corners(G, C.cq, C.slot_q, dq, ok);
   load_corners(G, C.cs, C.slot_s, ds, ok);
+  if (!((wq >> (lq & 31)) & 1u) || !((ws >> (ls & 31)) & 1u)) return false;
   if (!ok) {
     atomicOr(err, GP_EF_RANGE);
     return false;
