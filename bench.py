@@ -82,6 +82,22 @@ def alg_bytes(name, n, J, Vs, Vt):
 KERNEL_BOUND = {"k_nn": "hbm", "k_tv": "hbm", "k_query": "hbm", "k_adam": "hbm", "k_sample": "hbm"}
 
 
+def fwd_bwd_adam(per_kernel: dict, names, queries_per_step: float, V_trainable: int, peak: float) -> dict:
+    """The forward + backward + Adam part of the step alone (gp_step +
+    gp_update: the L_TV sweep, the fused query kernel, Adam), from the traced
+    per-kernel times: its query rate and its roofline against the algorithmic
+    bytes 24 B + 36 V_trainable per step (the record; D read and gradient write
+    plus Adam's 7 accesses per trainable vertex)."""
+    t_us = sum(per_kernel[n]["avg_us"] * per_kernel[n]["launches"] for n in names if n in per_kernel)
+    steps = max(per_kernel[n]["launches"] for n in names if n in per_kernel)
+    t_us /= steps
+    by = 24.0 * queries_per_step + 36.0 * V_trainable
+    gbs = by / (t_us * 1e-6) / 1e9
+    return {"value": queries_per_step / (t_us * 1e-6), "unit": UNIT, "us_per_step": round(t_us, 2),
+            "kernels": [n for n in names if n in per_kernel], "alg_bytes_per_step": int(by),
+            "achieved_gbs": round(gbs, 1), "peak_gbs": peak, "frac": round(gbs / peak, 4)}
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -162,24 +178,29 @@ def barrier(world):
         dist.barrier()
 
 
-def reduce_max(x: float, world: int) -> float:
+def _reduce(x: float, world: int, op: str) -> float:
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
     return float(t.item())
+
+
+def reduce_max(x: float, world: int) -> float:
+    return _reduce(x, world, "max")
 
 
 def reduce_sum(x: float, world: int) -> float:
-    if world == 1:
-        return x
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
-    return float(t.item())
+    return _reduce(x, world, "sum")
+
+
+def replica_rate(units: float, ms: float, world: int) -> float:
+    """Whole-job rate of N independent replicas: the units every rank
+    processed over the slowest rank's time (weak scaling)."""
+    return reduce_sum(float(units), world) / (reduce_max(float(ms), world) / 1e3)
 
 
 # -------------------------------------------------- oracle CPU baseline
@@ -331,6 +352,7 @@ def run_ours(args, world, rank, local):
         per_kernel[name] = {"launches": cnt, "avg_us": round(1e3 * avg_ms, 2),
                             "share": round(tot / max(sum(v[1] for v in kern.values()), 1e-12), 4),
                             "alg_bytes": int(by), "gbs": round(by / (avg_ms / 1e3) / 1e9, 1) if by else None}
+    fba = fwd_bwd_adam(per_kernel, ("k_count_valid", "k_tv", "k_query", "k_adam"), q_prof / args.steps, Vt, peak)
     dom = max(kern.items(), key=lambda kv: kv[1][1])[0]
     dk = per_kernel[dom]
     achieved = dk["gbs"] or 0.0
@@ -426,7 +448,8 @@ def run_ours(args, world, rank, local):
                           else "float atomics"},
                "roofline": roofline, "cpu_baseline": cpu,
                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 12 * B, "d2h_bytes_per_step": 32},
-               "gpu_launches": int(launches), "clocks": clk, "kernels": per_kernel, "torch_autograd": torch_cmp,
+               "gpu_launches": int(launches), "clocks": clk, "kernels": per_kernel, "fwd_bwd_adam": fba,
+               "torch_autograd": torch_cmp,
                "loss_last": loss_final}
         print(json.dumps(out), flush=True)
     gb.gp_band_check(band)
@@ -530,6 +553,7 @@ def run_collection(args, world, rank, local):
         avg_ms = tot / cnt
         per_kernel[name] = {"launches": cnt, "avg_us": round(1e3 * avg_ms, 2), "share": round(tot / tot_all, 4),
                             "alg_bytes": int(by), "gbs": round(by / (avg_ms / 1e3) / 1e9, 1) if by else None}
+    fba = fwd_bwd_adam(per_kernel, ("k_m_tv", "k_m_query", "k_m_adam", "k_m_finish"), q_prof / Kp, Vt, peak)
     dom = max(kern.items(), key=lambda kv: kv[1][1])[0]
     achieved = per_kernel[dom]["gbs"] or 0.0
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -567,6 +591,7 @@ def run_collection(args, world, rank, local):
                "roofline": roofline, "cpu_baseline": None,
                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 32 * n},
                "gpu_launches": int(per_step_launches * args.steps), "clocks": clk, "kernels": per_kernel,
+               "fwd_bwd_adam": fba,
                "error_bits": info["error_bits"],
                "loss_last_mean": float(hloss.view(n, 8)[:, gb.GP_LOSS_TOTAL].mean())}
         print(json.dumps(out), flush=True)
