@@ -266,6 +266,8 @@ void band_free(gp_band* b) {
   gp_free(b->inv_perm);
   gp_free(b->order_tiles);
   gp_free(b->emit_order);
+  gp_free(b->emit_slot);
+  gp_free(b->emit_pts);
   gp_free(b->partials);
   gp_free(b->dev_ints);
   delete b;

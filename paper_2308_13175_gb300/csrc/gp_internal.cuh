@@ -86,6 +86,8 @@ struct gp_band {
   int32_t* inv_perm = nullptr;     // J: Pi_e^-1 (point -> pool slot within a replica)
   int32_t* order_tiles = nullptr;  // per-tile counts / offsets of the spatial batch order
   int32_t* emit_order = nullptr;   // J: point indices in Morton order of their cell-list cells
+  int32_t* emit_slot = nullptr;    // J: Pi_e^-1(emit_order[u]), the epoch's pool slot of the u-th emitted point
+  float4* emit_pts = nullptr;      // J: (x, y, z, sigma) of emit_order[u]
   bool perm_valid = false;
   uint64_t perm_seed = 0;
   uint32_t perm_epoch = 0;
@@ -272,6 +274,12 @@ __device__ __forceinline__ float3 gp_draw_query(const float* __restrict__ pts, c
                      pts[3 * (int64_t)j + 2] + sg * z.z);
 }
 
+// The same query from a point's (x, y, z, sigma) packed in a float4.
+__device__ __forceinline__ float3 gp_draw_query4(float4 ps, int64_t k, uint32_t epoch, uint32_t k0, uint32_t k1) {
+  float3 z = gp_box_muller3(gp_philox((uint32_t)k, epoch, 0u, 0u, k0, k1));
+  return make_float3(ps.x + ps.w * z.x, ps.y + ps.w * z.y, ps.z + ps.w * z.z);
+}
+
 __host__ __device__ inline int gp_feistel_bits(int64_t J) {
   int m = 2;
   while ((int64_t(1) << m) < J) ++m;
@@ -281,16 +289,19 @@ __host__ __device__ inline int gp_feistel_bits(int64_t J) {
 // ------------------------------------------ device: spatial batch order
 // Replicas r >= 0 of pool slot p whose position k = p + r J lies in
 // [first, last): r in [r0, r0 + n).
+// All of p < J, first <= last <= Q are below 2^31, so the divisions are
+// unsigned 32-bit ones.
 __device__ __forceinline__ void owned_range(int64_t p, int64_t J, int64_t first, int64_t last, int64_t& r0, int& n) {
-  int64_t lo = first - p;
-  r0 = lo <= 0 ? 0 : (lo + J - 1) / J;
-  int64_t hi = last - 1 - p;
+  const int32_t lo = (int32_t)(first - p), hi = (int32_t)(last - 1 - p);
+  const uint32_t uj = (uint32_t)J;
+  const uint32_t a = lo <= 0 ? 0u : ((uint32_t)lo + uj - 1u) / uj;
+  r0 = a;
   if (hi < 0) {
     n = 0;
     return;
   }
-  int64_t r1 = hi / J;
-  n = r1 >= r0 ? (int)(r1 - r0 + 1) : 0;
+  const uint32_t b = (uint32_t)hi / uj;
+  n = b >= a ? (int)(b - a + 1u) : 0;
 }
 
 // Exclusive scan of one int per thread over a block of GP_ORDER_THREADS
@@ -323,6 +334,31 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* excl) {
   int t = total_s;
   __syncthreads();  // wsum and total_s may be reused by the next call
   return t;
+}
+
+// Exclusive scan, in place, of n ints by one block of GP_ORDER_THREADS threads.
+constexpr int GP_SCAN_PER_THREAD = 8;
+__device__ __forceinline__ void gp_block_scan_inplace(int32_t* __restrict__ a, int64_t n) {
+  int carry = 0;
+  for (int64_t base = 0; base < n; base += (int64_t)GP_ORDER_THREADS * GP_SCAN_PER_THREAD) {
+    const int64_t i0 = base + (int64_t)threadIdx.x * GP_SCAN_PER_THREAD;
+    int v[GP_SCAN_PER_THREAD];
+    int sum = 0;
+#pragma unroll
+    for (int k = 0; k < GP_SCAN_PER_THREAD; ++k) {
+      v[k] = i0 + k < n ? a[i0 + k] : 0;
+      sum += v[k];
+    }
+    int excl;
+    const int total = block_exclusive_scan(sum, &excl);
+    int run = carry + excl;
+#pragma unroll
+    for (int k = 0; k < GP_SCAN_PER_THREAD; ++k) {
+      if (i0 + k < n) a[i0 + k] = run;
+      run += v[k];
+    }
+    carry += total;
+  }
 }
 
 // ------------------------------------------------------ device: reductions

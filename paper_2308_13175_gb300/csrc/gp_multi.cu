@@ -45,8 +45,10 @@ struct MShape {
   const float* sigma;
   const float* normals;
   const int32_t* order;  // points in Morton order of their cells
+  const float4* epts;    // their (x, y, z, sigma)
   int32_t* perm;         // this cloud's slice of the multi's Pi_e
   int32_t* inv;          // and of Pi_e^-1
+  int32_t* eslot;        // and of Pi_e^-1(order[u]), the pool slot of the u-th emitted point
   const int32_t* coord;
   const int32_t* nbr;  // 27 neighbour slots per brick
   const int32_t* active;
@@ -126,6 +128,21 @@ __global__ void __launch_bounds__(PT_TILE) k_m_perm(const MShape* __restrict__ s
   }
 }
 
+// Pi_e^-1 in emission order, for the clouds whose order was just rebuilt.
+__global__ void __launch_bounds__(PT_TILE) k_m_emit_slots(const MShape* __restrict__ shapes,
+                                                          const MTile* __restrict__ tiles, int64_t ntiles,
+                                                          const int64_t* __restrict__ t_dev,
+                                                          const int64_t* __restrict__ perm_epoch) {
+  const int64_t t = *t_dev;
+  for (int64_t ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
+    const MTile tl = tiles[ti];
+    const MShape& S = shapes[tl.shape];
+    if (perm_epoch[tl.shape] == t / S.nb_epoch) continue;
+    const int64_t u = (int64_t)tl.first + threadIdx.x;
+    if (u < S.J) S.eslot[u] = S.inv[S.order[u]];
+  }
+}
+
 // Position order: record slot i of cloud k holds pool position first + i.
 __global__ void k_m_sample(const MShape* __restrict__ shapes, const MTile* __restrict__ tiles, int64_t ntiles,
                            int tq, const int64_t* __restrict__ t_dev, uint64_t seed, float* __restrict__ q,
@@ -166,7 +183,7 @@ __global__ void __launch_bounds__(PT_TILE) k_m_order_count(const MShape* __restr
     int c = 0;
     if (u < S.J) {
       int64_t r0;
-      owned_range(S.inv[S.order[u]], S.J, bt.first, bt.first + bt.count, r0, c);
+      owned_range(S.eslot[u], S.J, bt.first, bt.first + bt.count, r0, c);
     }
     int excl;
     const int total = block_exclusive_scan(c, &excl);
@@ -176,15 +193,7 @@ __global__ void __launch_bounds__(PT_TILE) k_m_order_count(const MShape* __restr
 
 // Pass 2: exclusive scan of the tile counts over all clouds (one block).
 __global__ void __launch_bounds__(GP_ORDER_THREADS) k_m_order_scan(int32_t* __restrict__ counts, int64_t ntiles) {
-  int carry = 0;
-  for (int64_t base = 0; base < ntiles; base += GP_ORDER_THREADS) {
-    const int64_t i = base + threadIdx.x;
-    const int v = i < ntiles ? counts[i] : 0;
-    int excl;
-    const int total = block_exclusive_scan(v, &excl);
-    if (i < ntiles) counts[i] = carry + excl;
-    carry += total;
-  }
+  gp_block_scan_inplace(counts, ntiles);
 }
 
 // Pass 3: every point writes its queries at its offset within the cloud's
@@ -205,9 +214,9 @@ __global__ void __launch_bounds__(PT_TILE) k_m_order_emit(const MShape* __restri
     int n = 0, j = 0;
     int64_t r0 = 0, p = 0;
     if (u < S.J) {
-      j = S.order[u];
-      p = S.inv[j];
+      p = S.eslot[u];
       owned_range(p, S.J, bt.first, bt.first + bt.count, r0, n);
+      if (n) j = S.order[u];
     }
     int excl;
     block_exclusive_scan(n, &excl);
@@ -219,7 +228,7 @@ __global__ void __launch_bounds__(PT_TILE) k_m_order_emit(const MShape* __restri
         atomicOr(err, GP_EF_RANGE);
         continue;
       }
-      put_query(S.rec_off + i, gp_draw_query(S.pts, S.sigma, j, k, (uint32_t)bt.epoch, k0, k1), j, q, src);
+      put_query(S.rec_off + i, gp_draw_query4(S.epts[u], k, (uint32_t)bt.epoch, k0, k1), j, q, src);
     }
     if (ti == S.tile0)
       for (int64_t i = bt.count + threadIdx.x; i < S.B; i += blockDim.x) put_nan_query(S.rec_off + i, q, src);
@@ -431,7 +440,8 @@ struct gp_multi {
   MTile *rec_tiles = nullptr, *pt_tiles = nullptr, *brick_tiles = nullptr, *active_tiles = nullptr;
   int64_t n_rec_tiles = 0, n_pt_tiles = 0, n_brick_tiles = 0, n_active_tiles = 0;
   float *q = nullptr, *rec = nullptr, *grad = nullptr;
-  int32_t *src = nullptr, *perm = nullptr, *inv = nullptr, *counts = nullptr, *nvalid = nullptr, *err = nullptr;
+  int32_t *src = nullptr, *perm = nullptr, *inv = nullptr, *eslot = nullptr, *counts = nullptr, *nvalid = nullptr,
+          *err = nullptr;
   double* sums = nullptr;
   int64_t* t = nullptr;
   int64_t* perm_epoch = nullptr;  // per cloud: epoch of the stored Pi_e (-1: none)
@@ -443,7 +453,7 @@ void multi_free(gp_multi* m) {
   if (!m) return;
   for (void* p : {(void*)m->shapes, (void*)m->rec_tiles, (void*)m->pt_tiles, (void*)m->brick_tiles,
                   (void*)m->active_tiles, (void*)m->q, (void*)m->rec, (void*)m->grad, (void*)m->src,
-                  (void*)m->perm, (void*)m->inv, (void*)m->counts, (void*)m->nvalid, (void*)m->err,
+                  (void*)m->perm, (void*)m->inv, (void*)m->eslot, (void*)m->counts, (void*)m->nvalid, (void*)m->err,
                   (void*)m->sums, (void*)m->t, (void*)m->perm_epoch})
     gp_free(p);
   delete m;
@@ -510,12 +520,14 @@ gp_status launch_sampling(gp_multi* m) {
   GP_KERNEL(ctx, "k_m_perm",
             k_m_perm<<<gp, PT_TILE, 0, s>>>(m->shapes, m->pt_tiles, m->n_pt_tiles, m->t, m->perm_epoch, m->seed,
                                             m->err));
-  if (!(m->flags & GP_SAMPLE_SPATIAL)) {
+  if (!(m->flags & GP_SAMPLE_SPATIAL)) {  // position order: no emission slots needed
     GP_KERNEL(ctx, "k_m_sample",
               k_m_sample<<<persistent_grid(m, 4, m->n_rec_tiles), 256, 0, s>>>(
                   m->shapes, m->rec_tiles, m->n_rec_tiles, m->tq, m->t, m->seed, m->q, m->src));
     return GP_OK;
   }
+  GP_KERNEL(ctx, "k_m_emit_slots",
+            k_m_emit_slots<<<gp, PT_TILE, 0, s>>>(m->shapes, m->pt_tiles, m->n_pt_tiles, m->t, m->perm_epoch));
   GP_KERNEL(ctx, "k_m_order_count",
             k_m_order_count<<<gp, PT_TILE, 0, s>>>(m->shapes, m->pt_tiles, m->n_pt_tiles, m->t, m->counts));
   GP_KERNEL(ctx, "k_m_order_scan", k_m_order_scan<<<1, GP_ORDER_THREADS, 0, s>>>(m->counts, m->n_pt_tiles));
@@ -565,7 +577,7 @@ extern "C" gp_status gp_multi_create(gp_ctx* ctx, gp_band* const* bands, int32_t
   std::vector<MTile> pt, br, ac;
   for (int k = 0; k < n; ++k) {
     gp_band* b = bands[k];
-    if (!b || b->ctx != ctx || !b->sigma || !b->emit_order) {
+    if (!b || b->ctx != ctx || !b->sigma || !b->emit_order || !b->emit_pts) {
       multi_free(m);
       return gp_fail(ctx, GP_ERR_ARG, "gp_multi_create: every band must come from this context, with sigma");
     }
@@ -601,6 +613,7 @@ extern "C" gp_status gp_multi_create(gp_ctx* ctx, gp_band* const* bands, int32_t
   if (!st) st = gp_alloc(ctx, &m->grad, m->V_total, "multi gradient");
   if (!st) st = gp_alloc(ctx, &m->perm, m->J_total, "multi permutation");
   if (!st) st = gp_alloc(ctx, &m->inv, m->J_total, "multi inverse permutation");
+  if (!st) st = gp_alloc(ctx, &m->eslot, m->J_total, "multi emission slots");
   if (!st) st = gp_alloc(ctx, &m->shapes, (size_t)n, "multi shapes");
   if (!st) st = gp_alloc(ctx, &m->q, 3 * m->total_B, "multi queries");
   if (!st) st = gp_alloc(ctx, &m->src, m->total_B, "multi sources");
@@ -635,8 +648,10 @@ extern "C" gp_status gp_multi_create(gp_ctx* ctx, gp_band* const* bands, int32_t
     S.sigma = b->sigma;
     S.normals = b->normals;
     S.order = b->emit_order;
+    S.epts = b->emit_pts;
     S.perm = m->perm + joff;
     S.inv = m->inv + joff;
+    S.eslot = m->eslot + joff;
     S.coord = b->brick_coord;
     S.nbr = b->brick_nbr;
     S.active = b->active;

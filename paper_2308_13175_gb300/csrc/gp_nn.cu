@@ -231,6 +231,15 @@ __global__ void __launch_bounds__(256) k_nn(NNGrid g, const float* __restrict__ 
   if (active) nn_finish(i, q, best, pts_orig, nn_out, rec, band, nvalid);
 }
 
+// Points and sigma in emission order, for the sampler's coalesced reads.
+__global__ void k_emit_pts(const int32_t* __restrict__ order, const float* __restrict__ pts,
+                           const float* __restrict__ sigma, int64_t J, float4* __restrict__ out) {
+  const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= J) return;
+  const int64_t j = order[u];
+  out[u] = make_float4(pts[3 * j], pts[3 * j + 1], pts[3 * j + 2], sigma[j]);
+}
+
 }  // namespace
 
 // Emission order of the spatial batches: point indices sorted by the Morton
@@ -323,10 +332,14 @@ gp_status gp_build_points(gp_band* b, const float* pts_dev) {
     if ((st = gp_alloc(ctx, &b->inv_perm, J, "inverse permutation"))) return st;
     if ((st = gp_alloc(ctx, &b->order_tiles, (J + GP_ORDER_TILE - 1) / GP_ORDER_TILE + 1, "order tiles"))) return st;
     if ((st = build_emit_order(b))) return st;
+    if ((st = gp_alloc(ctx, &b->emit_slot, J, "emission slots"))) return st;
     int k = (int)std::min<int64_t>(b->knn_k, J - 1);
     GP_KERNEL(ctx, "k_knn_sigma", k_knn_sigma<<<gp_blocks(J, 128), 128, 0, s>>>(g, J, k, b->sigma));
     if ((st = gp_alloc(ctx, &b->normals, 3 * J, "normals"))) return st;
     GP_KERNEL(ctx, "k_normals", k_normals<<<gp_blocks(J, 128), 128, 0, s>>>(g, J, b->sigma, b->normals));
+    if ((st = gp_alloc(ctx, &b->emit_pts, J, "emission points"))) return st;
+    GP_KERNEL(ctx, "k_emit_pts", k_emit_pts<<<gp_blocks(J, 256), 256, 0, s>>>(b->emit_order, b->pts, b->sigma, J,
+                                                                            b->emit_pts));
   }
   return GP_OK;
 }

@@ -37,6 +37,15 @@ __global__ void k_perm(int64_t J, int half, uint32_t epoch, uint32_t k0, uint32_
   inv[x] = (int32_t)p;
 }
 
+// Pi_e^-1 composed with the emission order, once per epoch, so that the
+// per-step count and emit passes read it in their own order (coalesced)
+// instead of gathering inv[order[u]].
+__global__ void k_emit_slots(const int32_t* __restrict__ order, const int32_t* __restrict__ inv, int64_t J,
+                             int32_t* __restrict__ slot) {
+  int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (u < J) slot[u] = inv[order[u]];
+}
+
 __device__ __forceinline__ void put_query(int64_t i, float3 v, int32_t j, int64_t k, float* __restrict__ q,
                                           int32_t* __restrict__ src, int32_t* __restrict__ pos) {
   q[3 * i + 0] = v.x;
@@ -58,8 +67,7 @@ __global__ void k_sample(const float* __restrict__ pts, const float* __restrict_
 }
 
 // Pass 1: queries owned by each tile of sorted points.
-__global__ void __launch_bounds__(GP_ORDER_THREADS) k_order_count(const int32_t* __restrict__ order,
-                                                                  const int32_t* __restrict__ inv, int64_t J,
+__global__ void __launch_bounds__(GP_ORDER_THREADS) k_order_count(const int32_t* __restrict__ eslot, int64_t J,
                                                                   int64_t first, int64_t last,
                                                                   int32_t* __restrict__ tiles) {
   int64_t base = (int64_t)blockIdx.x * GP_ORDER_TILE + (int64_t)threadIdx.x * GP_ORDER_PER_THREAD;
@@ -68,10 +76,9 @@ __global__ void __launch_bounds__(GP_ORDER_THREADS) k_order_count(const int32_t*
   for (int u = 0; u < GP_ORDER_PER_THREAD; ++u) {
     int64_t t = base + u;
     if (t < J) {
-      int j = order[t];
       int64_t r0;
       int n;
-      owned_range(inv[j], J, first, last, r0, n);
+      owned_range(eslot[t], J, first, last, r0, n);
       c += n;
     }
   }
@@ -80,23 +87,16 @@ __global__ void __launch_bounds__(GP_ORDER_THREADS) k_order_count(const int32_t*
   if (threadIdx.x == 0) tiles[blockIdx.x] = total;
 }
 
-// Pass 2: exclusive scan of the tile counts in place (one block, any length).
+// Pass 2: exclusive scan of the tile counts in place (one block, any length,
+// GP_SCAN_PER_THREAD consecutive counts per thread and round).
 __global__ void __launch_bounds__(GP_ORDER_THREADS) k_order_tiles(int32_t* __restrict__ tiles, int64_t ntiles) {
-  int carry = 0;
-  for (int64_t base = 0; base < ntiles; base += GP_ORDER_THREADS) {
-    int64_t i = base + threadIdx.x;
-    int v = i < ntiles ? tiles[i] : 0;
-    int excl;
-    int total = block_exclusive_scan(v, &excl);
-    if (i < ntiles) tiles[i] = carry + excl;
-    carry += total;
-  }
+  gp_block_scan_inplace(tiles, ntiles);
 }
 
 // Pass 3: every sorted point writes its queries at its offset.
 __global__ void __launch_bounds__(GP_ORDER_THREADS) k_order_emit(
-    const int32_t* __restrict__ order, const int32_t* __restrict__ inv, const float* __restrict__ pts,
-    const float* __restrict__ sigma, int64_t J, int64_t first, int64_t last, const int32_t* __restrict__ tiles,
+    const int32_t* __restrict__ order, const int32_t* __restrict__ eslot, const float4* __restrict__ epts,
+    int64_t J, int64_t first, int64_t last, const int32_t* __restrict__ tiles,
     uint32_t epoch, uint32_t k0, uint32_t k1, float* __restrict__ q, int32_t* __restrict__ src,
     int32_t* __restrict__ pos, int32_t* __restrict__ err) {
   int64_t base = (int64_t)blockIdx.x * GP_ORDER_TILE + (int64_t)threadIdx.x * GP_ORDER_PER_THREAD;
@@ -112,9 +112,9 @@ __global__ void __launch_bounds__(GP_ORDER_THREADS) k_order_emit(
     pp[u] = 0;
     rr[u] = 0;
     if (t < J) {
-      jj[u] = order[t];
-      pp[u] = inv[jj[u]];
+      pp[u] = eslot[t];
       owned_range(pp[u], J, first, last, rr[u], nn[u]);
+      if (nn[u]) jj[u] = order[t];
       c += nn[u];
     }
   }
@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(GP_ORDER_THREADS) k_order_emit(
         atomicOr(err, GP_EF_RANGE);
         continue;
       }
-      put_query(i, gp_draw_query(pts, sigma, jj[u], k, epoch, k0, k1), jj[u], k, q, src, pos);
+      put_query(i, gp_draw_query4(epts[base + u], k, epoch, k0, k1), jj[u], k, q, src, pos);
     }
   }
 }
@@ -145,6 +145,10 @@ gp_status gp_build_permutation(gp_band* b, uint64_t seed, uint32_t epoch) {
             k_perm<<<gp_blocks(b->J, 256), 256, 0, ctx->stream>>>(b->J, half, epoch, (uint32_t)seed,
                                                                   (uint32_t)(seed >> 32), b->perm, b->inv_perm,
                                                                   b->dev_ints + GP_DI_ERROR));
+  if (b->emit_order)
+    GP_KERNEL(ctx, "k_emit_slots",
+              k_emit_slots<<<gp_blocks(b->J, 256), 256, 0, ctx->stream>>>(b->emit_order, b->inv_perm, b->J,
+                                                                         b->emit_slot));
   b->perm_valid = true;
   b->perm_seed = seed;
   b->perm_epoch = epoch;
@@ -172,12 +176,12 @@ extern "C" gp_status gp_sample(gp_band* b, uint64_t seed, uint32_t epoch, int64_
   const int64_t J = b->J, last = first + count;
   const int64_t ntiles = (J + GP_ORDER_TILE - 1) / GP_ORDER_TILE;
   GP_KERNEL(ctx, "k_order_count",
-            k_order_count<<<(unsigned)ntiles, GP_ORDER_THREADS, 0, ctx->stream>>>(b->emit_order, b->inv_perm, J,
-                                                                                 first, last, b->order_tiles));
+            k_order_count<<<(unsigned)ntiles, GP_ORDER_THREADS, 0, ctx->stream>>>(b->emit_slot, J, first, last,
+                                                                                 b->order_tiles));
   GP_KERNEL(ctx, "k_order_tiles", k_order_tiles<<<1, GP_ORDER_THREADS, 0, ctx->stream>>>(b->order_tiles, ntiles));
   GP_KERNEL(ctx, "k_order_emit",
             k_order_emit<<<(unsigned)ntiles, GP_ORDER_THREADS, 0, ctx->stream>>>(
-                b->emit_order, b->inv_perm, b->pts, b->sigma, J, first, last, b->order_tiles, epoch, k0, k1, q_dev,
+                b->emit_order, b->emit_slot, b->emit_pts, J, first, last, b->order_tiles, epoch, k0, k1, q_dev,
                 src_dev, pos_dev, b->dev_ints + GP_DI_ERROR));
   return GP_OK;
 }
