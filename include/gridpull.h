@@ -251,7 +251,7 @@ typedef struct gp_loss_w {
 #define GP_LOSS_T 6     /* |T| (as float)                                          */
 
 /* One forward + hand-written backward pass of Eq. 8 over B step records
- * rec_dev (B x 6 float32: q then NN(q), e.g. from gp_nn).  Query terms are
+ * rec_dev (B x 6 float32: q then NN(q), e.g. from gp_nn; 8-byte aligned).  Query terms are
  * averaged over the B_v valid queries, L_TV over T.  Writes the loss slots to
  * loss_dev (8 floats) and, unless GP_STEP_LOSS_ONLY, overwrites grad_dev
  * (V_stored floats, storage order) with dL/dD at every stored slot (0 at
@@ -259,7 +259,8 @@ typedef struct gp_loss_w {
  * not NULL it holds B_v, the number of valid records among them (as gp_nn
  * counts it); otherwise gp_step counts them first.  If d_dev is not NULL the values are
  * read from it (V_stored floats) instead of the band's own.  Errors:
- * GP_ERR_ARG (B < 0, null rec/loss, B >= 2^31, rec_dev not 8-byte aligned),
+ * GP_ERR_ARG (B < 0, null rec/loss, B >= 2^31, rec_dev not 8-byte aligned,
+ * grad_dev not 16-byte aligned: its corner pairs are added as vector reductions),
  * GP_ERR_STATE (deterministic
  * flag on a band built without GP_BAND_DETERMINISTIC). */
 gp_status gp_step(gp_band* band, const float* rec_dev, int64_t B, const int32_t* nvalid_dev,

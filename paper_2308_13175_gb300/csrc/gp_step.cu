@@ -250,6 +250,8 @@ extern "C" gp_status gp_step(gp_band* b, const float* rec_dev, int64_t B, const 
   const bool tv_on = !(flags & GP_STEP_NO_TV);
   if (grad_on && !grad_dev) return gp_fail(ctx, GP_ERR_ARG, "gp_step: null gradient output");
   if (((uintptr_t)rec_dev & 7u) != 0) return gp_fail(ctx, GP_ERR_ARG, "gp_step: records must be 8-byte aligned");
+  if (((uintptr_t)grad_dev & 15u) != 0)
+    return gp_fail(ctx, GP_ERR_ARG, "gp_step: the gradient must be 16-byte aligned");
   if (det && grad_on && !b->acc)
     return gp_fail(ctx, GP_ERR_STATE, "gp_step: deterministic mode needs a band built with GP_BAND_DETERMINISTIC");
   cudaStream_t s = ctx->stream;

@@ -65,6 +65,16 @@ __device__ __forceinline__ Eval trilerp(const float d[8], const float t[3]) {
   return r;
 }
 
+// Two adjacent floats added as one 8-byte vector reduction (address 8-byte aligned).
+__device__ __forceinline__ void red_add_v2(float* addr, float a, float b) {
+  asm volatile("red.global.add.v2.f32 [%0], {%1, %2};\n" ::"l"(addr), "f"(a), "f"(b) : "memory");
+}
+// Four adjacent floats as one 16-byte vector reduction (address 16-byte aligned).
+__device__ __forceinline__ void red_add_v4(float* addr, float a, float b, float c, float d) {
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};\n" ::"l"(addr), "f"(a), "f"(b), "f"(c), "f"(d)
+               : "memory");
+}
+
 // Scatter of one cell's 8 corner contributions.
 template <bool DET>
 __device__ __forceinline__ void scatter8(const Grid& G, float* __restrict__ grad, unsigned long long* __restrict__ acc,
@@ -72,6 +82,30 @@ __device__ __forceinline__ void scatter8(const Grid& G, float* __restrict__ grad
                                          float A, const float Gt[3]) {
   float wx[2] = {1.f - t[0], t[0]}, wy[2] = {1.f - t[1], t[1]}, wz[2] = {1.f - t[2], t[2]};
   bool fast = (c[0] & 7) != 7 && (c[1] & 7) != 7 && (c[2] & 7) != 7;
+  if (!DET && fast && (c[0] & 3) != 3) {
+    // The corners (x, x + 1) of each of the 4 (y, z) edges are adjacent: one
+    // vector reduction per edge - 8 bytes at even x, 16 bytes from x - 1 (the
+    // outer two lanes adding zero) at x = 1 mod 4.
+    float* base = grad + gp_vaddr(slot, c[0], c[1], c[2]);
+    const bool odd = c[0] & 1;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int dy = e & 1, dz = e >> 1;
+      const float sy = dy ? 1.f : -1.f, sz = dz ? 1.f : -1.f;
+      const float wyz = wy[dy] * wz[dz];
+      float v[2];
+#pragma unroll
+      for (int dx = 0; dx < 2; ++dx) {
+        const float sx = dx ? 1.f : -1.f;
+        v[dx] = A * wx[dx] * wyz + Gt[0] * sx * wyz + Gt[1] * wx[dx] * sy * wz[dz] + Gt[2] * wx[dx] * wy[dy] * sz;
+      }
+      if (odd)
+        red_add_v4(base - 1 + dy * 8 + dz * 64, 0.f, v[0], v[1], 0.f);
+      else
+        red_add_v2(base + dy * 8 + dz * 64, v[0], v[1]);
+    }
+    return;
+  }
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
     int dx = k & 1, dy = (k >> 1) & 1, dz = k >> 2;

@@ -427,6 +427,19 @@ def test_step_deterministic_is_bitwise_repeatable(gb, ctx, object100k):
     assert ref["Bv"] > 90_000
 
 
+def test_step_rejects_misaligned_buffers(gb, ctx, sphere5k):
+    import torch
+    band = _band(gb, ctx, sphere5k, 32, 1, 1, knn_k=0)
+    rec = torch.zeros((11, 6), dtype=torch.float32, device="cuda")
+    grad = torch.zeros(band.V_stored + 4, dtype=torch.float32, device="cuda")
+    loss = torch.zeros(8, dtype=torch.float32, device="cuda")
+    gb.gp_step(band, rec, 10, grad[4:], loss)                      # 16-byte aligned view
+    with pytest.raises(gb.GridPullError):
+        gb.gp_step(band, rec, 10, grad[1:], loss)                  # gradient off by 4 bytes
+    with pytest.raises(gb.GridPullError):
+        gb.gp_step(band, rec.view(-1)[1:], 10, grad[:band.V_stored], loss)  # records off by 4 bytes
+
+
 def test_step_deterministic_needs_band_flag(gb, ctx, sphere5k):
     band = _band(gb, ctx, sphere5k, 32, 1, 1, knn_k=0)
     with pytest.raises(gb.GridPullError):
