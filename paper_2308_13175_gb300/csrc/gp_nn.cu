@@ -201,12 +201,34 @@ __global__ void __launch_bounds__(128) k_normals(NNGrid g, int64_t J, const floa
 
 // One thread per query.  Queries with a NaN, infinite or huge coordinate (whose
 // squared distances would overflow float32) get -1 and a NaN surface point.
-__global__ void __launch_bounds__(256) k_nn(NNGrid g, const float* __restrict__ qin, int64_t n,
-                                            const int32_t* __restrict__ hint, int64_t J,
-                                            const float* __restrict__ pts_orig, int32_t* __restrict__ nn_out,
-                                            float* __restrict__ rec, Grid band, int32_t* __restrict__ nvalid,
-                                            const float* __restrict__ normals) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+//
+// Each thread first seeds its own query; the block then sorts its queries (in
+// segments of NN_SPAN), stably, by the seeded radius (a counting sort on thr in
+// quarters of the squared cell size: the walk visits about thr / cs^2 rows),
+// and every thread searches the query of its rank, so that the lanes of a warp
+// have walks of similar length while queries of equal key keep their spatial
+// order.  Which thread searches a query does not change its result.
+constexpr int NN_THREADS = 256;
+#ifndef GP_NN_SORT_SPAN
+#define GP_NN_SORT_SPAN 32
+#endif
+constexpr int NN_SPAN = GP_NN_SORT_SPAN;  // queries sorted together (a multiple of 32 dividing 256)
+constexpr int NN_SEGS = NN_THREADS / NN_SPAN;
+constexpr int NN_SPAN_WARPS = NN_SPAN / 32;
+constexpr int NN_BUCKETS = 16;
+static_assert(NN_SPAN % 32 == 0 && NN_THREADS % NN_SPAN == 0, "sort span");
+
+__global__ void __launch_bounds__(NN_THREADS) k_nn(NNGrid g, const float* __restrict__ qin, int64_t n,
+                                                   const int32_t* __restrict__ hint, int64_t J,
+                                                   const float* __restrict__ pts_orig, int32_t* __restrict__ nn_out,
+                                                   float* __restrict__ rec, Grid band, int32_t* __restrict__ nvalid,
+                                                   const float* __restrict__ normals) {
+  __shared__ int s_off[NN_SEGS][NN_BUCKETS][NN_SPAN_WARPS];  // count, then first rank in the segment
+  __shared__ float4 s_q[NN_THREADS];   // q, and the query's offset in the block (int bits; -1 - offset if invalid)
+  __shared__ float4 s_st[NN_THREADS];  // b1, b2, thr, j1 (int bits)
+  const int t = threadIdx.x, lane = t & 31, seg = t / NN_SPAN, wseg = (t % NN_SPAN) >> 5;
+  const int64_t base = (int64_t)blockIdx.x * NN_THREADS;
+  int64_t i = base + t;
   const bool active = i < n;
   float q[3] = {0.f, 0.f, 0.f};
   if (active) {
@@ -214,21 +236,54 @@ __global__ void __launch_bounds__(256) k_nn(NNGrid g, const float* __restrict__ 
     q[1] = qin[3 * i + 1];
     q[2] = qin[3 * i + 2];
   }
-  const bool ok = active && nn_query_ok(q);
-  int c[3] = {0, 0, 0};
-  float margin = 0.f;
+  bool ok = active && nn_query_ok(q);
   NNState st{INFINITY, INFINITY, INFINITY, 0x7fffffff};
+  int key = 0;
   if (ok) {
-    c[0] = nn_cell(q[0], g);
-    c[1] = nn_cell(q[1], g);
-    c[2] = nn_cell(q[2], g);
-    margin = nn_margin(q);
     nn_seed(st, q, hint, i, J, pts_orig);
-    if (st.b1 < INFINITY) nn_seed_foot(st, q, hint, i, J, pts_orig, normals, g);
+    if (st.b1 < INFINITY) {
+      nn_seed_foot(st, q, hint, i, J, pts_orig, normals, g);
+      key = (int)fminf(4.0f * st.thr / (g.cs * g.cs), (float)(NN_BUCKETS - 2));
+    } else {
+      key = NN_BUCKETS - 1;  // unseeded: the ring search
+    }
   }
+  // Stable counting sort within each segment of NN_SPAN queries:
+  // rank = (smaller key) + (same key, lower warp) + (same key, lower lane).
+  const unsigned peers = __match_any_sync(0xffffffffu, key);
+  const int in_warp = __popc(peers & ((1u << lane) - 1u));
+  for (int k = t; k < NN_SEGS * NN_BUCKETS * NN_SPAN_WARPS; k += NN_THREADS) (&s_off[0][0][0])[k] = 0;
+  __syncthreads();
+  if (in_warp == 0) s_off[seg][key][wseg] = __popc(peers);
+  __syncthreads();
+  if (t < NN_SEGS) {
+    int run = 0;
+    for (int b = 0; b < NN_BUCKETS; ++b)
+      for (int w = 0; w < NN_SPAN_WARPS; ++w) {
+        const int c = s_off[t][b][w];
+        s_off[t][b][w] = run;
+        run += c;
+      }
+  }
+  __syncthreads();
+  const int rank = seg * NN_SPAN + s_off[seg][key][wseg] + in_warp;
+  s_q[rank] = make_float4(q[0], q[1], q[2], __int_as_float(ok ? t : -1 - t));
+  s_st[rank] = make_float4(st.b1, st.b2, st.thr, __int_as_float(st.j1));
+  __syncthreads();
+  const float4 mq = s_q[t], ms = s_st[t];
+  const int off = __float_as_int(mq.w);
+  ok = off >= 0;
+  i = base + (ok ? off : -1 - off);
+  q[0] = mq.x;
+  q[1] = mq.y;
+  q[2] = mq.z;
+  st = NNState{ms.x, ms.y, ms.z, __float_as_int(ms.w)};
   int best = -1;
-  if (ok) best = nn_thread_search(q, c, g, margin, st);
-  if (active) nn_finish(i, q, best, pts_orig, nn_out, rec, band, nvalid);
+  if (ok) {
+    const int c[3] = {nn_cell(q[0], g), nn_cell(q[1], g), nn_cell(q[2], g)};
+    best = nn_thread_search(q, c, g, nn_margin(q), st);
+  }
+  if (i < n) nn_finish(i, q, best, pts_orig, nn_out, rec, band, nvalid);
 }
 
 // Points and sigma in emission order, for the sampler's coalesced reads.
@@ -369,7 +424,7 @@ extern "C" gp_status gp_nn(gp_band* b, const float* q_dev, int64_t n, const int3
   band.nb = b->nb;
   band.R = b->R;
   band.half_r = 0.5f * (float)b->R;
-  GP_KERNEL(ctx, "k_nn", k_nn<<<gp_blocks(n, 256), 256, 0, ctx->stream>>>(g, q_dev, n, hint_dev, b->J, b->pts,
+  GP_KERNEL(ctx, "k_nn", k_nn<<<gp_blocks(n, NN_THREADS), NN_THREADS, 0, ctx->stream>>>(g, q_dev, n, hint_dev, b->J, b->pts,
                                                                            nn_dev, rec_dev, band, nvalid_dev,
                                                                            b->normals));
   return GP_OK;
