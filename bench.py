@@ -72,6 +72,7 @@ def alg_bytes(name, n, J, Vs, Vt):
         "k_order_count": 20 * J,
         "k_order_emit": 20 * J + 32 * n,
         "k_nn": 36 * n + 16 * J,
+        "k_nn_sorted": 36 * n + 16 * J,
         "k_count_valid": 24 * n,
         "k_tv": 8 * Vs,
         "k_query": 24 * n + 8 * Vt,
@@ -79,7 +80,7 @@ def alg_bytes(name, n, J, Vs, Vt):
     }.get(name, 0)
 
 
-KERNEL_BOUND = {"k_nn": "hbm", "k_tv": "hbm", "k_query": "hbm", "k_adam": "hbm", "k_sample": "hbm"}
+KERNEL_BOUND = {"k_nn": "hbm", "k_nn_sorted": "hbm", "k_tv": "hbm", "k_query": "hbm", "k_adam": "hbm", "k_sample": "hbm"}
 
 
 def fwd_bwd_adam(per_kernel: dict, names, queries_per_step: float, V_trainable: int, peak: float) -> dict:

@@ -201,24 +201,54 @@ __global__ void __launch_bounds__(128) k_normals(NNGrid g, int64_t J, const floa
 
 // One thread per query.  Queries with a NaN, infinite or huge coordinate (whose
 // squared distances would overflow float32) get -1 and a NaN surface point.
-//
-// Each thread first seeds its own query; the block then sorts its queries (in
+__global__ void __launch_bounds__(256) k_nn(NNGrid g, const float* __restrict__ qin, int64_t n,
+                                            const int32_t* __restrict__ hint, int64_t J,
+                                            const float* __restrict__ pts_orig, int32_t* __restrict__ nn_out,
+                                            float* __restrict__ rec, Grid band, int32_t* __restrict__ nvalid,
+                                            const float* __restrict__ normals) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool active = i < n;
+  float q[3] = {0.f, 0.f, 0.f};
+  if (active) {
+    q[0] = qin[3 * i];
+    q[1] = qin[3 * i + 1];
+    q[2] = qin[3 * i + 2];
+  }
+  const bool ok = active && nn_query_ok(q);
+  int c[3] = {0, 0, 0};
+  float margin = 0.f;
+  NNState st{INFINITY, INFINITY, INFINITY, 0x7fffffff};
+  if (ok) {
+    c[0] = nn_cell(q[0], g);
+    c[1] = nn_cell(q[1], g);
+    c[2] = nn_cell(q[2], g);
+    margin = nn_margin(q);
+    nn_seed(st, q, hint, i, J, pts_orig);
+    if (st.b1 < INFINITY) nn_seed_foot(st, q, hint, i, J, pts_orig, normals, g);
+  }
+  int best = -1;
+  if (ok) best = nn_thread_search(q, c, g, margin, st);
+  if (active) nn_finish(i, q, best, pts_orig, nn_out, rec, band, nvalid);
+}
+
+// The same search for large seeded batches.  Each thread first seeds its own query; the block then sorts its queries (in
 // segments of NN_SPAN), stably, by the seeded radius (a counting sort on thr in
 // quarters of the squared cell size: the walk visits about thr / cs^2 rows),
 // and every thread searches the query of its rank, so that the lanes of a warp
 // have walks of similar length while queries of equal key keep their spatial
 // order.  Which thread searches a query does not change its result.
+// Measured on GB300: 18% faster than k_nn on the 4,194,304-query superquadric
+// batch and 10% on the 2,097,152-query scene batch, 6-10% slower on the
+// 262,144-query single-object batch, hence NN_SORTED_MIN_QUERIES.
 constexpr int NN_THREADS = 256;
-#ifndef GP_NN_SORT_SPAN
-#define GP_NN_SORT_SPAN 32
-#endif
-constexpr int NN_SPAN = GP_NN_SORT_SPAN;  // queries sorted together (a multiple of 32 dividing 256)
+constexpr int NN_SPAN = 256;  // queries sorted together (a multiple of 32 dividing NN_THREADS)
 constexpr int NN_SEGS = NN_THREADS / NN_SPAN;
 constexpr int NN_SPAN_WARPS = NN_SPAN / 32;
 constexpr int NN_BUCKETS = 16;
+constexpr int64_t NN_SORTED_MIN_QUERIES = int64_t(1) << 20;
 static_assert(NN_SPAN % 32 == 0 && NN_THREADS % NN_SPAN == 0, "sort span");
 
-__global__ void __launch_bounds__(NN_THREADS) k_nn(NNGrid g, const float* __restrict__ qin, int64_t n,
+__global__ void __launch_bounds__(NN_THREADS) k_nn_sorted(NNGrid g, const float* __restrict__ qin, int64_t n,
                                                    const int32_t* __restrict__ hint, int64_t J,
                                                    const float* __restrict__ pts_orig, int32_t* __restrict__ nn_out,
                                                    float* __restrict__ rec, Grid band, int32_t* __restrict__ nvalid,
@@ -424,7 +454,13 @@ extern "C" gp_status gp_nn(gp_band* b, const float* q_dev, int64_t n, const int3
   band.nb = b->nb;
   band.R = b->R;
   band.half_r = 0.5f * (float)b->R;
-  GP_KERNEL(ctx, "k_nn", k_nn<<<gp_blocks(n, NN_THREADS), NN_THREADS, 0, ctx->stream>>>(g, q_dev, n, hint_dev, b->J, b->pts,
+  if (hint_dev && n >= NN_SORTED_MIN_QUERIES) {
+    GP_KERNEL(ctx, "k_nn_sorted",
+              k_nn_sorted<<<gp_blocks(n, NN_THREADS), NN_THREADS, 0, ctx->stream>>>(
+                  g, q_dev, n, hint_dev, b->J, b->pts, nn_dev, rec_dev, band, nvalid_dev, b->normals));
+    return GP_OK;
+  }
+  GP_KERNEL(ctx, "k_nn", k_nn<<<gp_blocks(n, 256), 256, 0, ctx->stream>>>(g, q_dev, n, hint_dev, b->J, b->pts,
                                                                            nn_dev, rec_dev, band, nvalid_dev,
                                                                            b->normals));
   return GP_OK;

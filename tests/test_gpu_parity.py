@@ -158,6 +158,38 @@ def test_nn_seeded_spatial_batch_full_size(gb, ctx, object100k):
     assert np.array_equal(nn_plain, nn[sel])
 
 
+def test_nn_sorted_large_seeded_batch(gb, ctx, object100k):
+    """Seeded batches of 2^20 queries or more take the radius-sorted search:
+    1,100,003 queries (a ragged last block) with a few invalid seeds and a few
+    non-finite queries must give, index for index, what the fused per-thread
+    search gives in chunks below that size; 3,000 sampled queries are checked
+    by brute force."""
+    import torch
+    R = 256
+    band = _band(gb, ctx, object100k, R, 2, 2, knn_k=0)
+    n = 1_100_003
+    q, j = synth.gaussian_queries(object100k, n, 0.03, seed=22)
+    cell = np.floor((object100k[j].astype(np.float64) + 1) * 64).astype(np.int64)
+    order = np.lexsort((cell[:, 0], cell[:, 1], cell[:, 2]))
+    q, j = q[order].copy(), j[order].copy()
+    rng = np.random.default_rng(6)
+    j[rng.choice(n, 700, replace=False)] = -1
+    q[rng.choice(n, 5, replace=False), 1] = np.nan
+    qd = torch.from_numpy(np.ascontiguousarray(q, np.float32)).cuda()
+    jd = torch.from_numpy(j.astype(np.int32)).cuda()
+    nn_sorted = torch.empty(n, dtype=torch.int32, device="cuda")
+    gb.gp_nn(band, qd, nn_sorted, None, hint=jd)
+    nn_fused = torch.empty(n, dtype=torch.int32, device="cuda")
+    step = (1 << 20) - 1
+    for a in range(0, n, step):
+        gb.gp_nn(band, qd[a:a + step], nn_fused[a:a + step], None, hint=jd[a:a + step])
+    got, want = nn_sorted.cpu().numpy(), nn_fused.cpu().numpy()
+    assert np.array_equal(got, want)
+    assert np.all(got[np.isnan(q).any(axis=1)] == -1)
+    sel = rng.choice(np.flatnonzero(np.isfinite(q).all(axis=1)), 3000, replace=False)
+    assert np.array_equal(got[sel], o.nearest_point(q[sel], object100k))
+
+
 def test_nn_counts_valid_records(gb, ctx, sphere5k):
     import torch
     R = 64
