@@ -237,63 +237,28 @@ __global__ void __launch_bounds__(PT_TILE) k_m_order_emit(const MShape* __restri
 
 // Nearest point of every query (seeded by its source point and the foot of q
 // on the source's tangent plane), the step records, and the per-cloud count of
-// valid records.  Per tile, every thread seeds one query, the block sorts the
-// tile's queries by seeded radius (nn_block_rank) and each thread then walks
-// the query of its rank; which thread walks a query does not change its result.
-constexpr int M_NN_MAX_THREADS = 512;
-
-__global__ void __launch_bounds__(M_NN_MAX_THREADS) k_m_nn(const MShape* __restrict__ shapes,
-                                                           const MTile* __restrict__ tiles, int64_t ntiles, int tq,
-                                                           const float* __restrict__ q,
-                                                           const int32_t* __restrict__ src, float* __restrict__ rec,
-                                                           int32_t* __restrict__ nvalid) {
-  __shared__ int s_off[NN_SORT_BUCKETS * NN_SORT_MAX_WARPS];
-  __shared__ float4 s_q[M_NN_MAX_THREADS];   // q, and the query's thread (int bits; see below)
-  __shared__ float4 s_st[M_NN_MAX_THREADS];  // b1, b2, thr, j1 (int bits)
-  const int t = threadIdx.x;
+// valid records.
+__global__ void __launch_bounds__(512) k_m_nn(const MShape* __restrict__ shapes, const MTile* __restrict__ tiles,
+                                              int64_t ntiles, int tq, const float* __restrict__ q,
+                                              const int32_t* __restrict__ src, float* __restrict__ rec,
+                                              int32_t* __restrict__ nvalid) {
   for (int64_t ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
     const MTile tl = tiles[ti];
     const MShape& S = shapes[tl.shape];
     const int64_t end = min((int64_t)tl.first + tq, S.B);
-    const int32_t* hint = src + S.rec_off;
     for (int64_t i0 = tl.first; i0 < end; i0 += blockDim.x) {
-      const int64_t i = i0 + t;
-      const bool in = i < end;
-      float qq[3] = {0.f, 0.f, 0.f};
-      if (in) {
-        const int64_t slot = S.rec_off + i;
-        qq[0] = q[3 * slot];
-        qq[1] = q[3 * slot + 1];
-        qq[2] = q[3 * slot + 2];
-      }
-      bool ok = in && nn_query_ok(qq);
-      NNState st{INFINITY, INFINITY, INFINITY, 0x7fffffff};
-      int key = 0;
-      if (ok) {
-        nn_seed(st, qq, hint, i, S.J, S.pts);
-        if (st.b1 < INFINITY) nn_seed_foot(st, qq, hint, i, S.J, S.pts, S.normals, S.nn);
-        key = nn_sort_key(st, S.nn);
-      }
-      const int r = nn_block_rank(key, s_off);
-      // Thread code: t (search it), -1 - t (in range, no search), INT_MIN (past the tile).
-      const int code = ok ? t : (in ? -1 - t : (int)0x80000000);
-      s_q[r] = make_float4(qq[0], qq[1], qq[2], __int_as_float(code));
-      s_st[r] = make_float4(st.b1, st.b2, st.thr, __int_as_float(st.j1));
-      __syncthreads();
-      const float4 mq = s_q[t], ms = s_st[t];
-      const int mc = __float_as_int(mq.w);
+      const int64_t i = i0 + threadIdx.x;
       bool valid = false;
-      if (mc != (int)0x80000000) {
-        ok = mc >= 0;
-        const int64_t k = i0 + (ok ? mc : -1 - mc);
-        const int64_t slot = S.rec_off + k;
-        qq[0] = mq.x;
-        qq[1] = mq.y;
-        qq[2] = mq.z;
+      if (i < end) {
+        const int64_t slot = S.rec_off + i;
+        float qq[3] = {q[3 * slot], q[3 * slot + 1], q[3 * slot + 2]};
         int best = -1;
-        if (ok) {
-          st = NNState{ms.x, ms.y, ms.z, __float_as_int(ms.w)};
-          const int c[3] = {nn_cell(qq[0], S.nn), nn_cell(qq[1], S.nn), nn_cell(qq[2], S.nn)};
+        if (nn_query_ok(qq)) {
+          int c[3] = {nn_cell(qq[0], S.nn), nn_cell(qq[1], S.nn), nn_cell(qq[2], S.nn)};
+          NNState st{INFINITY, INFINITY, INFINITY, 0x7fffffff};
+          const int32_t* hint = src + S.rec_off;
+          nn_seed(st, qq, hint, i, S.J, S.pts);
+          if (st.b1 < INFINITY) nn_seed_foot(st, qq, hint, i, S.J, S.pts, S.normals, S.nn);
           best = nn_thread_search(qq, c, S.nn, nn_margin(qq), st);
         }
         float s3[3];
@@ -314,7 +279,7 @@ __global__ void __launch_bounds__(M_NN_MAX_THREADS) k_m_nn(const MShape* __restr
         rec[6 * slot + 5] = s3[2];
       }
       const int n = __syncthreads_count(valid);
-      if (t == 0 && n) atomicAdd(nvalid + tl.shape, n);
+      if (threadIdx.x == 0 && n) atomicAdd(nvalid + tl.shape, n);
     }
   }
 }

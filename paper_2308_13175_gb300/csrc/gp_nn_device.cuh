@@ -373,46 +373,6 @@ __device__ __forceinline__ void nn_seed_foot(NNState& st, const float q[3], cons
   }
 }
 
-// Sorting a block's queries by seeded radius before the walk: the walk
-// visits about thr / cs^2 rows, so queries of similar thr have walks of
-// similar length, and a warp of them diverges less.
-constexpr int NN_SORT_BUCKETS = 16;
-constexpr int NN_SORT_MAX_WARPS = 16;  // blocks of up to 512 threads
-
-// Key of a query after seeding: thr in quarters of cs^2 (capped), or the last
-// bucket for an unseeded query (the ring search).
-__device__ __forceinline__ int nn_sort_key(const NNState& st, const NNGrid& g) {
-  if (!(st.b1 < INFINITY)) return NN_SORT_BUCKETS - 1;
-  return (int)fminf(4.0f * st.thr / (g.cs * g.cs), (float)(NN_SORT_BUCKETS - 2));
-}
-
-// Stable counting sort of one key (in [0, NN_SORT_BUCKETS)) per thread over the
-// block: returns this thread's rank (smaller key first; equal keys in thread
-// order).  Every thread of the block calls it; blockDim.x is a multiple of 32,
-// at most 32 * NN_SORT_MAX_WARPS.  s_off: NN_SORT_BUCKETS * NN_SORT_MAX_WARPS
-// ints of shared memory.
-__device__ __forceinline__ int nn_block_rank(int key, int* s_off) {
-  const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nw = blockDim.x >> 5;
-  const unsigned peers = __match_any_sync(0xffffffffu, key);
-  const int in_warp = __popc(peers & ((1u << lane) - 1u));
-  for (int k = t; k < NN_SORT_BUCKETS * nw; k += blockDim.x) s_off[k] = 0;
-  __syncthreads();
-  if (in_warp == 0) s_off[key * nw + warp] = __popc(peers);
-  __syncthreads();
-  if (t == 0) {
-    int run = 0;
-    for (int k = 0; k < NN_SORT_BUCKETS * nw; ++k) {
-      const int c = s_off[k];
-      s_off[k] = run;
-      run += c;
-    }
-  }
-  __syncthreads();
-  const int r = s_off[key * nw + warp] + in_warp;
-  __syncthreads();  // s_off is free for the next call
-  return r;
-}
-
 inline NNGrid make_grid(const gp_band* b) {
   NNGrid g;
   g.pts = b->pts_sorted;
