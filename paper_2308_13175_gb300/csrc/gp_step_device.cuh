@@ -221,7 +221,7 @@ __device__ __forceinline__ int iidx(int x, int y, int z) { return ((z + 1) * IS 
 
 
 // The L_TV sweep, one brick at a time per block of TV_SWEEP_THREADS threads
-// (each owns two vertices of the brick, stacked in z).  For each brick: stage
+// (each owns vertex l and vertex l + 256 of the brick).  For each brick: stage
 // the brick plus a two-vertex halo (12^3 values) and the T masks of its 27
 // neighbour bricks in shared memory, compute 1/TV_n on the brick plus a
 // one-vertex halo (10^3), then gather every vertex's
@@ -277,8 +277,10 @@ __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_g
 // This thread's fixed share of every brick's work, decoded once: its row
 // pieces to copy and its inner-region entries.
 constexpr int TV_TASKS = (TV_ROWS * 4 + TV_SWEEP_THREADS - 1) / TV_SWEEP_THREADS;  // 3
+constexpr int TV_INNER = (IN + TV_SWEEP_THREADS - 1) / TV_SWEEP_THREADS;          // 4
 struct TvPlan {
-  uint32_t task[TV_TASKS];  // region | local << 5 | destination << 14 | 16-byte piece << 26 | valid << 27
+  uint32_t task[TV_TASKS];   // region | local << 5 | destination << 14 | 16-byte piece << 26 | valid << 27
+  uint32_t entry[TV_INNER];  // halo index | region << 12 | local << 17 | inner << 26 | valid << 27
 };
 
 __device__ __forceinline__ TvPlan tv_plan() {
@@ -298,6 +300,17 @@ __device__ __forceinline__ TvPlan tv_plan() {
     const uint32_t dst = row * TV_ROW + col;
     const uint32_t big = (seg == 1 || seg == 2) ? 1u : 0u;
     pl.task[k] = reg | (loc << 5) | (dst << 14) | (big << 26) | (1u << 27);
+  }
+#pragma unroll
+  for (int k = 0; k < TV_INNER; ++k) {
+    const int h = threadIdx.x + k * TV_SWEEP_THREADS;
+    pl.entry[k] = 0;
+    if (h >= IN) continue;
+    const int x = h % IS - 1, y = (h / IS) % IS - 1, z = h / (IS * IS) - 1;
+    const uint32_t reg = ((z >> 3) + 1) * 9 + ((y >> 3) + 1) * 3 + ((x >> 3) + 1);
+    const uint32_t loc = ((z & 7) << 6) | ((y & 7) << 3) | (x & 7);
+    const uint32_t inner = (x >= 0 && y >= 0 && z >= 0 && x < 8 && y < 8 && z < 8) ? 1u : 0u;
+    pl.entry[k] = (uint32_t)tv_hc(x, y, z) | (reg << 12) | (loc << 17) | (inner << 26) | (1u << 27);
   }
   return pl;
 }
@@ -332,117 +345,82 @@ __device__ __forceinline__ bool tv_interior(const TvBrick& bk) {
   return bk.ox >= 2 && bk.oy >= 2 && bk.oz >= 2 && bk.ox + 9 <= bk.R && bk.oy + 9 <= bk.R && bk.oz + 9 <= bk.R;
 }
 
-// 1/TV over the inner region (x, y, z in [-1, 8]) of buffer p, one column of
-// fixed (x, y) per task: 100 columns, each split into z = -1..3 and 4..8, for
-// the first 200 threads.  The column's values at z - 1, z, z + 1 stay in
-// registers as z advances.  Adds this thread's share of the brick's own TV_i
-// to tsum.  CHECK: skip out-of-grid neighbours.
+// 1/TV over the inner region of buffer p; adds this thread's share of the
+// brick's own TV_i to tsum.  CHECK: skip out-of-grid neighbours.
 template <bool CHECK>
-__device__ __forceinline__ void tv_inverse(TvShared& sh, int p, const TvBrick& bk, float& tsum) {
-  const int t = threadIdx.x;
-  if (t >= 200) return;
+__device__ __forceinline__ void tv_inverse(TvShared& sh, int p, const TvBrick& bk, const TvPlan& pl, float& tsum) {
   const float* D = sh.D[p];
   const uint32_t* T = sh.T[p];
-  const int col = t % 100, half = t / 100;
-  const int x = col % IS - 1, y = col / IS - 1;
-  const int z0 = half ? 4 : -1, z1 = half ? 8 : 3;
-  const int rxy = ((y >> 3) + 1) * 3 + ((x >> 3) + 1);
-  const int wy = (y & 7) >> 2, bit = ((y & 3) << 3) | (x & 7);
-  const bool inner_xy = x >= 0 && y >= 0 && x < 8 && y < 8;
-  constexpr int DZ = HS * TV_ROW;  // one z step in the staged halo
-  bool okx0 = true, okx1 = true, oky0 = true, oky1 = true;
-  if (CHECK) {
-    okx0 = bk.ox + x > 0;
-    okx1 = bk.ox + x < bk.R;
-    oky0 = bk.oy + y > 0;
-    oky1 = bk.oy + y < bk.R;
-  }
-  int c = tv_hc(x, y, z0), ci = iidx(x, y, z0);
-  float dm = D[c - DZ], d0 = D[c];
-  for (int z = z0; z <= z1; ++z, c += DZ, ci += IS * IS) {
-    const float dp = D[c + DZ];
-    const int reg = rxy + ((z >> 3) + 1) * 9;
-    const uint32_t tw = T[reg * 16 + (((z & 7) << 1) | wy)];
+#pragma unroll
+  for (int k = 0; k < TV_INNER; ++k) {
+    const uint32_t e = pl.entry[k];
+    if (!(e >> 27)) continue;
+    const int h = threadIdx.x + k * TV_SWEEP_THREADS;
+    const int c = e & 4095, reg = (e >> 12) & 31, loc = (e >> 17) & 511;
     float inv = 0.f;
-    if ((tw >> bit) & 1u) {
-      bool okz0 = true, okz1 = true;
+    if ((T[reg * 16 + (loc >> 5)] >> (loc & 31)) & 1u) {
+      const float dc = D[c];
+      const int nb6[6] = {c - 1, c + 1, c - TV_ROW, c + TV_ROW, c - TV_ROW * HS, c + TV_ROW * HS};
+      bool ok[6] = {true, true, true, true, true, true};
       if (CHECK) {
-        okz0 = bk.oz + z > 0;
-        okz1 = bk.oz + z < bk.R;
+        const int x = h % IS - 1 + bk.ox, y = (h / IS) % IS - 1 + bk.oy, z = h / (IS * IS) - 1 + bk.oz;
+        ok[0] = x > 0;
+        ok[1] = x < bk.R;
+        ok[2] = y > 0;
+        ok[3] = y < bk.R;
+        ok[4] = z > 0;
+        ok[5] = z < bk.R;
       }
-      const float e0 = d0 - D[c - 1], e1 = d0 - D[c + 1], e2 = d0 - D[c - TV_ROW], e3 = d0 - D[c + TV_ROW];
-      const float e4 = d0 - dm, e5 = d0 - dp;
       float acc2 = 0.f;
-      if (okx0) acc2 = fmaf(e0, e0, acc2);
-      if (okx1) acc2 = fmaf(e1, e1, acc2);
-      if (oky0) acc2 = fmaf(e2, e2, acc2);
-      if (oky1) acc2 = fmaf(e3, e3, acc2);
-      if (okz0) acc2 = fmaf(e4, e4, acc2);
-      if (okz1) acc2 = fmaf(e5, e5, acc2);
+#pragma unroll
+      for (int t = 0; t < 6; ++t) {
+        const float d = dc - D[nb6[t]];
+        if (ok[t]) acc2 = fmaf(d, d, acc2);
+      }
       inv = acc2 > 0.f ? rsqrtf(acc2) : 0.f;  // 1/TV_n
-      if (inner_xy && z >= 0 && z < 8) tsum += acc2 * inv;  // TV_n
+      if ((e >> 26) & 1) tsum += acc2 * inv;  // TV_n
     }
-    sh.inv[ci] = inv;
-    dm = d0;
-    d0 = dp;
+    sh.inv[h] = inv;
   }
 }
 
-// dTV/dd of vertices (lx, ly, lz) and (lx, ly, lz + 1) of the brick in buffer
-// p, lx = t & 7, ly = (t >> 3) & 7, lz = 2 (t >> 6): vertex indices l0 =
-// (t & 63) + 128 (t >> 6) and l0 + 64.  0 outside the grid.
+// dTV/dd of vertex l of the brick in buffer p (0 outside the grid).
 template <bool CHECK>
-__device__ __forceinline__ void tv_gather(const TvShared& sh, int p, const TvBrick& bk, float& g0, float& g1) {
-  const int t = threadIdx.x;
-  const int lx = t & 7, ly = (t >> 3) & 7, lz = 2 * (t >> 6);
-  const float* D = sh.D[p];
-  const float* I = sh.inv;
-  constexpr int DZ = HS * TV_ROW;
-  bool okx0 = true, okx1 = true, oky0 = true, oky1 = true, in_xy = true;
+__device__ __forceinline__ float tv_gather(const TvShared& sh, int p, const TvBrick& bk, int l) {
+  const int lx = l & 7, ly = (l >> 3) & 7, lz = l >> 6;
+  bool ok[6] = {true, true, true, true, true, true};
   if (CHECK) {
-    const int x = bk.ox + lx, y = bk.oy + ly;
-    in_xy = x <= bk.R && y <= bk.R;
-    okx0 = x > 0;
-    okx1 = x < bk.R;
-    oky0 = y > 0;
-    oky1 = y < bk.R;
+    const int x = bk.ox + lx, y = bk.oy + ly, z = bk.oz + lz;
+    if (x > bk.R || y > bk.R || z > bk.R) return 0.f;  // padding slot
+    ok[0] = x > 0;
+    ok[1] = x < bk.R;
+    ok[2] = y > 0;
+    ok[3] = y < bk.R;
+    ok[4] = z > 0;
+    ok[5] = z < bk.R;
   }
-  const int c = tv_hc(lx, ly, lz), ci = iidx(lx, ly, lz);
-  // Values and inverses of the column at z - 1 .. z + 2.
-  const float dz[4] = {D[c - DZ], D[c], D[c + DZ], D[c + 2 * DZ]};
-  const float iz[4] = {I[ci - IS * IS], I[ci], I[ci + IS * IS], I[ci + 2 * IS * IS]};
-  float out[2];
+  const float* D = sh.D[p];
+  const int c = tv_hc(lx, ly, lz);
+  const float di = D[c];
+  const int ci = iidx(lx, ly, lz);
+  const float own = sh.inv[ci];
+  const int hn[6] = {c - 1, c + 1, c - TV_ROW, c + TV_ROW, c - TV_ROW * HS, c + TV_ROW * HS};
+  const int in6[6] = {ci - 1, ci + 1, ci - IS, ci + IS, ci - IS * IS, ci + IS * IS};
+  float gsum = 0.f;
 #pragma unroll
-  for (int k = 0; k < 2; ++k) {
-    const int cc = c + k * DZ, cci = ci + k * IS * IS;
-    const float di = dz[k + 1], own = iz[k + 1];
-    bool okz0 = true, okz1 = true, inside = in_xy;
-    if (CHECK) {
-      const int z = bk.oz + lz + k;
-      inside = inside && z <= bk.R;
-      okz0 = z > 0;
-      okz1 = z < bk.R;
-    }
+  for (int t = 0; t < 6; ++t) {
     // own != 0 only for i in T, whose in-grid neighbours are all stored;
     // inv[n] != 0 only for n in T (inside the grid and stored).
-    float gsum = 0.f;
-    if (okx0) gsum = fmaf(di - D[cc - 1], own + I[cci - 1], gsum);
-    if (okx1) gsum = fmaf(di - D[cc + 1], own + I[cci + 1], gsum);
-    if (oky0) gsum = fmaf(di - D[cc - TV_ROW], own + I[cci - IS], gsum);
-    if (oky1) gsum = fmaf(di - D[cc + TV_ROW], own + I[cci + IS], gsum);
-    if (okz0) gsum = fmaf(di - dz[k], own + iz[k], gsum);
-    if (okz1) gsum = fmaf(di - dz[k + 2], own + iz[k + 2], gsum);
-    out[k] = inside ? gsum : 0.f;
+    if (ok[t]) gsum = fmaf(di - D[hn[t]], own + sh.inv[in6[t]], gsum);
   }
-  g0 = out[0];
-  g1 = out[1];
+  return gsum;
 }
 
 // The sweep over work items first, first + stride, ... < n of this block.
-// src.brick(i) gives item i's TvBrick.  out(i, l0, g0, l1, g1, tsum) is called
-// by every thread once per item, in order, with the unscaled dTV/dd of the
-// thread's two vertices l0, l1 (tv_gather) and its share of the item's sum of
-// TV_i; it may synchronise the block.
+// src.brick(i) gives item i's TvBrick.  out(i, g0, g1, tsum) is called by
+// every thread once per item, in order, with the unscaled dTV/dd of vertices
+// l and l + 256 and the thread's share of the item's sum of TV_i; it may
+// synchronise the block.
 template <class Src, class Out>
 __device__ __forceinline__ void tv_sweep(const Src& src, int64_t first, int64_t stride, int64_t n, TvShared& sh,
                                          Out&& out) {
@@ -474,21 +452,23 @@ __device__ __forceinline__ void tv_sweep(const Src& src, int64_t first, int64_t 
     __syncthreads();   // ... and everyone's
     float tsum = 0.f;
     if (check)
-      tv_inverse<true>(sh, p, bk, tsum);
+      tv_inverse<true>(sh, p, bk, pl, tsum);
     else
-      tv_inverse<false>(sh, p, bk, tsum);
+      tv_inverse<false>(sh, p, bk, pl, tsum);
     __syncthreads();  // inv ready; bk[p] and slot[p] are free
     if (l == 0 && after < n) sh.bk[p] = ab;
     int rs = -1;
     if (l < 27 && after < n) rs = __ldg(ab.nbr + l);
     float g0, g1;
-    if (check)
-      tv_gather<true>(sh, p, bk, g0, g1);
-    else
-      tv_gather<false>(sh, p, bk, g0, g1);
+    if (check) {
+      g0 = tv_gather<true>(sh, p, bk, l);
+      g1 = tv_gather<true>(sh, p, bk, l + 256);
+    } else {
+      g0 = tv_gather<false>(sh, p, bk, l);
+      g1 = tv_gather<false>(sh, p, bk, l + 256);
+    }
     if (l < 27 && after < n) sh.slot[p][l] = rs;
-    const int l0 = (l & 63) + 128 * (l >> 6);
-    out(i, l0, g0, l0 + 64, g1, tsum);
+    out(i, g0, g1, tsum);
     p ^= 1;
   }
   cp_async_wait0();
