@@ -326,7 +326,7 @@ __global__ void __launch_bounds__(TV_SWEEP_THREADS, TV_BLOCKS_PER_SM) k_m_tv(con
     acc = 0.f;
   };
   tv_sweep(MultiTvSrc{shapes, tiles}, blockIdx.x, gridDim.x, ntiles, sh,
-           [&](int64_t ti, float g0, float g1, float ts) {
+           [&](int64_t ti, int l0, float g0, int l1, float g1, float ts) {
              const MTile tl = tiles[ti];
              const MShape& S = shapes[tl.shape];
              if (tl.shape != cur) {
@@ -335,9 +335,9 @@ __global__ void __launch_bounds__(TV_SWEEP_THREADS, TV_BLOCKS_PER_SM) k_m_tv(con
              }
              acc += ts;
              const float tv_scale = S.V_tv > 0 ? alpha / (float)S.V_tv : 0.f;
-             float* gp = S.grad + (int64_t)tl.first * 512 + threadIdx.x;
-             gp[0] = tv_scale * g0;
-             gp[256] = tv_scale * g1;
+             float* gp = S.grad + (int64_t)tl.first * 512;
+             gp[l0] = tv_scale * g0;
+             gp[l1] = tv_scale * g1;
            });
   if (cur >= 0) flush();
 }

@@ -191,10 +191,10 @@ __global__ void __launch_bounds__(TV_THREADS, TV_BLOCKS_PER_SM) k_tv(Grid G, con
   };
   if (TV) {
     tv_sweep(BandTvSrc{G, coord, nbrs}, blockIdx.x, gridDim.x, n_bricks, sh,
-             [&](int64_t slot, float g0, float g1, float ts) {
+             [&](int64_t slot, int l0, float g0, int l1, float g1, float ts) {
                tsum += ts;
-               emit(slot * 512 + l, tv_scale * g0);
-               emit(slot * 512 + l + 256, tv_scale * g1);
+               emit(slot * 512 + l0, tv_scale * g0);
+               emit(slot * 512 + l1, tv_scale * g1);
              });
   } else {
     for (int64_t slot = blockIdx.x; slot < n_bricks; slot += gridDim.x) {

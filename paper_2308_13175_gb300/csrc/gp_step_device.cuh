@@ -217,11 +217,16 @@ constexpr int IS = 10;            // TV edge: brick + 1 on each side
 constexpr int IN = IS * IS * IS;  // 1000
 
 __device__ __forceinline__ int hidx(int x, int y, int z) { return ((z + 2) * HS + (y + 2)) * HS + (x + 2); }
-__device__ __forceinline__ int iidx(int x, int y, int z) { return ((z + 1) * IS + (y + 1)) * IS + (x + 1); }
+// The inner region's 1/TV array: rows of IS values padded to TV_IROW floats,
+// so that the gather's warps (rows y, y + 2, y + 4, y + 6) meet no bank
+// conflict.
+constexpr int TV_IROW = 12;
+constexpr int TV_IPLANE = IS * TV_IROW;
+__device__ __forceinline__ int iidx(int x, int y, int z) { return ((z + 1) * IS + (y + 1)) * TV_IROW + (x + 1); }
 
 
 // The L_TV sweep, one brick at a time per block of TV_SWEEP_THREADS threads
-// (each owns vertex l and vertex l + 256 of the brick).  For each brick: stage
+// (each owns two vertices of the brick).  For each brick: stage
 // the brick plus a two-vertex halo (12^3 values) and the T masks of its 27
 // neighbour bricks in shared memory, compute 1/TV_n on the brick plus a
 // one-vertex halo (10^3), then gather every vertex's
@@ -255,7 +260,7 @@ struct TvBrick {
 struct TvShared {
   __align__(16) float D[2][TV_ROWS * TV_ROW];   // staged values (0 in absent bricks)
   __align__(16) uint32_t T[2][27 * 16];         // T-mask words of the 27 neighbour bricks (0 if absent)
-  float inv[IN];                                // 1/TV of T vertices of the inner region, else 0
+  float inv[IS * TV_IPLANE];                    // 1/TV of T vertices of the inner region, else 0
   int slot[2][27];
   TvBrick bk[2];
 };
@@ -277,10 +282,8 @@ __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_g
 // This thread's fixed share of every brick's work, decoded once: its row
 // pieces to copy and its inner-region entries.
 constexpr int TV_TASKS = (TV_ROWS * 4 + TV_SWEEP_THREADS - 1) / TV_SWEEP_THREADS;  // 3
-constexpr int TV_INNER = (IN + TV_SWEEP_THREADS - 1) / TV_SWEEP_THREADS;          // 4
 struct TvPlan {
-  uint32_t task[TV_TASKS];   // region | local << 5 | destination << 14 | 16-byte piece << 26 | valid << 27
-  uint32_t entry[TV_INNER];  // halo index | region << 12 | local << 17 | inner << 26 | valid << 27
+  uint32_t task[TV_TASKS];  // region | local << 5 | destination << 14 | 16-byte piece << 26 | valid << 27
 };
 
 __device__ __forceinline__ TvPlan tv_plan() {
@@ -300,17 +303,6 @@ __device__ __forceinline__ TvPlan tv_plan() {
     const uint32_t dst = row * TV_ROW + col;
     const uint32_t big = (seg == 1 || seg == 2) ? 1u : 0u;
     pl.task[k] = reg | (loc << 5) | (dst << 14) | (big << 26) | (1u << 27);
-  }
-#pragma unroll
-  for (int k = 0; k < TV_INNER; ++k) {
-    const int h = threadIdx.x + k * TV_SWEEP_THREADS;
-    pl.entry[k] = 0;
-    if (h >= IN) continue;
-    const int x = h % IS - 1, y = (h / IS) % IS - 1, z = h / (IS * IS) - 1;
-    const uint32_t reg = ((z >> 3) + 1) * 9 + ((y >> 3) + 1) * 3 + ((x >> 3) + 1);
-    const uint32_t loc = ((z & 7) << 6) | ((y & 7) << 3) | (x & 7);
-    const uint32_t inner = (x >= 0 && y >= 0 && z >= 0 && x < 8 && y < 8 && z < 8) ? 1u : 0u;
-    pl.entry[k] = (uint32_t)tv_hc(x, y, z) | (reg << 12) | (loc << 17) | (inner << 26) | (1u << 27);
   }
   return pl;
 }
@@ -345,82 +337,101 @@ __device__ __forceinline__ bool tv_interior(const TvBrick& bk) {
   return bk.ox >= 2 && bk.oy >= 2 && bk.oz >= 2 && bk.ox + 9 <= bk.R && bk.oy + 9 <= bk.R && bk.oz + 9 <= bk.R;
 }
 
-// 1/TV over the inner region of buffer p; adds this thread's share of the
-// brick's own TV_i to tsum.  CHECK: skip out-of-grid neighbours.
+// 1/TV over the inner region (x, y, z in [-1, 8]) of buffer p.  A warp takes
+// two rows (y, y + 1) of one z plane per task, 16 lanes per row of which the
+// first 10 are active: with rows TV_ROW = 20 floats apart, the two rows fall in
+// distinct banks for every one of the seven loads.  Adds this thread's share
+// of the brick's own TV_i to tsum.  CHECK: skip out-of-grid neighbours.
 template <bool CHECK>
-__device__ __forceinline__ void tv_inverse(TvShared& sh, int p, const TvBrick& bk, const TvPlan& pl, float& tsum) {
+__device__ __forceinline__ void tv_inverse(TvShared& sh, int p, const TvBrick& bk, float& tsum) {
   const float* D = sh.D[p];
   const uint32_t* T = sh.T[p];
-#pragma unroll
-  for (int k = 0; k < TV_INNER; ++k) {
-    const uint32_t e = pl.entry[k];
-    if (!(e >> 27)) continue;
-    const int h = threadIdx.x + k * TV_SWEEP_THREADS;
-    const int c = e & 4095, reg = (e >> 12) & 31, loc = (e >> 17) & 511;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int xl = lane & 15, x = xl - 1;
+  if (xl >= IS) return;
+  for (int task = warp; task < IS * IS / 2; task += TV_SWEEP_THREADS / 32) {
+    const int z = task / (IS / 2) - 1, y = 2 * (task % (IS / 2)) + (lane >> 4) - 1;
+    const int c = tv_hc(x, y, z);
+    const int reg = ((z >> 3) + 1) * 9 + ((y >> 3) + 1) * 3 + ((x >> 3) + 1);
+    const int loc = ((z & 7) << 6) | ((y & 7) << 3) | (x & 7);
     float inv = 0.f;
     if ((T[reg * 16 + (loc >> 5)] >> (loc & 31)) & 1u) {
       const float dc = D[c];
       const int nb6[6] = {c - 1, c + 1, c - TV_ROW, c + TV_ROW, c - TV_ROW * HS, c + TV_ROW * HS};
       bool ok[6] = {true, true, true, true, true, true};
       if (CHECK) {
-        const int x = h % IS - 1 + bk.ox, y = (h / IS) % IS - 1 + bk.oy, z = h / (IS * IS) - 1 + bk.oz;
-        ok[0] = x > 0;
-        ok[1] = x < bk.R;
-        ok[2] = y > 0;
-        ok[3] = y < bk.R;
-        ok[4] = z > 0;
-        ok[5] = z < bk.R;
+        const int gx = x + bk.ox, gy = y + bk.oy, gz = z + bk.oz;
+        ok[0] = gx > 0;
+        ok[1] = gx < bk.R;
+        ok[2] = gy > 0;
+        ok[3] = gy < bk.R;
+        ok[4] = gz > 0;
+        ok[5] = gz < bk.R;
       }
       float acc2 = 0.f;
 #pragma unroll
-      for (int t = 0; t < 6; ++t) {
-        const float d = dc - D[nb6[t]];
-        if (ok[t]) acc2 = fmaf(d, d, acc2);
+      for (int k = 0; k < 6; ++k) {
+        const float d = dc - D[nb6[k]];
+        if (ok[k]) acc2 = fmaf(d, d, acc2);
       }
       inv = acc2 > 0.f ? rsqrtf(acc2) : 0.f;  // 1/TV_n
-      if ((e >> 26) & 1) tsum += acc2 * inv;  // TV_n
+      if (x >= 0 && y >= 0 && z >= 0 && x < 8 && y < 8 && z < 8) tsum += acc2 * inv;  // TV_n
     }
-    sh.inv[h] = inv;
+    sh.inv[iidx(x, y, z)] = inv;
   }
 }
 
-// dTV/dd of vertex l of the brick in buffer p (0 outside the grid).
+// dTV/dd of this thread's two vertices of the brick in buffer p: (lx, ly, lz)
+// and (lx, ly + 1, lz) with lx = t & 7, ly = 2 ((t >> 3) & 3), lz = t >> 5,
+// vertex indices l0 = lx + 8 ly + 64 lz and l0 + 8.  A warp's four rows y are
+// two apart, which keeps both the staged values (rows 40 floats apart) and
+// the inverses (24 apart) free of bank conflicts.  0 outside the grid.
 template <bool CHECK>
-__device__ __forceinline__ float tv_gather(const TvShared& sh, int p, const TvBrick& bk, int l) {
-  const int lx = l & 7, ly = (l >> 3) & 7, lz = l >> 6;
-  bool ok[6] = {true, true, true, true, true, true};
-  if (CHECK) {
-    const int x = bk.ox + lx, y = bk.oy + ly, z = bk.oz + lz;
-    if (x > bk.R || y > bk.R || z > bk.R) return 0.f;  // padding slot
-    ok[0] = x > 0;
-    ok[1] = x < bk.R;
-    ok[2] = y > 0;
-    ok[3] = y < bk.R;
-    ok[4] = z > 0;
-    ok[5] = z < bk.R;
-  }
+__device__ __forceinline__ void tv_gather(const TvShared& sh, int p, const TvBrick& bk, float& g0, float& g1,
+                                          int& l0) {
+  const int t = threadIdx.x;
+  const int lx = t & 7, ly0 = 2 * ((t >> 3) & 3), lz = t >> 5;
   const float* D = sh.D[p];
-  const int c = tv_hc(lx, ly, lz);
-  const float di = D[c];
-  const int ci = iidx(lx, ly, lz);
-  const float own = sh.inv[ci];
-  const int hn[6] = {c - 1, c + 1, c - TV_ROW, c + TV_ROW, c - TV_ROW * HS, c + TV_ROW * HS};
-  const int in6[6] = {ci - 1, ci + 1, ci - IS, ci + IS, ci - IS * IS, ci + IS * IS};
-  float gsum = 0.f;
+  const float* I = sh.inv;
+  l0 = lx + 8 * ly0 + 64 * lz;
+  float out[2];
 #pragma unroll
-  for (int t = 0; t < 6; ++t) {
-    // own != 0 only for i in T, whose in-grid neighbours are all stored;
-    // inv[n] != 0 only for n in T (inside the grid and stored).
-    if (ok[t]) gsum = fmaf(di - D[hn[t]], own + sh.inv[in6[t]], gsum);
+  for (int k = 0; k < 2; ++k) {
+    const int ly = ly0 + k;
+    bool ok[6] = {true, true, true, true, true, true};
+    bool inside = true;
+    if (CHECK) {
+      const int x = bk.ox + lx, y = bk.oy + ly, z = bk.oz + lz;
+      inside = x <= bk.R && y <= bk.R && z <= bk.R;
+      ok[0] = x > 0;
+      ok[1] = x < bk.R;
+      ok[2] = y > 0;
+      ok[3] = y < bk.R;
+      ok[4] = z > 0;
+      ok[5] = z < bk.R;
+    }
+    const int c = tv_hc(lx, ly, lz), ci = iidx(lx, ly, lz);
+    const float di = D[c], own = I[ci];
+    const int hn[6] = {c - 1, c + 1, c - TV_ROW, c + TV_ROW, c - TV_ROW * HS, c + TV_ROW * HS};
+    const int in6[6] = {ci - 1, ci + 1, ci - TV_IROW, ci + TV_IROW, ci - TV_IPLANE, ci + TV_IPLANE};
+    float gsum = 0.f;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      // own != 0 only for i in T, whose in-grid neighbours are all stored;
+      // inv[n] != 0 only for n in T (inside the grid and stored).
+      if (ok[j]) gsum = fmaf(di - D[hn[j]], own + I[in6[j]], gsum);
+    }
+    out[k] = inside ? gsum : 0.f;
   }
-  return gsum;
+  g0 = out[0];
+  g1 = out[1];
 }
 
 // The sweep over work items first, first + stride, ... < n of this block.
-// src.brick(i) gives item i's TvBrick.  out(i, g0, g1, tsum) is called by
-// every thread once per item, in order, with the unscaled dTV/dd of vertices
-// l and l + 256 and the thread's share of the item's sum of TV_i; it may
-// synchronise the block.
+// src.brick(i) gives item i's TvBrick.  out(i, l0, g0, l1, g1, tsum) is called
+// by every thread once per item, in order, with the unscaled dTV/dd of the
+// thread's two vertices l0, l1 (tv_gather) and its share of the item's sum of
+// TV_i; it may synchronise the block.
 template <class Src, class Out>
 __device__ __forceinline__ void tv_sweep(const Src& src, int64_t first, int64_t stride, int64_t n, TvShared& sh,
                                          Out&& out) {
@@ -452,23 +463,21 @@ __device__ __forceinline__ void tv_sweep(const Src& src, int64_t first, int64_t 
     __syncthreads();   // ... and everyone's
     float tsum = 0.f;
     if (check)
-      tv_inverse<true>(sh, p, bk, pl, tsum);
+      tv_inverse<true>(sh, p, bk, tsum);
     else
-      tv_inverse<false>(sh, p, bk, pl, tsum);
+      tv_inverse<false>(sh, p, bk, tsum);
     __syncthreads();  // inv ready; bk[p] and slot[p] are free
     if (l == 0 && after < n) sh.bk[p] = ab;
     int rs = -1;
     if (l < 27 && after < n) rs = __ldg(ab.nbr + l);
     float g0, g1;
-    if (check) {
-      g0 = tv_gather<true>(sh, p, bk, l);
-      g1 = tv_gather<true>(sh, p, bk, l + 256);
-    } else {
-      g0 = tv_gather<false>(sh, p, bk, l);
-      g1 = tv_gather<false>(sh, p, bk, l + 256);
-    }
+    int l0;
+    if (check)
+      tv_gather<true>(sh, p, bk, g0, g1, l0);
+    else
+      tv_gather<false>(sh, p, bk, g0, g1, l0);
     if (l < 27 && after < n) sh.slot[p][l] = rs;
-    out(i, g0, g1, tsum);
+    out(i, l0, g0, l0 + 8, g1, tsum);
     p ^= 1;
   }
   cp_async_wait0();
