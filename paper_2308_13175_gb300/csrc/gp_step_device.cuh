@@ -282,8 +282,10 @@ __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_g
 // This thread's fixed share of every brick's work, decoded once: its row
 // pieces to copy and its inner-region entries.
 constexpr int TV_TASKS = (TV_ROWS * 4 + TV_SWEEP_THREADS - 1) / TV_SWEEP_THREADS;  // 3
+constexpr int TV_INNER = (IN + TV_SWEEP_THREADS - 1) / TV_SWEEP_THREADS;          // 4
 struct TvPlan {
-  uint32_t task[TV_TASKS];  // region | local << 5 | destination << 14 | 16-byte piece << 26 | valid << 27
+  uint32_t task[TV_TASKS];   // region | local << 5 | destination << 14 | 16-byte piece << 26 | valid << 27
+  uint32_t entry[TV_INNER];  // halo index | region << 12 | local << 17 | inner << 26 | valid << 27
 };
 
 __device__ __forceinline__ TvPlan tv_plan() {
@@ -303,6 +305,17 @@ __device__ __forceinline__ TvPlan tv_plan() {
     const uint32_t dst = row * TV_ROW + col;
     const uint32_t big = (seg == 1 || seg == 2) ? 1u : 0u;
     pl.task[k] = reg | (loc << 5) | (dst << 14) | (big << 26) | (1u << 27);
+  }
+#pragma unroll
+  for (int k = 0; k < TV_INNER; ++k) {
+    const int h = threadIdx.x + k * TV_SWEEP_THREADS;
+    pl.entry[k] = 0;
+    if (h >= IN) continue;
+    const int x = h % IS - 1, y = (h / IS) % IS - 1, z = h / (IS * IS) - 1;
+    const uint32_t reg = ((z >> 3) + 1) * 9 + ((y >> 3) + 1) * 3 + ((x >> 3) + 1);
+    const uint32_t loc = ((z & 7) << 6) | ((y & 7) << 3) | (x & 7);
+    const uint32_t inner = (x >= 0 && y >= 0 && z >= 0 && x < 8 && y < 8 && z < 8) ? 1u : 0u;
+    pl.entry[k] = (uint32_t)tv_hc(x, y, z) | (reg << 12) | (loc << 17) | (inner << 26) | (1u << 27);
   }
   return pl;
 }
@@ -337,47 +350,42 @@ __device__ __forceinline__ bool tv_interior(const TvBrick& bk) {
   return bk.ox >= 2 && bk.oy >= 2 && bk.oz >= 2 && bk.ox + 9 <= bk.R && bk.oy + 9 <= bk.R && bk.oz + 9 <= bk.R;
 }
 
-// 1/TV over the inner region (x, y, z in [-1, 8]) of buffer p.  A warp takes
-// two rows (y, y + 1) of one z plane per task, 16 lanes per row of which the
-// first 10 are active: with rows TV_ROW = 20 floats apart, the two rows fall in
-// distinct banks for every one of the seven loads.  Adds this thread's share
-// of the brick's own TV_i to tsum.  CHECK: skip out-of-grid neighbours.
+// 1/TV over the inner region of buffer p; adds this thread's share of the
+// brick's own TV_i to tsum.  CHECK: skip out-of-grid neighbours.
 template <bool CHECK>
-__device__ __forceinline__ void tv_inverse(TvShared& sh, int p, const TvBrick& bk, float& tsum) {
+__device__ __forceinline__ void tv_inverse(TvShared& sh, int p, const TvBrick& bk, const TvPlan& pl, float& tsum) {
   const float* D = sh.D[p];
   const uint32_t* T = sh.T[p];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int xl = lane & 15, x = xl - 1;
-  if (xl >= IS) return;
-  for (int task = warp; task < IS * IS / 2; task += TV_SWEEP_THREADS / 32) {
-    const int z = task / (IS / 2) - 1, y = 2 * (task % (IS / 2)) + (lane >> 4) - 1;
-    const int c = tv_hc(x, y, z);
-    const int reg = ((z >> 3) + 1) * 9 + ((y >> 3) + 1) * 3 + ((x >> 3) + 1);
-    const int loc = ((z & 7) << 6) | ((y & 7) << 3) | (x & 7);
+#pragma unroll
+  for (int k = 0; k < TV_INNER; ++k) {
+    const uint32_t e = pl.entry[k];
+    if (!(e >> 27)) continue;
+    const int h = threadIdx.x + k * TV_SWEEP_THREADS;
+    const int c = e & 4095, reg = (e >> 12) & 31, loc = (e >> 17) & 511;
     float inv = 0.f;
     if ((T[reg * 16 + (loc >> 5)] >> (loc & 31)) & 1u) {
       const float dc = D[c];
       const int nb6[6] = {c - 1, c + 1, c - TV_ROW, c + TV_ROW, c - TV_ROW * HS, c + TV_ROW * HS};
       bool ok[6] = {true, true, true, true, true, true};
       if (CHECK) {
-        const int gx = x + bk.ox, gy = y + bk.oy, gz = z + bk.oz;
-        ok[0] = gx > 0;
-        ok[1] = gx < bk.R;
-        ok[2] = gy > 0;
-        ok[3] = gy < bk.R;
-        ok[4] = gz > 0;
-        ok[5] = gz < bk.R;
+        const int x = h % IS - 1 + bk.ox, y = (h / IS) % IS - 1 + bk.oy, z = h / (IS * IS) - 1 + bk.oz;
+        ok[0] = x > 0;
+        ok[1] = x < bk.R;
+        ok[2] = y > 0;
+        ok[3] = y < bk.R;
+        ok[4] = z > 0;
+        ok[5] = z < bk.R;
       }
       float acc2 = 0.f;
 #pragma unroll
-      for (int k = 0; k < 6; ++k) {
-        const float d = dc - D[nb6[k]];
-        if (ok[k]) acc2 = fmaf(d, d, acc2);
+      for (int t = 0; t < 6; ++t) {
+        const float d = dc - D[nb6[t]];
+        if (ok[t]) acc2 = fmaf(d, d, acc2);
       }
       inv = acc2 > 0.f ? rsqrtf(acc2) : 0.f;  // 1/TV_n
-      if (x >= 0 && y >= 0 && z >= 0 && x < 8 && y < 8 && z < 8) tsum += acc2 * inv;  // TV_n
+      if ((e >> 26) & 1) tsum += acc2 * inv;  // TV_n
     }
-    sh.inv[iidx(x, y, z)] = inv;
+    sh.inv[(h / IS) * TV_IROW + h % IS] = inv;  // iidx of the entry
   }
 }
 
@@ -463,9 +471,9 @@ __device__ __forceinline__ void tv_sweep(const Src& src, int64_t first, int64_t 
     __syncthreads();   // ... and everyone's
     float tsum = 0.f;
     if (check)
-      tv_inverse<true>(sh, p, bk, tsum);
+      tv_inverse<true>(sh, p, bk, pl, tsum);
     else
-      tv_inverse<false>(sh, p, bk, tsum);
+      tv_inverse<false>(sh, p, bk, pl, tsum);
     __syncthreads();  // inv ready; bk[p] and slot[p] are free
     if (l == 0 && after < n) sh.bk[p] = ab;
     int rs = -1;
