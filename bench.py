@@ -99,6 +99,12 @@ def fwd_bwd_adam(per_kernel: dict, names, queries_per_step: float, V_trainable: 
             "achieved_gbs": round(gbs, 1), "peak_gbs": peak, "frac": round(gbs / peak, 4)}
 
 
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of
+# the dominant kernel from one ncu capture of this build (profiles/), by
+# workload; a kernel changed since its capture must be dropped from here.
+NCU_TRAFFIC = {("object", "k_nn"): 10_772_992, ("scene", "k_nn_sorted"): 1_132_552_704}
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -358,8 +364,8 @@ def run_ours(args, world, rank, local):
     dk = per_kernel[dom]
     achieved = dk["gbs"] or 0.0
     roofline = {"bound": KERNEL_BOUND.get(dom, "hbm"), "kernel": dom, "achieved": achieved, "peak": peak,
-                "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
-                "peak_kind": peak_kind}
+                "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "traffic": NCU_TRAFFIC.get((args.workload, dom)), "peak_kind": peak_kind}
 
     # End to end through the public API: host queries (pinned) -> device,
     # NN + step + update, loss back to the host, every step.
