@@ -24,6 +24,7 @@
 namespace {
 
 constexpr int Q_THREADS = 256;
+constexpr int Q_BLOCKS_PER_SM = 3;  // resident k_query blocks per SM at its register cap
 constexpr int TV_THREADS = TV_SWEEP_THREADS;
 // Loss slots from the per-block partial sums, in a fixed order (run by one
 // whole block).
@@ -127,7 +128,7 @@ __device__ __forceinline__ void block_store3(double* __restrict__ partials, floa
 }
 
 template <bool DET, bool GRAD, bool LAST>
-__global__ void __launch_bounds__(Q_THREADS, 3) k_query(Grid G, const float* __restrict__ rec, int64_t B,
+__global__ void __launch_bounds__(Q_THREADS, Q_BLOCKS_PER_SM) k_query(Grid G, const float* __restrict__ rec, int64_t B,
                                                      const int32_t* __restrict__ bv, float beta, float gamma,
                                                      float* __restrict__ grad, unsigned long long* __restrict__ acc,
                                                      double* __restrict__ partials, int32_t* __restrict__ err,
@@ -226,8 +227,12 @@ __global__ void __launch_bounds__(256) k_adam(const int32_t* __restrict__ active
     adam_quad(__ldg(active + (i >> 7)), (int)(i & 127), masks, grad, D, m, v, lr, b1, b2, eps, bc1, bc2);
 }
 
+// One resident wave of k_query: each thread takes several records and the
+// block's loss reduction runs once per thread instead of once per record.
 unsigned q_grid(const gp_ctx* ctx, int64_t B) {
-  return gp_blocks(B, Q_THREADS, GP_MAX_PARTIAL_BLOCKS);
+  int64_t cap = (int64_t)ctx->num_sms * Q_BLOCKS_PER_SM;
+  if (cap > GP_MAX_PARTIAL_BLOCKS) cap = GP_MAX_PARTIAL_BLOCKS;
+  return gp_blocks(B, Q_THREADS, cap);
 }
 
 unsigned tv_grid(const gp_ctx* ctx, int64_t n_bricks) {
