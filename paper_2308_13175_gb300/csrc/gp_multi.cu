@@ -350,27 +350,38 @@ __global__ void __launch_bounds__(256) k_m_query(const MShape* __restrict__ shap
                                                  const int32_t* __restrict__ nvalid, float beta, float gamma,
                                                  double* __restrict__ sums, int32_t* __restrict__ err) {
   __shared__ float red[32];
+  // Loss sums stay in registers over a block's run of tiles of one cloud and
+  // are reduced over the block when the cloud changes and at the end.
+  int cur = -1;
+  float sp = 0.f, sg = 0.f, ss = 0.f;
+  auto flush = [&]() {
+    const float a = block_sum(sp, red);
+    const float b = block_sum(sg, red);
+    const float c = block_sum(ss, red);
+    if (threadIdx.x == 0) {
+      if (a != 0.f) atomicAdd(sums + 4 * cur + 0, (double)a);
+      if (b != 0.f) atomicAdd(sums + 4 * cur + 1, (double)b);
+      if (c != 0.f) atomicAdd(sums + 4 * cur + 2, (double)c);
+    }
+    sp = sg = ss = 0.f;
+  };
   for (int64_t ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
     const MTile tl = tiles[ti];
     const MShape& S = shapes[tl.shape];
+    if (tl.shape != cur) {
+      if (cur >= 0) flush();
+      cur = tl.shape;
+    }
     const int bv = nvalid[tl.shape];
     const float w = bv > 0 ? 1.0f / (float)bv : 0.f;
     const int64_t end = min((int64_t)tl.first + tq, S.B);
-    float sp = 0.f, sg = 0.f, ss = 0.f;
     for (int64_t i = (int64_t)tl.first + threadIdx.x; i < end; i += blockDim.x) {
       float qq[3], s3[3];
       load_rec(rec, S.rec_off + i, qq, s3);
       query_record<false, true>(S.G, qq, s3, w, beta, gamma, S.grad, nullptr, err, sp, sg, ss);
     }
-    const float a = block_sum(sp, red);
-    const float b = block_sum(sg, red);
-    const float c = block_sum(ss, red);
-    if (threadIdx.x == 0) {
-      if (a != 0.f) atomicAdd(sums + 4 * tl.shape + 0, (double)a);
-      if (b != 0.f) atomicAdd(sums + 4 * tl.shape + 1, (double)b);
-      if (c != 0.f) atomicAdd(sums + 4 * tl.shape + 2, (double)c);
-    }
   }
+  if (cur >= 0) flush();
 }
 
 // Adam on every active brick of every cloud, as step t + 1, learning rate
