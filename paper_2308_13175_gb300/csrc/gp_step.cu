@@ -147,13 +147,12 @@ __global__ void __launch_bounds__(Q_THREADS, Q_BLOCKS_PER_SM) k_query(Grid G, co
   if (LAST) finish_if_last(partials, fa);
 }
 
-// One block of 512 threads per brick (grid-stride over bricks).  The brick and
-// a two-vertex halo (12^3 values, with stored / in-grid / T flags) are staged in
-// shared memory; TV and 1/TV are computed for the brick plus a one-vertex halo
-// (10^3), and each of the 512 vertices then gathers its gradient from shared
-// memory.  Writes the gradient of every stored slot: alpha/|T| * dTV/dd_i (+ the
-// fixed-point query sums in deterministic mode, which are cleared for the next
-// step).  Each TV_i enters the loss sum once, from the brick that stores i.
+// The L_TV sweep over the band's bricks (tv_sweep: one brick at a time per
+// block of TV_THREADS, one persistent wave of blocks, the next brick's halo
+// copied while the current one is computed).  Writes the gradient of every
+// stored slot: alpha/|T| * dTV/dd_i (+ the fixed-point query sums in
+// deterministic mode, which are cleared for the next step).  Each TV_i enters
+// the loss sum once, from the brick that stores i.
 struct BandTvSrc {
   Grid G;
   const int32_t* coord;
