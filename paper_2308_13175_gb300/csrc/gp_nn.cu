@@ -201,7 +201,12 @@ __global__ void __launch_bounds__(128) k_normals(NNGrid g, int64_t J, const floa
 
 // One thread per query.  Queries with a NaN, infinite or huge coordinate (whose
 // squared distances would overflow float32) get -1 and a NaN surface point.
-__global__ void __launch_bounds__(256) k_nn(NNGrid g, const float* __restrict__ qin, int64_t n,
+#ifdef GP_NN_MIN_BLOCKS
+#define GP_NN_BOUNDS __launch_bounds__(256, GP_NN_MIN_BLOCKS)
+#else
+#define GP_NN_BOUNDS __launch_bounds__(256)
+#endif
+__global__ void GP_NN_BOUNDS k_nn(NNGrid g, const float* __restrict__ qin, int64_t n,
                                             const int32_t* __restrict__ hint, int64_t J,
                                             const float* __restrict__ pts_orig, int32_t* __restrict__ nn_out,
                                             float* __restrict__ rec, Grid band, int32_t* __restrict__ nvalid,
