@@ -117,7 +117,7 @@ typedef struct gp_grid_desc {
                       point (0 = do not compute; gp_sample then fails)           */
   int32_t nn_grid; /* cells per axis of the point cell list used by gp_nn
                       (0 = chosen for about 6.5 points per occupied cell, at
-                      most 512)                                                  */
+                      most sqrt(J/3) and 512)                                    */
   uint32_t flags;  /* GP_BAND_* flags                                            */
 } gp_grid_desc;
 

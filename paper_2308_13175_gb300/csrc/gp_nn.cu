@@ -386,8 +386,13 @@ gp_status gp_build_points(gp_band* b, const float* pts_dev) {
     // optimum (4.9 to 8 points per cell were within 1-3% on the benchmark
     // clouds).  The cloud is a surface, so the cells it occupies at grid G are
     // about n_occ (G / R)^2, n_occ being its occupied cells at the band's R.
+    // That estimate fails for a cloud too sparse to cover its surface at R
+    // (n_occ near J); there sqrt(J / 3) cells per axis, the bound that served
+    // such clouds before, is the smaller one and is taken.
     const double occ = (double)std::max<int64_t>(b->n_occ, 1);
-    const int G = (int)((double)b->R * std::sqrt((double)J / (NN_POINTS_PER_CELL * occ)));
+    const double g_area = (double)b->R * std::sqrt((double)J / (NN_POINTS_PER_CELL * occ));
+    const double g_count = std::sqrt((double)J / 3.0);
+    const int G = (int)std::min(g_area, g_count);
     b->G = std::min(std::max(G, 4), 512);
   }
   const int G = b->G;
