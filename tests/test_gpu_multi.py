@@ -145,6 +145,43 @@ def test_multi_steps_match_single_band_calls_and_oracle(gb, ctx, clouds, spatial
     multi.close()
 
 
+def test_multi_tiny_clouds(gb, ctx):
+    """Edge sizes: a one-point cloud (sigma 0, batch of one), a seven-point cloud
+    whose epochs end in a short batch, and a 600-point cloud, in one multi; four
+    steps, records bit-exact against the single-band calls and loss and
+    gradient against the oracle."""
+    import torch
+    tiny = [
+        (synth.sphere_cloud(1, 0.3, seed=11), 8, 1, 1, 1, 1),
+        (synth.sphere_cloud(7, 0.4, seed=12), 16, 1, 1, 21, 8),
+        (synth.sphere_cloud(600, 0.5, seed=13), 16, 2, 2, 1200, 500),
+    ]
+    bands = _make_bands(gb, ctx, tiny)
+    sets = [o.band_sets(pts, R, M1, M2) for pts, R, M1, M2, _, _ in tiny]
+    multi = gb.gp_multi_create(ctx, bands, [c[4] for c in tiny], [c[5] for c in tiny], seed=SEED)
+    loss = torch.zeros(8 * len(tiny), dtype=torch.float32, device="cuda")
+    for t in range(4):
+        before = [export_band(b) for b in bands]
+        gb.gp_multi_step(multi, loss, W, lr=LR)
+        L = loss.cpu().numpy().reshape(len(tiny), 8)
+        for k, ((pts, R, M1, M2, Q, B), band) in enumerate(zip(tiny, bands)):
+            rec = gb.gp_multi_buffers(multi, k)[0].cpu().numpy()
+            want, _, count = _single_records(gb, band, k, t, Q, B, True)
+            assert np.array_equal(_bits(rec[:count]), _bits(want)), f"cloud {k} step {t}"
+            assert np.all(np.isnan(rec[count:, :3]))
+            ijk, d0, fl, exists = before[k]
+            D = dense_from_band(d0.astype(np.float64), ijk, exists, R)
+            ref = o.step_loss_grad(D, R, sets[k], rec[:count, :3], rec[:count, 3:], W)
+            assert L[k, gb.GP_LOSS_BV] == ref["Bv"] and ref["Bv"] >= 1
+            for slot, key in ((gb.GP_LOSS_PULL, "l_pull"), (gb.GP_LOSS_TV, "l_tv"), (gb.GP_LOSS_TOTAL, "loss")):
+                assert_rel(L[k, slot], ref[key], what=f"cloud {k} step {t} {key}")
+            grad = gb.gp_multi_buffers(multi, k)[2].cpu().numpy()
+            keys = vertex_keys(ijk[exists], R)
+            assert_grad_close(grad[exists], ref["grad"][keys], ref["abs_terms"][keys], what=f"cloud {k} step {t}")
+    assert gb.gp_multi_get_info(multi)["error_bits"] == 0
+    multi.close()
+
+
 def test_multi_resume_mid_epoch(gb, ctx, clouds):
     """set_step into the middle of an epoch rebuilds that epoch's order first."""
     import torch
