@@ -147,9 +147,10 @@ def test_multi_steps_match_single_band_calls_and_oracle(gb, ctx, clouds, spatial
 
 def test_multi_tiny_clouds(gb, ctx):
     """Edge sizes: a one-point cloud (sigma 0, batch of one), a seven-point cloud
-    whose epochs end in a short batch, and a 600-point cloud, in one multi; four
-    steps, records bit-exact against the single-band calls and loss and
-    gradient against the oracle."""
+    whose epochs end in a short batch (its sigma spans the cloud, so whole
+    batches can fall outside the band: B_v = 0), and a 600-point cloud, in one
+    multi; four steps, records bit-exact against the single-band calls and loss
+    and gradient against the oracle."""
     import torch
     tiny = [
         (synth.sphere_cloud(1, 0.3, seed=11), 8, 1, 1, 1, 1),
@@ -172,7 +173,9 @@ def test_multi_tiny_clouds(gb, ctx):
             ijk, d0, fl, exists = before[k]
             D = dense_from_band(d0.astype(np.float64), ijk, exists, R)
             ref = o.step_loss_grad(D, R, sets[k], rec[:count, :3], rec[:count, 3:], W)
-            assert L[k, gb.GP_LOSS_BV] == ref["Bv"] and ref["Bv"] >= 1
+            assert L[k, gb.GP_LOSS_BV] == ref["Bv"], f"cloud {k} step {t}"
+            if k == 0:  # sigma 0: the one query is the point itself, always valid
+                assert ref["Bv"] == 1
             for slot, key in ((gb.GP_LOSS_PULL, "l_pull"), (gb.GP_LOSS_TV, "l_tv"), (gb.GP_LOSS_TOTAL, "loss")):
                 assert_rel(L[k, slot], ref[key], what=f"cloud {k} step {t} {key}")
             grad = gb.gp_multi_buffers(multi, k)[2].cpu().numpy()
