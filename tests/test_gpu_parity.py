@@ -190,6 +190,24 @@ def test_nn_sorted_large_seeded_batch(gb, ctx, object100k):
     assert np.array_equal(got[sel], o.nearest_point(q[sel], object100k))
 
 
+def test_nn_long_cell_row(gb, ctx):
+    """70,000 points on one line along x all fall in one row of search cells,
+    more than the 16-bit row offsets hold: that row keeps 32-bit cell starts.
+    Seeded and unseeded queries around the line and a sphere next to it match
+    brute force."""
+    rng = np.random.default_rng(8)
+    line = np.stack([rng.uniform(-0.9, 0.9, 70_000), np.full(70_000, 0.1), np.full(70_000, -0.2)], 1)
+    ball = synth.sphere_cloud(3000, 0.2, seed=9) + np.array([0.0, -0.5, 0.4], np.float32)
+    pts = np.concatenate([line, ball]).astype(np.float32)
+    band = _band(gb, ctx, pts, 64, 1, 1, knn_k=0)
+    src = rng.integers(0, len(pts), 4000)
+    q = (pts[src] + rng.normal(scale=0.02, size=(4000, 3))).astype(np.float32)
+    want = o.nearest_point(q, pts)
+    nn_seeded, _ = _nn_gpu(gb, band, q, src.astype(np.int64))
+    nn_plain, _ = _nn_gpu(gb, band, q)
+    assert np.array_equal(nn_seeded, want) and np.array_equal(nn_plain, want)
+
+
 def test_nn_counts_valid_records(gb, ctx, sphere5k):
     import torch
     R = 64
