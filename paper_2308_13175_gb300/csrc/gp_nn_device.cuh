@@ -25,11 +25,13 @@ struct NNGrid {
 // the row's first point plus a 16-bit offset within the row, half the bytes of
 // a 32-bit table; rows of more than 65535 points keep the 32-bit starts.
 __device__ __forceinline__ void nn_row_range(const NNGrid& g, int64_t r, int xa, int xb, int& a, int& e) {
+  // The three loads are independent (the offsets of a long row are unused).
+  const uint16_t* o = g.roff + r * (g.G + 1);
   const int b = __ldg(g.rbase + r);
+  const int oa = __ldg(o + xa), oe = __ldg(o + xb + 1);
   if (b >= 0) {
-    const uint16_t* o = g.roff + r * (g.G + 1);
-    a = b + (int)__ldg(o + xa);
-    e = b + (int)__ldg(o + xb + 1);
+    a = b + oa;
+    e = b + oe;
   } else {
     const int32_t* st = g.start + r * g.G;
     a = __ldg(st + xa);
