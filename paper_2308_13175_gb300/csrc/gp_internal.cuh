@@ -79,9 +79,7 @@ struct gp_band {
   // Point cloud: original order copy, cell list sorted copy, sigma, permutation.
   float* pts = nullptr;            // J x 3
   float4* pts_sorted = nullptr;    // J: x, y, z, original index (int bits)
-  int32_t* cell_start = nullptr;   // G^3 + 1 (freed after set-up unless some row holds > 65535 points)
-  int32_t* row_base = nullptr;     // G^2: first point of each cell row (y, z), -1 for a long row
-  uint16_t* row_off = nullptr;     // G^2 x (G + 1): cell starts relative to the row's first point
+  int32_t* cell_start = nullptr;   // G^3 + 1
   float* sigma = nullptr;          // J
   float* normals = nullptr;        // J x 3: unit normal estimate (PCA of the sigma-ball), seeds gp_nn
   int32_t* perm = nullptr;         // J: Pi_e of the cached epoch

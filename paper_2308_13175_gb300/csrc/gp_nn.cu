@@ -376,28 +376,6 @@ static gp_status build_emit_order(gp_band* b) {
 
 constexpr double NN_POINTS_PER_CELL = 6.5;
 
-// Per row r = cz G + cy of the cell list: its first point (or -1 when the row
-// holds more than 65535 points) and, for x in [0, G], the start of cell x
-// relative to it.
-__global__ void k_row_offsets(const int32_t* __restrict__ start, int G, int32_t* __restrict__ rbase,
-                              uint16_t* __restrict__ roff, int32_t* __restrict__ long_rows) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= (int64_t)G * G * (G + 1)) return;
-  const int64_t r = i / (G + 1);
-  const int x = (int)(i - r * (G + 1));
-  const int32_t base = start[r * G];
-  const int32_t len = start[(r + 1) * G] - base;  // start has G^3 + 1 entries
-  if (len > 65535) {
-    if (x == 0) {
-      rbase[r] = -1;
-      atomicAdd(long_rows, 1);
-    }
-    return;
-  }
-  if (x == 0) rbase[r] = base;
-  roff[i] = (uint16_t)(start[r * G + x] - base);
-}
-
 // Point copy, cell list and sigma (called by gp_build_band).
 gp_status gp_build_points(gp_band* b, const float* pts_dev) {
   gp_ctx* ctx = b->ctx;
@@ -450,30 +428,6 @@ gp_status gp_build_points(gp_band* b, const float* pts_dev) {
   cudaFree(cursor);
   if (st) return st;
   if (e != cudaSuccess) return gp_cuda_fail(ctx, e, "point cell list");
-  // Compact cell starts for the search: row bases and 16-bit offsets.
-  {
-    const int64_t nrow = (int64_t)G * G;
-    int32_t* long_rows = nullptr;
-    if ((st = gp_alloc(ctx, &b->row_base, nrow, "cell row bases"))) return st;
-    if ((st = gp_alloc(ctx, &b->row_off, nrow * (G + 1), "cell row offsets"))) return st;
-    if ((st = gp_alloc(ctx, &long_rows, 1, "long-row count"))) return st;
-    int32_t n_long = 0;
-    cudaError_t e2 = cudaMemsetAsync(long_rows, 0, sizeof(int32_t), s);
-    if (e2 == cudaSuccess) {
-      k_row_offsets<<<gp_blocks(nrow * (G + 1), 256), 256, 0, s>>>(b->cell_start, G, b->row_base, b->row_off,
-                                                                  long_rows);
-      e2 = cudaGetLastError();
-    }
-    if (e2 == cudaSuccess) e2 = cudaMemcpyAsync(&n_long, long_rows, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
-    if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(s);
-    cudaFree(long_rows);
-    if (e2 != cudaSuccess) return gp_cuda_fail(ctx, e2, "cell row offsets");
-    if (n_long == 0) {  // every row fits the 16-bit offsets: the 32-bit table is not needed
-      gp_free(b->cell_start);
-      b->cell_start = nullptr;
-    }
-  }
-  g = make_grid(b);
   if (b->knn_k > 0) {
     if ((st = gp_alloc(ctx, &b->sigma, J, "sigma"))) return st;
     if ((st = gp_alloc(ctx, &b->perm, J, "permutation"))) return st;

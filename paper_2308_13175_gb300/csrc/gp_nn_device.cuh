@@ -13,31 +13,11 @@ constexpr float NN_TINY = 1e-30f;
 
 struct NNGrid {
   const float4* __restrict__ pts;      // sorted by cell: x, y, z, original index bits
-  const int32_t* __restrict__ rbase;   // G^2 rows (y, z): first point of the row, or -1 for a long row
-  const uint16_t* __restrict__ roff;   // G^2 x (G + 1): cell starts relative to the row's first point
-  const int32_t* __restrict__ start;   // G^3 + 1 cell starts, kept only if some row is long (else null)
+  const int32_t* __restrict__ start;   // G^3 + 1
   int G;
   float half_g;  // G / 2
   float cs;      // 2 / G
 };
-
-// Point range [a, e) of the cells xa..xb of row r = cz G + cy.  Cell starts are
-// the row's first point plus a 16-bit offset within the row, half the bytes of
-// a 32-bit table; rows of more than 65535 points keep the 32-bit starts.
-__device__ __forceinline__ void nn_row_range(const NNGrid& g, int64_t r, int xa, int xb, int& a, int& e) {
-  // The three loads are independent (the offsets of a long row are unused).
-  const uint16_t* o = g.roff + r * (g.G + 1);
-  const int b = __ldg(g.rbase + r);
-  const int oa = __ldg(o + xa), oe = __ldg(o + xb + 1);
-  if (b >= 0) {
-    a = b + oa;
-    e = b + oe;
-  } else {
-    const int32_t* st = g.start + r * g.G;
-    a = __ldg(st + xa);
-    e = __ldg(st + xb + 1);
-  }
-}
 
 __device__ __forceinline__ int nn_cell(float x, const NNGrid& g) {
   float t = __fmul_rn(__fadd_rn(x, 1.0f), g.half_g);
@@ -78,23 +58,15 @@ __device__ __forceinline__ void nn_ring(const int c[3], int r, const NNGrid& g, 
     for (int dy = -r; dy <= r; ++dy) {
       int cy = c[1] + dy;
       if (cy < 0 || cy >= G) continue;
-      const int64_t row = (int64_t)cz * G + cy;
+      int64_t row = ((int64_t)cz * G + cy) * G;
       bool full = (dz == -r || dz == r || dy == -r || dy == r);
-      int a, e;
       if (full) {
         int x0 = max(c[0] - r, 0), x1 = min(c[0] + r, G - 1);
-        nn_row_range(g, row, x0, x1, a, e);
-        visit(a, e);
+        visit(__ldg(g.start + row + x0), __ldg(g.start + row + x1 + 1));
       } else {
         int xa = c[0] - r, xb = c[0] + r;
-        if (xa >= 0) {
-          nn_row_range(g, row, xa, xa, a, e);
-          visit(a, e);
-        }
-        if (xb < G) {
-          nn_row_range(g, row, xb, xb, a, e);
-          visit(a, e);
-        }
+        if (xa >= 0) visit(__ldg(g.start + row + xa), __ldg(g.start + row + xa + 1));
+        if (xb < G) visit(__ldg(g.start + row + xb), __ldg(g.start + row + xb + 1));
       }
     }
   }
@@ -181,9 +153,8 @@ __device__ __forceinline__ void nn_row_ring(const float q[3], const int c[3], in
         xa = nn_cell(q[0] - rad, g);
         xb = nn_cell(q[0] + rad, g);
       }
-      int a, e;
-      nn_row_range(g, (int64_t)cz * G + cy, xa, xb, a, e);
-      visit(a, e);
+      int64_t row = ((int64_t)cz * G + cy) * G;
+      visit(__ldg(g.start + row + xa), __ldg(g.start + row + xb + 1));
       if (r == 0) break;
     }
   }
@@ -284,9 +255,8 @@ __device__ __forceinline__ void nn_ball_walk(const float q[3], const int c[3], c
           }
           const float rad = sqrtf(thr - lyz2) * 1.000001f + margin;
           const int xa = nn_cell(q[0] - rad, g), xb = nn_cell(q[0] + rad, g);
-          int a, e;
-          nn_row_range(g, (int64_t)cz * G + cy, xa, xb, a, e);
-          visit(a, e);
+          const int64_t row = ((int64_t)cz * G + cy) * G;
+          visit(__ldg(g.start + row + xa), __ldg(g.start + row + xb + 1));
         }
       }
     }
@@ -394,8 +364,8 @@ __device__ __forceinline__ void nn_seed_foot(NNState& st, const float q[3], cons
   const float s0 = pts_orig[3 * (int64_t)j], s1 = pts_orig[3 * (int64_t)j + 1], s2 = pts_orig[3 * (int64_t)j + 2];
   const float h = (q[0] - s0) * n0 + (q[1] - s1) * n1 + (q[2] - s2) * n2;
   const int cx = nn_cell(q[0] - h * n0, g), cy = nn_cell(q[1] - h * n1, g), cz = nn_cell(q[2] - h * n2, g);
-  int a, b;
-  nn_row_range(g, (int64_t)cz * g.G + cy, cx, cx, a, b);
+  const int64_t cell = ((int64_t)cz * g.G + cy) * g.G + cx;
+  const int a = __ldg(g.start + cell), b = __ldg(g.start + cell + 1);
   for (int p = a; p < b; ++p) {
     float4 P = __ldg(g.pts + p);
     float dx = q[0] - P.x, dy = q[1] - P.y, dz = q[2] - P.z;
@@ -406,8 +376,6 @@ __device__ __forceinline__ void nn_seed_foot(NNState& st, const float q[3], cons
 inline NNGrid make_grid(const gp_band* b) {
   NNGrid g;
   g.pts = b->pts_sorted;
-  g.rbase = b->row_base;
-  g.roff = b->row_off;
   g.start = b->cell_start;
   g.G = b->G;
   g.half_g = 0.5f * (float)b->G;
