@@ -191,10 +191,9 @@ def test_nn_sorted_large_seeded_batch(gb, ctx, object100k):
 
 
 def test_nn_long_cell_row(gb, ctx):
-    """70,000 points on one line along x all fall in one row of search cells,
-    more than the 16-bit row offsets hold: that row keeps 32-bit cell starts.
-    Seeded and unseeded queries around the line and a sphere next to it match
-    brute force."""
+    """70,000 points on one line along x all fall in one row of search cells
+    (a long row, many points per cell).  Seeded and unseeded queries around the
+    line and a sphere next to it match brute force."""
     rng = np.random.default_rng(8)
     line = np.stack([rng.uniform(-0.9, 0.9, 70_000), np.full(70_000, 0.1), np.full(70_000, -0.2)], 1)
     ball = synth.sphere_cloud(3000, 0.2, seed=9) + np.array([0.0, -0.5, 0.4], np.float32)
