@@ -201,10 +201,13 @@ __global__ void __launch_bounds__(128) k_normals(NNGrid g, int64_t J, const floa
 
 // One thread per query.  Queries with a NaN, infinite or huge coordinate (whose
 // squared distances would overflow float32) get -1 and a NaN surface point.
+#ifndef GP_NN_BLOCK
+#define GP_NN_BLOCK 256
+#endif
 #ifdef GP_NN_MIN_BLOCKS
-#define GP_NN_BOUNDS __launch_bounds__(256, GP_NN_MIN_BLOCKS)
+#define GP_NN_BOUNDS __launch_bounds__(GP_NN_BLOCK, GP_NN_MIN_BLOCKS)
 #else
-#define GP_NN_BOUNDS __launch_bounds__(256)
+#define GP_NN_BOUNDS __launch_bounds__(GP_NN_BLOCK)
 #endif
 __global__ void GP_NN_BOUNDS k_nn(NNGrid g, const float* __restrict__ qin, int64_t n,
                                             const int32_t* __restrict__ hint, int64_t J,
@@ -477,7 +480,7 @@ extern "C" gp_status gp_nn(gp_band* b, const float* q_dev, int64_t n, const int3
                   g, q_dev, n, hint_dev, b->J, b->pts, nn_dev, rec_dev, band, nvalid_dev, b->normals));
     return GP_OK;
   }
-  GP_KERNEL(ctx, "k_nn", k_nn<<<gp_blocks(n, 256), 256, 0, ctx->stream>>>(g, q_dev, n, hint_dev, b->J, b->pts,
+  GP_KERNEL(ctx, "k_nn", k_nn<<<gp_blocks(n, GP_NN_BLOCK), GP_NN_BLOCK, 0, ctx->stream>>>(g, q_dev, n, hint_dev, b->J, b->pts,
                                                                            nn_dev, rec_dev, band, nvalid_dev,
                                                                            b->normals));
   return GP_OK;
