@@ -66,25 +66,35 @@ __global__ void k_sample(const float* __restrict__ pts, const float* __restrict_
   put_query(i, gp_draw_query(pts, sigma, j, k, epoch, k0, k1), j, k, q, src, pos);
 }
 
-// Pass 1: queries owned by each tile of sorted points.
+// Pass 1: queries owned by each tile of sorted points (GP_ORDER_TILE points,
+// one per thread), COUNT_TILES tiles per block; only the tile totals are
+// needed, so each is a warp-sum reduction with one barrier for all four.
+constexpr int COUNT_TILES = 4;
+constexpr int COUNT_WARPS = GP_ORDER_THREADS / 32;
+
 __global__ void __launch_bounds__(GP_ORDER_THREADS) k_order_count(const int32_t* __restrict__ eslot, int64_t J,
                                                                   int64_t first, int64_t last,
-                                                                  int32_t* __restrict__ tiles) {
-  int64_t base = (int64_t)blockIdx.x * GP_ORDER_TILE + (int64_t)threadIdx.x * GP_ORDER_PER_THREAD;
-  int c = 0;
+                                                                  int32_t* __restrict__ tiles, int64_t ntiles) {
+  static_assert(GP_ORDER_PER_THREAD == 1, "one point per thread and tile");
+  __shared__ int red[COUNT_TILES][COUNT_WARPS];
+  const int64_t tile0 = (int64_t)blockIdx.x * COUNT_TILES;
 #pragma unroll
-  for (int u = 0; u < GP_ORDER_PER_THREAD; ++u) {
-    int64_t t = base + u;
+  for (int k = 0; k < COUNT_TILES; ++k) {
+    const int64_t t = (tile0 + k) * GP_ORDER_TILE + threadIdx.x;
+    int c = 0;
     if (t < J) {
       int64_t r0;
-      int n;
-      owned_range(eslot[t], J, first, last, r0, n);
-      c += n;
+      owned_range(eslot[t], J, first, last, r0, c);
     }
+    c = gp_warp_sum_i(c);
+    if ((threadIdx.x & 31) == 0) red[k][threadIdx.x >> 5] = c;
   }
-  int excl;
-  int total = block_exclusive_scan(c, &excl);
-  if (threadIdx.x == 0) tiles[blockIdx.x] = total;
+  __syncthreads();
+  if (threadIdx.x < COUNT_TILES && tile0 + threadIdx.x < ntiles) {
+    int total = 0;
+    for (int w = 0; w < COUNT_WARPS; ++w) total += red[threadIdx.x][w];
+    tiles[tile0 + threadIdx.x] = total;
+  }
 }
 
 // Pass 2: exclusive scan of the tile counts in place (one block, any length,
@@ -176,8 +186,8 @@ extern "C" gp_status gp_sample(gp_band* b, uint64_t seed, uint32_t epoch, int64_
   const int64_t J = b->J, last = first + count;
   const int64_t ntiles = (J + GP_ORDER_TILE - 1) / GP_ORDER_TILE;
   GP_KERNEL(ctx, "k_order_count",
-            k_order_count<<<(unsigned)ntiles, GP_ORDER_THREADS, 0, ctx->stream>>>(b->emit_slot, J, first, last,
-                                                                                 b->order_tiles));
+            k_order_count<<<(unsigned)((ntiles + COUNT_TILES - 1) / COUNT_TILES), GP_ORDER_THREADS, 0,
+                            ctx->stream>>>(b->emit_slot, J, first, last, b->order_tiles, ntiles));
   GP_KERNEL(ctx, "k_order_tiles", k_order_tiles<<<1, GP_ORDER_THREADS, 0, ctx->stream>>>(b->order_tiles, ntiles));
   GP_KERNEL(ctx, "k_order_emit",
             k_order_emit<<<(unsigned)ntiles, GP_ORDER_THREADS, 0, ctx->stream>>>(
