@@ -170,40 +170,24 @@ __global__ void k_m_sample(const MShape* __restrict__ shapes, const MTile* __res
 
 // Spatial order, pass 1: queries of the batch owned by each point tile (the
 // cloud's points in Morton order; point j owns positions Pi_e^-1(j) + r J).
-// M_COUNT_TILES tiles per block and round; only the totals are needed, each a
-// warp-sum reduction, one barrier for all of them.
-constexpr int M_COUNT_TILES = 4;
-
 __global__ void __launch_bounds__(PT_TILE) k_m_order_count(const MShape* __restrict__ shapes,
                                                            const MTile* __restrict__ tiles, int64_t ntiles,
                                                            const int64_t* __restrict__ t_dev,
                                                            int32_t* __restrict__ counts) {
-  __shared__ int red[M_COUNT_TILES][PT_TILE / 32];
   const int64_t t = *t_dev;
-  for (int64_t t0 = (int64_t)blockIdx.x * M_COUNT_TILES; t0 < ntiles; t0 += (int64_t)gridDim.x * M_COUNT_TILES) {
-#pragma unroll
-    for (int k = 0; k < M_COUNT_TILES; ++k) {
-      int c = 0;
-      if (t0 + k < ntiles) {
-        const MTile tl = tiles[t0 + k];
-        const MShape& S = shapes[tl.shape];
-        const MBatch bt = batch_at(S, t);
-        const int64_t u = (int64_t)tl.first + threadIdx.x;
-        if (u < S.J) {
-          int64_t r0;
-          owned_range(S.eslot[u], S.J, bt.first, bt.first + bt.count, r0, c);
-        }
-      }
-      c = gp_warp_sum_i(c);
-      if ((threadIdx.x & 31) == 0) red[k][threadIdx.x >> 5] = c;
+  for (int64_t ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
+    const MTile tl = tiles[ti];
+    const MShape& S = shapes[tl.shape];
+    const MBatch bt = batch_at(S, t);
+    const int64_t u = (int64_t)tl.first + threadIdx.x;
+    int c = 0;
+    if (u < S.J) {
+      int64_t r0;
+      owned_range(S.eslot[u], S.J, bt.first, bt.first + bt.count, r0, c);
     }
-    __syncthreads();
-    if (threadIdx.x < M_COUNT_TILES && t0 + threadIdx.x < ntiles) {
-      int total = 0;
-      for (int w = 0; w < PT_TILE / 32; ++w) total += red[threadIdx.x][w];
-      counts[t0 + threadIdx.x] = total;
-    }
-    __syncthreads();  // red is rewritten in the next round
+    int excl;
+    const int total = block_exclusive_scan(c, &excl);
+    if (threadIdx.x == 0) counts[ti] = total;
   }
 }
 
