@@ -211,6 +211,11 @@ def replica_rate(units: float, ms: float, world: int) -> float:
 
 
 # -------------------------------------------------- oracle CPU baseline
+# Largest cloud the timed oracle sample runs on: its set-up is a dense
+# (R+1)^3 FP64 array and its NN is brute force over every point.
+CPU_BASELINE_MAX_POINTS = 1_000_000
+
+
 def oracle_rate(pts, wl, sample_q: int, seed: int = 0, repeats: int = 1):
     """Queries/s of the FP64 oracle on a bounded sample of the workload.
 
@@ -460,7 +465,11 @@ def run_ours(args, world, rank, local):
         del ts, Dt, opt
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and J > CPU_BASELINE_MAX_POINTS:
+        cpu = {"value": None, "unit": UNIT, "kind": "oracle",
+               "skipped": f"{J} points: the oracle's dense (R+1)^3 value array, band set-up and brute-force NN "
+                          f"over the whole cloud are not a bounded sample above {CPU_BASELINE_MAX_POINTS} points"}
+    elif rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, cinfo = oracle_rate(pts, wl, args.cpu_sample)
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"{args.cpu_sample} queries (sampler + brute-force NN + query terms) and the full vertex "
