@@ -372,6 +372,36 @@ def run_ours(args, world, rank, local):
                 "unit": "GB/s", "frac": round(achieved / peak, 4),
                 "traffic": NCU_TRAFFIC.get((args.workload, dom)), "peak_kind": peak_kind}
 
+    # Mesh extraction of the band as the steps left it (outside the timed
+    # region): marching cubes over the optimised cells, each kernel traced.
+    # Algorithmic bytes per launch: every active brick's 512 values and 16
+    # trainable-mask words once (the +1 apron re-reads are overhead), plus the
+    # 36-byte triangles the emit pass writes.
+    mesh = None
+    if rank == 0 and not args.deterministic:
+        gb.gp_mesh_extract(band, 0.0, with_cells=False)  # warm-up
+        gb.gp_profile(ctx, True)
+        t_host = time.perf_counter()
+        runs = 5
+        for _ in range(runs):
+            tri, _ = gb.gp_mesh_extract(band, 0.0, with_cells=False)
+        torch.cuda.synchronize()
+        t_host = (time.perf_counter() - t_host) / runs
+        gb.gp_profile(ctx, False)
+        mk = gb.gp_profile_read(ctx)
+        T = int(tri.shape[0])
+        nact = info["n_active_bricks"]
+        mesh = {"triangles": T, "active_bricks": nact, "ms_per_call_host": round(1e3 * t_host, 3), "kernels": {}}
+        for name in ("k_mesh_count", "k_mesh_emit"):
+            if name not in mk:
+                continue
+            cnt, tot = mk[name]
+            by = nact * (512 * 4 + 64) + (36 * T if name == "k_mesh_emit" else 4 * nact)
+            avg_s = tot / cnt / 1e3
+            mesh["kernels"][name] = {"launches": cnt, "avg_us": round(1e6 * avg_s, 2), "alg_bytes": int(by),
+                                     "gbs": round(by / avg_s / 1e9, 1), "frac": round(by / avg_s / 1e9 / peak, 4)}
+        del tri
+
     # End to end through the public API: every step copies its queries and
     # their source points from pinned host memory, runs NN + step + update and
     # copies its loss back to pinned host memory.  The copy of step k + 1 runs
@@ -490,6 +520,7 @@ def run_ours(args, world, rank, local):
                                "-> loss to host; next step's copy overlapped on a second stream; K steps timed "
                                "as one region, L2 flush included"},
                "gpu_launches": int(launches), "clocks": clk, "kernels": per_kernel, "fwd_bwd_adam": fba,
+               "mesh": mesh,
                "torch_autograd": torch_cmp,
                "loss_last": loss_final}
         print(json.dumps(out), flush=True)

@@ -285,6 +285,43 @@ typedef struct gp_adam {
  * optimised).  Errors: GP_ERR_ARG (step < 1, null pointers). */
 gp_status gp_update(gp_band* band, const float* grad_dev, const gp_adam* hp, int64_t step);
 
+/* ------------------------------------------------------------------ mesh */
+
+/* The surface of the fitted field at level `iso` as a triangle soup: marching
+ * cubes (Sec. 3 "Overview") over the cells whose 8 corners are all trainable
+ * (cells the fit did not optimise are skipped, Sec. 3 after Eq. 8), at the
+ * grid's resolution (Sec. 4 "Details").
+ *
+ * Corner c = dx + 2 dy + 4 dz of a cell is negative iff d < iso.  On each face
+ * of the cell, walked counter-clockwise as seen from outside, every maximal run
+ * of negative corners gives one segment from the cut edge where the walk
+ * enters the run to the one where it leaves it; the segments chain into cycles,
+ * each fanned from its lowest edge id (edge id 4 axis + p + 2 q, (p, q) the
+ * lower corner's coordinates on the other two axes, lower axis first).  Every
+ * triangle's normal (v1 - v0) x (v2 - v0) points to the positive side.  A
+ * crossing lies at t = (iso - d_lo) / (d_hi - d_lo) from the edge's lower
+ * corner.  Two cells sharing a face produce the same crossings on it, bit for
+ * bit, so the soup welds into a closed mesh wherever all cells are meshed.
+ *
+ * tri_dev: cap x 9 float32 (three xyz vertices per triangle); cell_dev: cap
+ * int64 keys i + R (j + R k) of each triangle's cell, or NULL.  Triangles come
+ * in a fixed order (active bricks in storage order, cells x-fastest within a
+ * brick, a cell's triangles in fan order).  *n_tri (host) receives the total;
+ * the buffers are written only if it is <= cap, so a call with cap = 0 sizes
+ * them.  Synchronises the stream; allocates and frees a small count array.
+ * Errors: GP_ERR_ARG (null n_tri, iso not finite, cap < 0, cap > 0 with a null
+ * tri_dev, more than 2^31 - 1 triangles), GP_ERR_OOM, GP_ERR_CUDA. */
+gp_status gp_mesh_extract(gp_band* band, float iso, float* tri_dev, int64_t* cell_dev, int64_t cap,
+                          int64_t* n_tri);
+
+/* The 256-case table gp_mesh_extract uses, built on the host from the face
+ * rule above (no GPU needed): ntri[c] triangles for the cell whose negative
+ * corners are the set bits of c, and edges[15 c + 3 k + v] the edge id of
+ * vertex v of triangle k (255 past the last triangle).  At most 5 triangles.
+ * Errors: GP_ERR_ARG (null pointer), GP_ERR_STATE (the table failed its own
+ * consistency checks). */
+gp_status gp_mesh_case_table(uint8_t* ntri, uint8_t* edges);
+
 /* ------------------------------------------------------------- many clouds */
 
 /* Several clouds of uneven size fitted together: the whole step of Sec. 3

@@ -98,6 +98,8 @@ SIGNATURES = {
     "gp_multi_buffers": (ctypes.c_int, [_vp, _i32, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp)]),
     "gp_multi_destroy": (None, [_vp]),
     "gp_step_dense_noalloc": (ctypes.c_int, [_vp, _i32, _vp, _vp, _i64, ctypes.POINTER(LossW), _vp, _vp]),
+    "gp_mesh_extract": (ctypes.c_int, [_vp, _f, _vp, _vp, _i64, ctypes.POINTER(_i64)]),
+    "gp_mesh_case_table": (ctypes.c_int, [_vp, _vp]),
 }
 
 
@@ -324,6 +326,40 @@ def gp_sample(band: Band, seed: int, epoch: int, Q: int, first: int, count: int,
                                           GP_SAMPLE_SPATIAL if spatial else 0, _ptr(out), _ptr(src_out),
                                           _ptr(pos_out)))
     return out
+
+
+def gp_mesh_case_table():
+    """The library's marching-cubes case table (host only): (ntri uint8 (256,),
+    edges uint8 (256, 15), 255 past each case's last triangle)."""
+    import numpy as np
+    lib = load()
+    ntri = np.zeros(256, dtype=np.uint8)
+    edges = np.zeros((256, 15), dtype=np.uint8)
+    st = lib.gp_mesh_case_table(ntri.ctypes.data_as(ctypes.c_void_p), edges.ctypes.data_as(ctypes.c_void_p))
+    if st != GP_OK:
+        raise GridPullError(st, "gp_mesh_case_table")
+    return ntri, edges
+
+
+def gp_mesh_extract(band: Band, iso: float = 0.0, with_cells: bool = True):
+    """Marching-cubes triangle soup of the band's optimised cells at level iso.
+
+    Returns (tri float32 (T, 3, 3), cells int64 (T,) or None) on the device: one
+    sizing call (cap = 0), then the extracting call."""
+    import torch
+    n = ctypes.c_int64(0)
+    band.ctx.sync_stream()
+    band.ctx.check(band.ctx.lib.gp_mesh_extract(band.handle, float(iso), None, None, 0, ctypes.byref(n)))
+    dev = torch.device("cuda", band.ctx.device)
+    T = int(n.value)
+    tri = torch.empty((T, 3, 3), dtype=torch.float32, device=dev)
+    cells = torch.empty(T, dtype=torch.int64, device=dev) if with_cells else None
+    if T:
+        band.ctx.check(band.ctx.lib.gp_mesh_extract(band.handle, float(iso), _ptr(tri), _ptr(cells), T,
+                                                    ctypes.byref(n)))
+        if int(n.value) != T:
+            raise GridPullError(5, f"gp_mesh_extract: {n.value} triangles on the second pass, {T} on the first")
+    return tri, cells
 
 
 def gp_nn(band: Band, q, nn_out=None, rec_out=None, hint=None, nvalid_out=None):
