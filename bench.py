@@ -685,9 +685,20 @@ def main():
     ap.add_argument("--nn-grid", type=int, default=0, help="cells per axis of the point cell list (0 = automatic)")
     ap.add_argument("--deterministic", action="store_true",
                     help="bit-reproducible gradient sums (fixed point) instead of float atomics")
+    ap.add_argument("--m1", type=int, default=None, help="override the pull bandwidth M1 (-1 = all grids)")
+    ap.add_argument("--m2", type=int, default=None, help="override the TV bandwidth M2 (-1 = all grids)")
     args = ap.parse_args()
     if args.impl == "reference" and args.workload == "collection":
         ap.error("the oracle arm times the single-cloud workloads")
+    if args.m1 is not None or args.m2 is not None:
+        if args.workload == "collection":
+            ap.error("--m1/--m2 apply to the single-cloud workloads")
+        wl = dict(WORKLOADS[args.workload])
+        wl["M1"] = wl["M1"] if args.m1 is None else args.m1
+        wl["M2"] = wl["M2"] if args.m2 is None else args.m2
+        name = lambda m: "all grids" if m < 0 else str(m)
+        wl["desc"] += f"; bands overridden: M1 = {name(wl['M1'])}, M2 = {name(wl['M2'])}"
+        WORKLOADS[args.workload] = wl
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     world, rank, local = dist_setup()
