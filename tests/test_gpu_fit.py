@@ -17,7 +17,8 @@ Ground truth comes from shapes with a closed-form SDF (a sphere and a torus,
 points area-uniform on the surface).  Checked after the fit: values at
 trainable vertices within h and 3 h of the surface match the SDF, the surface
 term |f(s)| is small, the loss fell, and the marching-cubes surface of the
-optimised cells passes within h of every ground-truth point (no holes).  Away
+optimised cells has a vertex within sqrt(3) h of every ground-truth point (no
+holes).  Away
 from the points (beyond the reach of the queries, where only L_TV acts and the
 band's frozen vertices keep the initial sign) the field can cross zero again;
 those crossings are reported, not asserted.
@@ -112,5 +113,8 @@ def test_fit_converges_to_the_ground_truth_sdf(gb, ctx, name):
     assert err[1] < 0.5 and err[3] < 1.0, metrics
     assert loss[gb.GP_LOSS_SURF] < 0.05 * h, metrics
     assert loss[gb.GP_LOSS_TOTAL] < 0.5 * first, metrics
-    assert reach.max() < 1.0, metrics
+    # A point lies in a cell that the surface crosses, and every crossing is a
+    # mesh vertex on that cell's edges: with no hole, the nearest vertex is
+    # within the cell's diagonal, sqrt(3) h.
+    assert reach.max() < np.sqrt(3.0) and np.percentile(reach, 99) < 1.0, metrics
     band.close()
