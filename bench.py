@@ -400,6 +400,26 @@ def run_ours(args, world, rank, local):
             avg_s = tot / cnt / 1e3
             mesh["kernels"][name] = {"launches": cnt, "avg_us": round(1e6 * avg_s, 2), "alg_bytes": int(by),
                                      "gbs": round(by / avg_s / 1e9, 1), "frac": round(by / avg_s / 1e9 / peak, 4)}
+        # Metrics of that mesh against the input cloud (Sec. 4: CD_L1, CD_L2,
+        # HD, F; no reference normals, so no NC): quadrature, the two bands'
+        # cell lists, the two nearest-point passes and their reductions.
+        from paper_2308_13175_gb300 import metrics as gmetrics
+        if T > 0:
+            pts_dev = torch.from_numpy(pts).cuda()
+            gmetrics.surface_metrics(ctx, tri, pts_dev, None)  # warm-up
+            gb.gp_profile(ctx, True)
+            t_host = time.perf_counter()
+            res = gmetrics.surface_metrics(ctx, tri, pts_dev, None)
+            torch.cuda.synchronize()
+            t_host = time.perf_counter() - t_host
+            gb.gp_profile(ctx, False)
+            ek = gb.gp_profile_read(ctx)
+            mesh["metrics"] = {"cd_l1": res["cd_l1"], "cd_l2": res["cd_l2"], "hd": res["hd"],
+                               "fscore": {str(k): v for k, v in res["fscore"].items()},
+                               "mesh_points": res["points"], "reference_points": int(len(pts)),
+                               "ms_host": round(1e3 * t_host, 3),
+                               "kernels_us": {k: round(1e3 * v[1] / v[0], 2) for k, v in ek.items()}}
+            del pts_dev
         del tri
 
     # End to end through the public API: every step copies its queries and

@@ -322,6 +322,43 @@ gp_status gp_mesh_extract(gp_band* band, float iso, float* tri_dev, int64_t* cel
  * consistency checks). */
 gp_status gp_mesh_case_table(uint8_t* ntri, uint8_t* edges);
 
+/* --------------------------------------------------------------- metrics */
+
+/* Weighted oriented points of a triangle soup for the metrics of Sec. 4
+ * "Datasets and Metrics": every triangle of tri_dev (T x 9 float32) is split at
+ * m equal steps along its edges into m^2 congruent triangles, and each gives
+ * its centroid, the triangle's unit normal and area / m^2 (zero normal and
+ * weight for a degenerate triangle).  Point k of triangle i is row i m^2 + k;
+ * pieces are ordered by (i, j) of their lowest lattice corner, i outer, the
+ * upright piece (corners (i,j), (i+1,j), (i,j+1)) before the inverted one
+ * (corners (i+1,j), (i,j+1), (i+1,j+1)); the centroid is
+ * v0 + a (v1 - v0) + b (v2 - v0) with (a, b) = ((3i+1)/(3m), (3j+1)/(3m))
+ * upright and ((3i+2)/(3m), (3j+2)/(3m)) inverted.  Outputs: pts_dev and
+ * nrm_dev T m^2 x 3 float32, w_dev T m^2 float32.  Asynchronous.  Errors:
+ * GP_ERR_ARG (T < 0, m outside [1, 64], null pointers with T > 0). */
+gp_status gp_mesh_quadrature(gp_ctx* ctx, const float* tri_dev, int64_t T, int32_t m, float* pts_dev,
+                             float* nrm_dev, float* w_dev);
+
+/* One direction of the metrics: for each of the n query points q_dev (n x 3
+ * float32) its exact nearest point in the band's cloud (as gp_nn), at distance
+ * d = sqrt((dx^2 + dy^2) + dz^2) in float64 from the float32 coordinates.
+ * q_w_dev: n float32 weights (NULL = 1); points of weight <= 0 are skipped.
+ * q_nrm_dev and target_nrm_dev (n x 3 and J x 3 float32 unit normals, the
+ * latter in the cloud's original order) give the normal term; NULL skips it.
+ * out_host (5 + ntau doubles): [0] the weight sum W, [1] sum w d / W,
+ * [2] sum w d^2 / W, [3] the largest d, [4] sum w |n_q . n_NN(q)| / W (NaN
+ * without normals), [5 + k] sum w [d < tau_k] / W.  With the two directions
+ * (A into a band over B, B into a band over A):
+ * CD_L1 = ([1]_AB + [1]_BA) / 2, CD_L2 = ([2]_AB + [2]_BA) / 2,
+ * HD = max([3]_AB, [3]_BA), NC = ([4]_AB + [4]_BA) / 2, F(tau_k) = 2 P R /
+ * (P + R) with P = [5+k]_AB, R = [5+k]_BA.  Means are NaN when W = 0.
+ * Synchronises the stream; allocates and frees n int32 of scratch.  Errors:
+ * GP_ERR_ARG (n outside [0, 2^31), ntau outside [0, 16] or without taus,
+ * null out_host or q_dev), GP_ERR_OOM, GP_ERR_CUDA. */
+gp_status gp_eval_nearest(gp_band* band, const float* q_dev, const float* q_nrm_dev, const float* q_w_dev,
+                          int64_t n, const float* target_nrm_dev, const double* tau_host, int32_t ntau,
+                          double* out_host);
+
 /* ------------------------------------------------------------- many clouds */
 
 /* Several clouds of uneven size fitted together: the whole step of Sec. 3

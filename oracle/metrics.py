@@ -70,7 +70,10 @@ def nearest_terms(a, a_nrm, a_w, b, b_nrm, taus):
     a_w None = weight 1; normals None = NC not computed (NaN)."""
     a = np.asarray(a, dtype=np.float64)
     b = np.asarray(b, dtype=np.float64)
-    d, j = cKDTree(b).query(a)
+    _, j = cKDTree(b).query(a)
+    diff = a - b[j]
+    # the distance of the nearest point, as ((dx^2 + dy^2) + dz^2) then sqrt
+    d = np.sqrt((diff[:, 0] * diff[:, 0] + diff[:, 1] * diff[:, 1]) + diff[:, 2] * diff[:, 2])
     w = np.ones(len(a)) if a_w is None else np.asarray(a_w, dtype=np.float64)
     W = w.sum()
     out = {"mean_d": float((w * d).sum() / W), "mean_d2": float((w * d * d).sum() / W),
@@ -99,8 +102,8 @@ def surface_metrics(tri, gt_pts, gt_nrm, taus=(0.002, 0.004, 0.01), m: int = 4) 
     """Metrics of a triangle soup (sampled by mesh_quadrature with m^2 points
     per triangle) against oriented ground-truth points."""
     c, n, w = mesh_quadrature(tri, m)
-    keep = w > 0
-    c, n, w = c[keep], n[keep], w[keep]
+    # a degenerate triangle's points still lie on the mesh: they stay targets
+    # of the completeness direction, with weight 0 in the accuracy direction
     acc = nearest_terms(c, n, w, gt_pts, gt_nrm, taus)
     comp = nearest_terms(gt_pts, gt_nrm, None, c, n, taus)
     return combine(acc, comp, taus)

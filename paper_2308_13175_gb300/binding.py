@@ -100,6 +100,9 @@ SIGNATURES = {
     "gp_step_dense_noalloc": (ctypes.c_int, [_vp, _i32, _vp, _vp, _i64, ctypes.POINTER(LossW), _vp, _vp]),
     "gp_mesh_extract": (ctypes.c_int, [_vp, _f, _vp, _vp, _i64, ctypes.POINTER(_i64)]),
     "gp_mesh_case_table": (ctypes.c_int, [_vp, _vp]),
+    "gp_mesh_quadrature": (ctypes.c_int, [_vp, _vp, _i64, _i32, _vp, _vp, _vp]),
+    "gp_eval_nearest": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i64, _vp, ctypes.POINTER(ctypes.c_double), _i32,
+                                       ctypes.POINTER(ctypes.c_double)]),
 }
 
 
@@ -360,6 +363,41 @@ def gp_mesh_extract(band: Band, iso: float = 0.0, with_cells: bool = True):
         if int(n.value) != T:
             raise GridPullError(5, f"gp_mesh_extract: {n.value} triangles on the second pass, {T} on the first")
     return tri, cells
+
+
+def gp_mesh_quadrature(ctx: Context, tri, m: int = 4):
+    """(points (T m^2, 3), unit normals (T m^2, 3), weights (T m^2,)) float32 on
+    the device: the centroids of the m^2 sub-triangles of every triangle."""
+    import torch
+    _need(tri, torch.float32, name="triangles")
+    T = tri.numel() // 9
+    n = T * int(m) * int(m)
+    dev = torch.device("cuda", ctx.device)
+    pts = torch.empty((n, 3), dtype=torch.float32, device=dev)
+    nrm = torch.empty((n, 3), dtype=torch.float32, device=dev)
+    w = torch.empty(n, dtype=torch.float32, device=dev)
+    ctx.sync_stream()
+    ctx.check(ctx.lib.gp_mesh_quadrature(ctx.handle, _ptr(tri), T, int(m), _ptr(pts), _ptr(nrm), _ptr(w)))
+    return pts, nrm, w
+
+
+def gp_eval_nearest(band: Band, q, q_nrm=None, q_w=None, target_nrm=None, taus=()):
+    """One direction of the metrics (see the header): a dict with W, mean_d,
+    mean_d2, max_d, mean_cos and below (one fraction per tau)."""
+    import torch
+    _need(q, torch.float32, name="q")
+    n = q.numel() // 3
+    _need(q_nrm, torch.float32, 3 * n, "q normals")
+    _need(q_w, torch.float32, n, "q weights")
+    _need(target_nrm, torch.float32, 3 * band.info["J"], "target normals")
+    k = len(taus)
+    tau = (ctypes.c_double * max(k, 1))(*[float(t) for t in taus])
+    out = (ctypes.c_double * (5 + k))()
+    band.ctx.sync_stream()
+    band.ctx.check(band.ctx.lib.gp_eval_nearest(band.handle, _ptr(q), _ptr(q_nrm), _ptr(q_w), n, _ptr(target_nrm),
+                                                tau, k, out))
+    v = list(out)
+    return {"W": v[0], "mean_d": v[1], "mean_d2": v[2], "max_d": v[3], "mean_cos": v[4], "below": v[5:5 + k]}
 
 
 def gp_nn(band: Band, q, nn_out=None, rec_out=None, hint=None, nvalid_out=None):

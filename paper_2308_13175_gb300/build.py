@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "libgridpull.so")
-SOURCES = ["gp_core.cu", "gp_band.cu", "gp_nn.cu", "gp_sample.cu", "gp_step.cu", "gp_multi.cu", "gp_noalloc.cu", "gp_mesh.cu"]
+SOURCES = ["gp_core.cu", "gp_band.cu", "gp_nn.cu", "gp_sample.cu", "gp_step.cu", "gp_multi.cu", "gp_noalloc.cu", "gp_mesh.cu", "gp_eval.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2", "--expt-relaxed-constexpr"]
 
