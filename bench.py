@@ -392,11 +392,11 @@ def run_ours(args, world, rank, local):
         T = int(tri.shape[0])
         nact = info["n_active_bricks"]
         mesh = {"triangles": T, "active_bricks": nact, "ms_per_call_host": round(1e3 * t_host, 3), "kernels": {}}
-        for name in ("k_mesh_count", "k_mesh_emit"):
+        for name in ("k_mesh_count", "k_mesh_emit", "k_mesh_count_w", "k_mesh_emit_w"):
             if name not in mk:
                 continue
             cnt, tot = mk[name]
-            by = nact * (512 * 4 + 64) + (36 * T if name == "k_mesh_emit" else 4 * nact)
+            by = nact * (512 * 4 + 64) + (36 * T if name.startswith("k_mesh_emit") else 4 * nact)
             avg_s = tot / cnt / 1e3
             mesh["kernels"][name] = {"launches": cnt, "avg_us": round(1e6 * avg_s, 2), "alg_bytes": int(by),
                                      "gbs": round(by / avg_s / 1e9, 1), "frac": round(by / avg_s / 1e9 / peak, 4)}

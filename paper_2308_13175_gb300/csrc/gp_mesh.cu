@@ -18,10 +18,12 @@
 // corner hi lies at t = (iso - d_lo) / (d_hi - d_lo), at the world point
 // -1 + h * lo + h * t along the edge's axis.
 //
-// Launch plan: one warp per active brick (a meshed cell's lowest corner is
-// trainable, so its brick is active), 8 bricks per block, 16 consecutive cells
-// per lane; the warp stages the brick's 9^3 corner values and trainable bits in
-// shared memory through the 27-neighbour brick table, with no block barrier.
+// Launch plan: a meshed cell's lowest corner is trainable, so its brick is
+// active; the active bricks are meshed either by one 512-thread block each (one
+// cell per thread) or, on large bands, by one warp each (8 per block, 16
+// consecutive cells per lane, no block barrier).  Either stages the brick's
+// 9^3 corner values and trainable bits in shared memory through the
+// 27-neighbour brick table.
 // Pass 1 counts triangles per brick, a device scan turns the counts into
 // offsets, pass 2 writes the triangles: bricks in active-list order, cells in
 // x-fastest order within a brick, each cell's triangles in table order.
@@ -33,9 +35,17 @@
 namespace {
 
 constexpr int MC_MAX_TRI = 5;       // most triangles any of the 256 cases yields
-constexpr int MC_WARPS = 8;         // bricks per block, one warp each
+constexpr int MB_THREADS = 512;     // small bands: one thread per cell of a brick
+constexpr int MC_WARPS = 8;         // large bands: bricks per block, one warp each
 constexpr int MC_BLOCK = 32 * MC_WARPS;
 constexpr int MC_CELLS = 16;        // consecutive cells per lane (512 / 32)
+// Bricks per SM from which a warp per brick pays: below it one block per
+// brick keeps more threads busy (single object, 7 bricks per SM: 12 / 24 us
+// against 18 / 71 us); above it the warp form keeps more bricks in flight
+// (dense 257^3, 236 per SM: 98 / 151 us against 184 / 239 us).
+constexpr int MC_WARP_MIN_BRICKS_PER_SM = 32;
+
+static_assert(MB_THREADS == GP_ORDER_THREADS, "block_exclusive_scan is sized for GP_ORDER_THREADS");
 constexpr int MC_S = 9;             // staged corners per axis (8 + the +1 apron)
 constexpr int MC_STAGED = MC_S * MC_S * MC_S;
 
@@ -146,6 +156,113 @@ struct MeshArgs {
   float h;
 };
 
+struct MeshShared {
+  float d[MC_STAGED];
+  uint8_t tr[MC_STAGED];
+};
+
+// Stage the corners (x, y, z) in [0, 8]^3 of the brick: the brick's own 8^3
+// and the +x / +y / +z apron from its neighbours; absent bricks read as not
+// trainable.
+__device__ __forceinline__ void mesh_stage(const MeshArgs& a, int slot, MeshShared& sh) {
+  for (int s = threadIdx.x; s < MC_STAGED; s += MB_THREADS) {
+    const int x = s % MC_S, y = (s / MC_S) % MC_S, z = s / (MC_S * MC_S);
+    const int dx = x >> 3, dy = y >> 3, dz = z >> 3;
+    const int src = (dx | dy | dz) ? __ldg(a.brick_nbr + (int64_t)slot * 27 + (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1))
+                                   : slot;
+    float d = 0.f;
+    uint8_t t = 0;
+    if (src >= 0) {
+      const int l = (((z & 7) << 3) | (y & 7)) << 3 | (x & 7);
+      d = __ldg(a.D + (int64_t)src * 512 + l);
+      t = gp_mask_bit(a.masks, src, 1, l) ? 1 : 0;
+    }
+    sh.d[s] = d;
+    sh.tr[s] = t;
+  }
+}
+
+// Case of this thread's cell (one thread per cell), or -1 when it is not meshed.
+__device__ __forceinline__ int mesh_case_thread(const MeshArgs& a, const MeshShared& sh, int bx, int by, int bz) {
+  const int x = threadIdx.x & 7, y = (threadIdx.x >> 3) & 7, z = threadIdx.x >> 6;
+  if (bx * 8 + x >= a.R || by * 8 + y >= a.R || bz * 8 + z >= a.R) return -1;
+  int cas = 0;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const int s = (z + (c >> 2)) * (MC_S * MC_S) + (y + ((c >> 1) & 1)) * MC_S + (x + (c & 1));
+    if (!sh.tr[s]) return -1;
+    cas |= (sh.d[s] < a.iso ? 1 : 0) << c;
+  }
+  return cas;
+}
+
+// Small bands: one 512-thread block per active brick, one cell per thread.
+__global__ void __launch_bounds__(MB_THREADS) k_mesh_count(MeshArgs a, int32_t* __restrict__ counts) {
+  __shared__ MeshShared sh;
+  __shared__ int wsum[MB_THREADS / 32];
+  const int slot = __ldg(a.active + blockIdx.x);
+  mesh_stage(a, slot, sh);
+  __syncthreads();
+  const int cas = mesh_case_thread(a, sh, __ldg(a.brick_coord + 3 * slot), __ldg(a.brick_coord + 3 * slot + 1),
+                            __ldg(a.brick_coord + 3 * slot + 2));
+  int n = cas >= 0 ? c_mc.ntri[cas] : 0;
+  n = gp_warp_sum_i(n);
+  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = n;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    int v = threadIdx.x < MB_THREADS / 32 ? wsum[threadIdx.x] : 0;
+    v = gp_warp_sum_i(v);
+    if (threadIdx.x == 0) counts[blockIdx.x] = v;
+  }
+}
+
+__global__ void __launch_bounds__(MB_THREADS) k_mesh_emit(MeshArgs a, const int32_t* __restrict__ offsets,
+                                                          float* __restrict__ tri, int64_t* __restrict__ tri_cell) {
+  __shared__ MeshShared sh;
+  const int slot = __ldg(a.active + blockIdx.x);
+  const int bx = __ldg(a.brick_coord + 3 * slot), by = __ldg(a.brick_coord + 3 * slot + 1),
+            bz = __ldg(a.brick_coord + 3 * slot + 2);
+  mesh_stage(a, slot, sh);
+  __syncthreads();
+  const int cas = mesh_case_thread(a, sh, bx, by, bz);
+  const int n = cas >= 0 ? c_mc.ntri[cas] : 0;
+  int local;
+  block_exclusive_scan(n, &local);
+  if (n == 0) return;
+  const int x = threadIdx.x & 7, y = (threadIdx.x >> 3) & 7, z = threadIdx.x >> 6;
+  const int gi = bx * 8 + x, gj = by * 8 + y, gk = bz * 8 + z;
+  const int64_t first = (int64_t)__ldg(offsets + blockIdx.x) + local;
+  const int64_t key = gi + (int64_t)a.R * (gj + (int64_t)a.R * gk);
+  for (int k = 0; k < n; ++k) {
+    float* out = tri + (first + k) * 9;
+#pragma unroll
+    for (int v = 0; v < 3; ++v) {
+      const int e = c_mc.edge[cas][3 * k + v];
+      const int axis = e >> 2, r = e & 3;
+      // lower corner of the edge: the edge's own axis at 0, (p, q) on the others
+      const int lo = axis == 0 ? ((r & 1) << 1) | ((r >> 1) << 2)
+                               : (axis == 1 ? (r & 1) | ((r >> 1) << 2) : (r & 1) | ((r >> 1) << 1));
+      const int hi = lo | (1 << axis);
+      const int slo = (z + (lo >> 2)) * (MC_S * MC_S) + (y + ((lo >> 1) & 1)) * MC_S + (x + (lo & 1));
+      const int shi = (z + (hi >> 2)) * (MC_S * MC_S) + (y + ((hi >> 1) & 1)) * MC_S + (x + (hi & 1));
+      const float dlo = sh.d[slo], dhi = sh.d[shi];
+      const float t = __fdiv_rn(__fsub_rn(a.iso, dlo), __fsub_rn(dhi, dlo));
+      // -1 + h * (integer corner) is exact in float32 for R <= 2048
+      float px = __fadd_rn(-1.0f, __fmul_rn(a.h, (float)(gi + (lo & 1))));
+      float py = __fadd_rn(-1.0f, __fmul_rn(a.h, (float)(gj + ((lo >> 1) & 1))));
+      float pz = __fadd_rn(-1.0f, __fmul_rn(a.h, (float)(gk + (lo >> 2))));
+      const float step = __fmul_rn(a.h, t);
+      if (axis == 0) px = __fadd_rn(px, step);
+      else if (axis == 1) py = __fadd_rn(py, step);
+      else pz = __fadd_rn(pz, step);
+      out[3 * v + 0] = px;
+      out[3 * v + 1] = py;
+      out[3 * v + 2] = pz;
+    }
+    if (tri_cell) tri_cell[first + k] = key;
+  }
+}
+
 struct MeshStage {
   float d[MC_STAGED];
   uint8_t tr[MC_STAGED];
@@ -197,9 +314,9 @@ __device__ __forceinline__ int mesh_case(const MeshArgs& a, const MeshStage& sh,
   return cas;
 }
 
-// One warp per active brick, MC_WARPS bricks per block; lane L owns the
-// MC_CELLS consecutive cells [MC_CELLS L, MC_CELLS (L + 1)) of its brick.
-__global__ void __launch_bounds__(MC_BLOCK) k_mesh_count(MeshArgs a, int64_t n_active, int32_t* __restrict__ counts) {
+// Large bands: one warp per active brick, MC_WARPS bricks per block; lane L
+// owns the MC_CELLS consecutive cells [MC_CELLS L, MC_CELLS (L + 1)).
+__global__ void __launch_bounds__(MC_BLOCK) k_mesh_count_w(MeshArgs a, int64_t n_active, int32_t* __restrict__ counts) {
   __shared__ MeshStage st[MC_WARPS];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t b = (int64_t)blockIdx.x * MC_WARPS + w;
@@ -219,7 +336,7 @@ __global__ void __launch_bounds__(MC_BLOCK) k_mesh_count(MeshArgs a, int64_t n_a
   if (lane == 0) counts[b] = n;
 }
 
-__global__ void __launch_bounds__(MC_BLOCK) k_mesh_emit(MeshArgs a, int64_t n_active,
+__global__ void __launch_bounds__(MC_BLOCK) k_mesh_emit_w(MeshArgs a, int64_t n_active,
                                                         const int32_t* __restrict__ offsets, float* __restrict__ tri,
                                                         int64_t* __restrict__ tri_cell) {
   __shared__ MeshStage st[MC_WARPS];
@@ -332,9 +449,15 @@ extern "C" gp_status gp_mesh_extract(gp_band* b, float iso, float* tri_dev, int6
   int64_t total = 0;
   do {
     gp_prof_pre(ctx);
+    const bool warp_form = nb >= (int64_t)MC_WARP_MIN_BRICKS_PER_SM * ctx->num_sms;
     const unsigned grid = (unsigned)((nb + MC_WARPS - 1) / MC_WARPS);
-    k_mesh_count<<<grid, MC_BLOCK, 0, ctx->stream>>>(a, nb, counts);
-    gp_prof_post(ctx, "k_mesh_count");
+    if (warp_form) {
+      k_mesh_count_w<<<grid, MC_BLOCK, 0, ctx->stream>>>(a, nb, counts);
+      gp_prof_post(ctx, "k_mesh_count_w");
+    } else {
+      k_mesh_count<<<(unsigned)nb, MB_THREADS, 0, ctx->stream>>>(a, counts);
+      gp_prof_post(ctx, "k_mesh_count");
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) { st = gp_cuda_fail(ctx, e, "k_mesh_count"); break; }
     // Each brick holds at most 512 * 5 triangles, so the int32 offsets are
@@ -344,8 +467,13 @@ extern "C" gp_status gp_mesh_extract(gp_band* b, float iso, float* tri_dev, int6
     *n_tri = total;
     if (total == 0 || total > cap) break;
     gp_prof_pre(ctx);
-    k_mesh_emit<<<grid, MC_BLOCK, 0, ctx->stream>>>(a, nb, counts, tri_dev, cell_dev);
-    gp_prof_post(ctx, "k_mesh_emit");
+    if (warp_form) {
+      k_mesh_emit_w<<<grid, MC_BLOCK, 0, ctx->stream>>>(a, nb, counts, tri_dev, cell_dev);
+      gp_prof_post(ctx, "k_mesh_emit_w");
+    } else {
+      k_mesh_emit<<<(unsigned)nb, MB_THREADS, 0, ctx->stream>>>(a, counts, tri_dev, cell_dev);
+      gp_prof_post(ctx, "k_mesh_emit");
+    }
     e = cudaGetLastError();
     if (e != cudaSuccess) { st = gp_cuda_fail(ctx, e, "k_mesh_emit"); break; }
     // counts is freed below: wait until the emit pass has read it.

@@ -92,6 +92,23 @@ def test_mesh_dense_random_field_covers_every_case(gb, ctx):
     band.close()
 
 
+def test_mesh_large_band_takes_the_warp_form(gb, ctx):
+    """A dense R = 128 band has 17^3 = 4,913 active bricks, enough for the
+    warp-per-brick kernels (32 bricks per SM on 152 SMs); random values put
+    many triangles on every lane."""
+    R = 128
+    pts = synth.sphere_cloud(2000, 0.5, seed=0)
+    band = _band(gb, ctx, pts, R, -1, -1)
+    rng = np.random.default_rng(5)
+    _set_values(gb, band, lambda x: rng.standard_normal(len(x)))
+    gb.gp_profile(ctx, True)
+    _compare(gb, band, pts, R, -1, -1)
+    gb.gp_profile(ctx, False)
+    names = set(gb.gp_profile_read(ctx))
+    assert {"k_mesh_count_w", "k_mesh_emit_w"} <= names, names
+    band.close()
+
+
 @pytest.mark.parametrize("R,M", [(64, 2), (128, 1), (256, 2)])
 def test_mesh_band_skips_cells_not_optimised(gb, ctx, R, M):
     """The single-object cloud's band with a noisy sphere field: only cells whose
