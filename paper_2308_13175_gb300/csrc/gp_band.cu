@@ -260,7 +260,6 @@ void band_free(gp_band* b) {
   gp_free(b->pts);
   gp_free(b->pts_sorted);
   gp_free(b->cell_start);
-  gp_free(b->coarse_occ);
   gp_free(b->sigma);
   gp_free(b->normals);
   gp_free(b->perm);

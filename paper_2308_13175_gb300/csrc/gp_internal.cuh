@@ -80,8 +80,6 @@ struct gp_band {
   float* pts = nullptr;            // J x 3
   float4* pts_sorted = nullptr;    // J: x, y, z, original index (int bits)
   int32_t* cell_start = nullptr;   // G^3 + 1
-  uint32_t* coarse_occ = nullptr;  // one bit per block of coarse_k^3 cells: any point in it
-  int coarse_k = 0, coarse_g = 0;  // block edge in cells, blocks per axis
   float* sigma = nullptr;          // J
   float* normals = nullptr;        // J x 3: unit normal estimate (PCA of the sigma-ball), seeds gp_nn
   int32_t* perm = nullptr;         // J: Pi_e of the cached epoch

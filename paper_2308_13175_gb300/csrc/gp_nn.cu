@@ -28,17 +28,6 @@
 
 namespace {
 
-// Coarse occupancy: bit ((z/k) cg + y/k) cg + x/k is set iff cell (x, y, z)
-// holds a point.
-__global__ void k_coarse_occ(const int32_t* __restrict__ start, int G, int k, int cg, uint32_t* __restrict__ occ) {
-  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t ncell = (int64_t)G * G * G;
-  if (c >= ncell || start[c + 1] == start[c]) return;
-  const int x = (int)(c % G), y = (int)((c / G) % G), z = (int)(c / ((int64_t)G * G));
-  const int64_t bit = ((int64_t)(z / k) * cg + y / k) * cg + x / k;
-  atomicOr(occ + (bit >> 5), 1u << (bit & 31));
-}
-
 __global__ void k_point_cells(const float* __restrict__ pts, int64_t J, NNGrid g, int32_t* __restrict__ cid,
                               int32_t* __restrict__ counts) {
   int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -442,16 +431,6 @@ gp_status gp_build_points(gp_band* b, const float* pts_dev) {
   cudaFree(cursor);
   if (st) return st;
   if (e != cudaSuccess) return gp_cuda_fail(ctx, e, "point cell list");
-  // Coarse occupancy for the ball walk: blocks of k^3 cells, k = ceil(G / 64),
-  // so the bits take at most 64^3 / 8 = 32 KB and stay in L1.
-  b->coarse_k = (G + 63) / 64;
-  b->coarse_g = (G + b->coarse_k - 1) / b->coarse_k;
-  const int64_t nbits = (int64_t)b->coarse_g * b->coarse_g * b->coarse_g;
-  if ((st = gp_alloc(ctx, &b->coarse_occ, (nbits + 31) / 32, "coarse occupancy"))) return st;
-  GP_CUDA(ctx, cudaMemsetAsync(b->coarse_occ, 0, ((nbits + 31) / 32) * sizeof(uint32_t), s));
-  GP_KERNEL(ctx, "k_coarse_occ", k_coarse_occ<<<gp_blocks(ncell, 256), 256, 0, s>>>(b->cell_start, G, b->coarse_k,
-                                                                                 b->coarse_g, b->coarse_occ));
-  g = make_grid(b);
   if (b->knn_k > 0) {
     if ((st = gp_alloc(ctx, &b->sigma, J, "sigma"))) return st;
     if ((st = gp_alloc(ctx, &b->perm, J, "permutation"))) return st;

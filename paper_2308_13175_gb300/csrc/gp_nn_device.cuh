@@ -14,29 +14,10 @@ constexpr float NN_TINY = 1e-30f;
 struct NNGrid {
   const float4* __restrict__ pts;      // sorted by cell: x, y, z, original index bits
   const int32_t* __restrict__ start;   // G^3 + 1
-  const uint32_t* __restrict__ occ;    // coarse occupancy bits (NULL: none)
   int G;
   float half_g;  // G / 2
   float cs;      // 2 / G
-  int ck;        // coarse block edge in cells
-  int cg;        // coarse blocks per axis
 };
-
-// Whether any point lies in the cells [xa, xb] of row (cy, cz), up to the
-// coarse blocks: false only when every block the row segment crosses is
-// empty, so a row it rejects holds no point.
-__device__ __forceinline__ bool nn_row_occupied(const NNGrid& g, int cz, int cy, int xa, int xb) {
-  const int64_t base = ((int64_t)(cz / g.ck) * g.cg + cy / g.ck) * g.cg;
-  const int64_t b0 = base + xa / g.ck, b1 = base + xb / g.ck;
-  for (int64_t w = b0 >> 5; w <= (b1 >> 5); ++w) {
-    uint32_t m = __ldg(g.occ + w);
-    const int lo = (w == (b0 >> 5)) ? (int)(b0 & 31) : 0;
-    const int hi = (w == (b1 >> 5)) ? (int)(b1 & 31) : 31;
-    m &= (0xffffffffu << lo) & (0xffffffffu >> (31 - hi));
-    if (m) return true;
-  }
-  return false;
-}
 
 __device__ __forceinline__ int nn_cell(float x, const NNGrid& g) {
   float t = __fmul_rn(__fadd_rn(x, 1.0f), g.half_g);
@@ -274,7 +255,6 @@ __device__ __forceinline__ void nn_ball_walk(const float q[3], const int c[3], c
           }
           const float rad = sqrtf(thr - lyz2) * 1.000001f + margin;
           const int xa = nn_cell(q[0] - rad, g), xb = nn_cell(q[0] + rad, g);
-          if (g.occ && !nn_row_occupied(g, cz, cy, xa, xb)) continue;  // no point there
           const int64_t row = ((int64_t)cz * G + cy) * G;
           visit(__ldg(g.start + row + xa), __ldg(g.start + row + xb + 1));
         }
@@ -397,12 +377,9 @@ inline NNGrid make_grid(const gp_band* b) {
   NNGrid g;
   g.pts = b->pts_sorted;
   g.start = b->cell_start;
-  g.occ = b->coarse_occ;
   g.G = b->G;
   g.half_g = 0.5f * (float)b->G;
   g.cs = 2.0f / (float)b->G;
-  g.ck = b->coarse_k > 0 ? b->coarse_k : 1;
-  g.cg = b->coarse_g;
   return g;
 }
 
