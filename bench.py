@@ -62,9 +62,10 @@ WORKLOADS = {
                        R=0, M1=2, M2=2, lr=1e-3, n_shapes=64, q_per_point=10, batches_per_epoch=8),
 }
 
-# Algorithmic bytes per launch of each kernel ("Kernels and
-# their rooflines").  n = queries in the launch, J = points, Vs = stored
-# slots, Vt = trainable vertices.
+# Algorithmic bytes per launch of each kernel: every array the kernel must
+# touch, once (re-reads, padding and frozen slots are overhead, not counted).
+# n = queries in the launch, J = points, Vs = stored slots, Vt = trainable
+# vertices.
 def alg_bytes(name, n, J, Vs, Vt):
     return {
         "k_sample": 32 * n,

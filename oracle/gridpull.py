@@ -462,7 +462,7 @@ def query_terms(D: np.ndarray, R: int, pull_cells: np.ndarray, q: np.ndarray, s:
         # <= 1); the unit residual u = r/|r| itself carries a relative error
         # kappa = |q - s| / |r| times u (r is a difference of vectors of size
         # |q - s|).  Those sizes, times |w_c| and |dw_c/dx_a|, are the scale
-        # against which a float32 evaluation is judged.
+        # against which a float32 evaluation is compared.
         kappa = np.maximum(1.0, np.linalg.norm(q64 - s64, axis=1) / np.maximum(l_pull, 1e-300))
         sq_g = kappa * np.linalg.norm(dL_dn, axis=1) / np.maximum(_norm(g), NORM_FLOOR)
         ss_g = np.linalg.norm(dL_dns, axis=1) / np.maximum(_norm(gs), NORM_FLOOR)

@@ -744,7 +744,7 @@ extern "C" gp_status gp_multi_autotune(gp_multi* m, const gp_loss_w* w) {
   };
   // The current step's queries, as input of the record stages.
   if (!st) st = launch_sampling(m);
-  // Records per tile (also the block size of the record kernels), judged on
+  // Records per tile (also the block size of the record kernels), timed on
   // the nearest-point stage, the heaviest.
   int best_tq = m->tq;
   float best_ms = INFINITY;
