@@ -101,8 +101,9 @@ def fwd_bwd_adam(per_kernel: dict, names, queries_per_step: float, V_trainable: 
 
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of
-# the dominant kernel from one ncu capture of this build (profiles/), by
-# workload; a kernel changed since its capture must be dropped from here.
+# the dominant kernel from one ncu capture of the current kernel code
+# (summaries in profiles/), by workload; a kernel changed since its capture
+# must be dropped from here.
 NCU_TRAFFIC = {("object", "k_nn"): 10_305_024, ("scene", "k_nn_sorted"): 1_132_552_704}
 
 
