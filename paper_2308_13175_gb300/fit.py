@@ -55,3 +55,34 @@ class FitStep:
         gb.gp_step(band, self.rec, count, self.grad, self.loss, self.weights, nvalid=self.nvalid, flags=self.flags)
         gb.gp_update(band, self.grad, self.lr_at(t), t + 1)
         return self.loss
+
+
+def fit_cloud(ctx: gb.Context, points, R: int = 256, M1: int = 3, M2: int = 14, iters: int = 1600,
+              batch: int = 50_000, queries_per_point: int = 10, lr_voxels: float = 1.0, lr_decay: float = 0.3,
+              lr_every: int = 400, weights=PAPER_WEIGHTS, init_radius_voxels: float = 2.0, knn_k: int = 50,
+              seed: int = 0, deterministic: bool = False):
+    """The whole fit of Sec. 3 with the defaults of Sec. 4 "Details": build the
+    band of `points` ((J, 3) float32 on the device, in [-1, 1]^3), start from a
+    sphere of init_radius_voxels cells about the cloud's bounding-box centre,
+    and run `iters` steps of FitStep (a pool of queries_per_point queries per
+    point, re-drawn every epoch; Adam at lr_voxels * h, times lr_decay every
+    lr_every steps).  Returns (band, fit): the band holds the fitted values,
+    fit.loss the last step's loss slots."""
+    band = gb.gp_build_band(ctx, points, R, M1, M2, knn_k, deterministic=deterministic)
+    lo = points.min(dim=0).values.cpu().numpy()
+    hi = points.max(dim=0).values.cpu().numpy()
+    h = 2.0 / R
+    gb.gp_band_init_sphere(band, 0.5 * (lo + hi), init_radius_voxels * h, 0.0, seed=seed)
+    fit = FitStep(band, Q=queries_per_point * band.info["J"], B=batch, seed=seed, weights=weights,
+                  lr=lr_voxels * h, lr_decay=lr_decay, lr_every=lr_every, deterministic=deterministic)
+    for t in range(iters):
+        fit.run(t)
+    return band, fit
+
+
+def reconstruct(ctx: gb.Context, points, iso: float = 0.0, **fit_args):
+    """fit_cloud, then marching cubes over the optimised cells at level iso.
+    Returns (triangles (T, 3, 3) float32 on the device, band)."""
+    band, _ = fit_cloud(ctx, points, **fit_args)
+    tri, _ = gb.gp_mesh_extract(band, iso, with_cells=False)
+    return tri, band

@@ -11,7 +11,8 @@ the mirrored minimum of Eq. 4 (f = +delta with grad f pointing inwards), which
 pulls them onto the surface as well; measured, the field near the surface was
 then 0.7-0.8 h off and L_grad 0.81.  Every step is FitStep.run: per-epoch
 resampling of the query pool (10 queries per point), exact NN, the forward and
-backward of Eq. 3-8, L_TV and Adam, all in the library's kernels.
+backward of Eq. 3-8, L_TV and Adam, all in the library's kernels; fit_cloud
+strings them together with these defaults.
 
 Ground truth comes from shapes with a closed-form SDF (a sphere and a torus,
 points area-uniform on the surface).  Checked after the fit: values at
@@ -73,17 +74,16 @@ def _shape(name):
 def test_fit_converges_to_the_ground_truth_sdf(gb, ctx, name):
     import torch
     from scipy.spatial import cKDTree
-    from paper_2308_13175_gb300.fit import FitStep
+    from paper_2308_13175_gb300.fit import fit_cloud
     pts, sdf = _shape(name)
-    R, M1, M2 = 256, 3, 14
+    R = 256
     h = 2.0 / R
-    band = gb.gp_build_band(ctx, torch.from_numpy(pts).cuda(), R, M1, M2, 50)
-    gb.gp_band_init_sphere(band, 0.5 * (pts.min(0) + pts.max(0)), 2 * h, 0.0, seed=0)
-    fit = FitStep(band, Q=10 * len(pts), B=50_000, seed=0, weights=(1.0, 1.0, 0.05), lr=1.0 * h,
-                  lr_decay=0.3, lr_every=400)
-    first = float(fit.run(0)[gb.GP_LOSS_TOTAL])
-    for t in range(1, 1600):
-        loss = fit.run(t)
+    band, first_fit = fit_cloud(ctx, torch.from_numpy(pts).cuda(), iters=1, weights=(1.0, 1.0, 0.05))
+    first = float(first_fit.loss[gb.GP_LOSS_TOTAL])
+    band.close()
+    band, fit = fit_cloud(ctx, torch.from_numpy(pts).cuda(), R=R, M1=3, M2=14, iters=1600, batch=50_000,
+                          weights=(1.0, 1.0, 0.05))
+    loss = fit.loss
     torch.cuda.synchronize()
     gb.gp_band_check(band)
     loss = loss.cpu().numpy()
