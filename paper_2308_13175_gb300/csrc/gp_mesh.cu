@@ -326,10 +326,12 @@ __global__ void __launch_bounds__(MC_BLOCK) k_mesh_count_w(MeshArgs a, int64_t n
             bz = __ldg(a.brick_coord + 3 * slot + 2);
   MeshStage& sh = st[w];
   mesh_stage_warp(a, slot, sh, lane);
+  // Only the total matters here, so the cells go round-robin over the lanes
+  // (cell lane + 32 k): a warp's staged reads then spread over the banks.
   int n = 0;
 #pragma unroll
   for (int k = 0; k < MC_CELLS; ++k) {
-    const int cas = mesh_case(a, sh, lane * MC_CELLS + k, bx, by, bz);
+    const int cas = mesh_case(a, sh, lane + 32 * k, bx, by, bz);
     if (cas >= 0) n += c_mc.ntri[cas];
   }
   n = gp_warp_sum_i(n);
