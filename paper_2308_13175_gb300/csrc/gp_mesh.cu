@@ -42,7 +42,7 @@ constexpr int MC_CELLS = 16;        // consecutive cells per lane (512 / 32)
 // Bricks per SM from which a warp per brick pays: below it one block per
 // brick keeps more threads busy (single object, 7 bricks per SM: 12 / 24 us
 // against 18 / 71 us); above it the warp form keeps more bricks in flight
-// (dense 257^3, 236 per SM: 98 / 151 us against 184 / 239 us).
+// (dense 257^3, 236 per SM: 88 / 150 us against 184 / 239 us).
 constexpr int MC_WARP_MIN_BRICKS_PER_SM = 32;
 
 static_assert(MB_THREADS == GP_ORDER_THREADS, "block_exclusive_scan is sized for GP_ORDER_THREADS");
