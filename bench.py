@@ -70,7 +70,7 @@ def alg_bytes(name, n, J, Vs, Vt):
     return {
         "k_sample": 32 * n,
         "k_perm": 8 * J,
-        "k_order_count": 20 * J,
+        "k_order_count": 4 * J,
         "k_order_emit": 20 * J + 32 * n,
         "k_nn": 36 * n + 16 * J,
         "k_nn_sorted": 36 * n + 16 * J,

@@ -1,0 +1,44 @@
+"""Host-side checks of the benchmark's roofline bookkeeping (no GPU): every
+kernel a fitting step can launch has an algorithmic byte count, and the counts
+are the arrays each kernel must touch once."""
+import os
+import re
+
+import bench
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_2308_13175_gb300", "csrc")
+
+# Launched by a step of FitStep: sampling (once-per-epoch kernels move no
+# per-step data the roofline counts), NN, the step and the update.
+STEP_KERNELS = {"k_sample", "k_perm", "k_order_count", "k_order_emit", "k_nn", "k_nn_sorted", "k_count_valid",
+                "k_tv", "k_query", "k_adam"}
+UNCOUNTED = {"k_order_tiles", "k_emit_slots"}  # a scan of tile counts; a per-epoch gather
+
+
+def _launched(files):
+    names = set()
+    for f in files:
+        text = open(os.path.join(CSRC, f)).read()
+        # launched through GP_KERNEL, or traced by hand with gp_prof_post
+        names |= set(re.findall(r'GP_KERNEL\(ctx, "(k_[a-z_0-9]+)"', text))
+        names |= set(re.findall(r'gp_prof_post\(ctx, "(k_[a-z_0-9]+)"\)', text))
+    return names
+
+
+def test_every_step_kernel_has_algorithmic_bytes():
+    launched = _launched(["gp_sample.cu", "gp_nn.cu", "gp_step.cu"])
+    setup = {"k_knn_sigma", "k_normals", "k_emit_pts"}  # band set-up, untimed
+    assert STEP_KERNELS <= launched
+    for name in launched - setup - UNCOUNTED:
+        assert bench.alg_bytes(name, 1000, 100, 512, 300) > 0, name
+
+
+def test_byte_counts_are_the_arrays_touched_once():
+    n, J, Vs, Vt = 1000, 100, 512, 300
+    assert bench.alg_bytes("k_order_count", n, J, Vs, Vt) == 4 * J          # the epoch's slot of each point
+    assert bench.alg_bytes("k_nn", n, J, Vs, Vt) == 36 * n + 16 * J          # q in, record + index out; points
+    assert bench.alg_bytes("k_query", n, J, Vs, Vt) == 24 * n + 8 * Vt      # records; D read, grad written
+    assert bench.alg_bytes("k_adam", n, J, Vs, Vt) == 28 * Vt               # D, g, m, v read; D, m, v written
+    assert bench.alg_bytes("k_tv", n, J, Vs, Vt) == 8 * Vs                  # D read, grad written
+    assert bench.alg_bytes("k_unknown", n, J, Vs, Vt) == 0
