@@ -433,14 +433,15 @@ void gp_multi_destroy(gp_multi* m);
 
 /* ------------------------------------------------------- no allocation */
 
-/* The query part of gp_step (Eq. 4, 6, 7: L_Pull + beta L_Surface +
- * gamma L_grad, averaged over the valid records, and its gradient) on a dense
- * grid the caller owns, for callers that cannot allocate device memory: a
- * plugin whose host framework owns every device allocation, a real-time loop
- * that may not block on the allocator, or code that plans all of its memory up
- * front.  The paper has no counterpart; it is the same arithmetic as gp_step
- * with GP_STEP_NO_TV on a band built with M1 = M2 = -1 (every cell in the pull
- * band), without the band.
+/* An allocation-free form of the query part of gp_step (L_Pull + beta
+ * L_Surface + gamma L_grad, averaged over the valid records, and its
+ * gradient) on a dense grid the caller owns.  It is for callers that cannot
+ * allocate device memory: a plugin whose host framework owns every device
+ * allocation, a real-time loop that may not block on the allocator, or code
+ * that plans all of its memory up front.  Such callers cannot build a band,
+ * since gp_build_band allocates.  The paper has no counterpart to this entry
+ * point; its results equal those of gp_step with GP_STEP_NO_TV on a band built
+ * with M1 = M2 = -1 (every cell in the pull band).
  *
  * d_dev: (R+1)^3 float32 grid values, vertex (i,j,k) at i + (R+1)(j + (R+1)k).
  * rec_dev: B step records (qx,qy,qz,sx,sy,sz); a record is valid when q lies in
@@ -451,10 +452,12 @@ void gp_multi_destroy(gp_multi* m);
  * Nothing is allocated: the call's scratch (one row of partial sums per 256
  * records, two counters) is a fixed array of about 128 KiB compiled into the
  * library, which every GPU that loads the library holds until the process
- * exits.  The first call on a device looks up that array's device address
- * (with the device current) and keeps it: make that first call before any
- * stream capture.  Every call shares the array; calls whose work overlaps on
- * the GPU (other streams or host threads) race on it and give wrong results.
+ * exits.  The call makes the context's device current while it runs and puts
+ * the caller's current device back before it returns.  The first call on a
+ * device looks up that array's device address and keeps it: make that first
+ * call before any stream capture.  Every call shares the array and clears the
+ * counters it needs; calls whose work overlaps on the GPU (other streams or
+ * host threads) race on it and give wrong results.
  * Errors: GP_ERR_ARG (R or B out of range, null pointers), GP_ERR_CUDA. */
 gp_status gp_step_dense_noalloc(gp_ctx* ctx, int32_t R, const float* d_dev, const float* rec_dev, int64_t B,
                                 const gp_loss_w* w, float* grad_dev, float* loss_dev);

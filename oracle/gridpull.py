@@ -47,6 +47,10 @@ import numpy as np
 # Loss weights of Sec. 4 "Details": alpha (TV), beta (surface), gamma (gradient).
 DEFAULT_WEIGHTS = (1.0, 1.0, 0.005)
 NORM_FLOOR = 1e-12
+# Cap of the residual's conditioning factor kappa = |q - s| / |r| in the
+# per-vertex tolerance scale (abs_terms): kappa grows without bound as r -> 0,
+# so the scale it multiplies is capped at this factor over the plain terms.
+KAPPA_MAX = 64.0
 
 
 # ------------------------------------------------------------------ grid
@@ -463,13 +467,19 @@ def query_terms(D: np.ndarray, R: int, pull_cells: np.ndarray, q: np.ndarray, s:
         # kappa = |q - s| / |r| times u (r is a difference of vectors of size
         # |q - s|).  Those sizes, times |w_c| and |dw_c/dx_a|, are the scale
         # against which a float32 evaluation is compared.
-        kappa = np.maximum(1.0, np.linalg.norm(q64 - s64, axis=1) / np.maximum(l_pull, 1e-300))
+        kappa_raw = np.maximum(1.0, np.linalg.norm(q64 - s64, axis=1) / np.maximum(l_pull, 1e-300))
+        kappa = np.minimum(kappa_raw, KAPPA_MAX)
+        out["kappa_max"] = float(kappa_raw.max())
         sq_g = kappa * np.linalg.norm(dL_dn, axis=1) / np.maximum(_norm(g), NORM_FLOOR)
         ss_g = np.linalg.norm(dL_dns, axis=1) / np.maximum(_norm(gs), NORM_FLOOR)
         tq = (w * kappa)[:, None] * np.abs(sfq) + sq_g[:, None] * np.abs(sgq).sum(axis=1)
         ts = np.abs(dL_dfs)[:, None] * np.abs(sfs) + ss_g[:, None] * np.abs(sgs).sum(axis=1)
         out["abs_terms"] = np.zeros_like(D)
         np.add.at(out["abs_terms"], keys, np.concatenate([tq, ts], axis=1).reshape(-1))
+        # The plain absolute sum of the contributions added at each vertex,
+        # sum_k |c_k|: the condition of the sum itself (abs_terms >= this).
+        out["abs_contrib"] = np.zeros_like(D)
+        np.add.at(out["abs_contrib"], keys, np.abs(vals))
     out["grad"] = grad
     return out
 
@@ -529,6 +539,8 @@ def step_loss_grad(D: np.ndarray, R: int, sets: dict, q: np.ndarray, s: np.ndarr
     if with_grad:
         res["grad"] = qt["grad"] + alpha * tv_grad
         res["abs_terms"] = qt.get("abs_terms", np.zeros_like(D)) + alpha * tv_abs
+        res["abs_contrib"] = qt.get("abs_contrib", np.zeros_like(D)) + alpha * tv_abs
+        res["kappa_max"] = qt.get("kappa_max", 1.0)
     return res
 
 

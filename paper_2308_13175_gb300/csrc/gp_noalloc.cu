@@ -13,7 +13,9 @@
 // it (about 128 KiB) until the process exits.  Host code cannot hand the
 // array's name to a kernel (on the host it is only a stand-in), so the first
 // call on a device, with that device current, looks up its device address with
-// cudaGetSymbolAddress and keeps it.  Every call on a device shares the array
+// cudaGetSymbolAddress and keeps it.  Each call makes the context's device
+// current while it runs and restores the caller's current device before it
+// returns.  Every call on a device shares the array
 // and leaves the last call's sums in it; each call clears the counters it needs
 // before use.  Two calls whose work overlaps on the GPU (different streams, or
 // different host threads) race on the array and both results are then wrong:
@@ -247,14 +249,31 @@ __global__ void __launch_bounds__(NA_THREADS) k_na_query(int R, const float* __r
   }
 }
 
-// Device address of the scratch array on the context's device; looked up once
-// per device by the first call, with that device current.
+// Makes `dev` the calling thread's current device for the scope of the call
+// and puts the caller's device back on every return path, so the call never
+// leaves the thread on another device than it found it on.
+struct DeviceScope {
+  int prev = -1;
+  cudaError_t err = cudaSuccess;
+  explicit DeviceScope(int dev) {
+    err = cudaGetDevice(&prev);
+    if (err == cudaSuccess && prev != dev) err = cudaSetDevice(dev);
+    if (err != cudaSuccess) cudaGetLastError();
+  }
+  ~DeviceScope() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+// Device address of the scratch array on the current device (the context's,
+// made current by the caller's DeviceScope); looked up once per device by the
+// first call.
 gp_status na_scratch(gp_ctx* ctx, double** out) {
   const int dev = ctx->device;
   if (dev < 0 || dev >= NA_MAX_DEVICES) return gp_fail(ctx, GP_ERR_ARG, "gp_step_dense_noalloc: device index >= 64");
   std::lock_guard<std::mutex> lock(g_scratch_mutex);
   if (!g_scratch_addr[dev]) {
-    GP_CUDA(ctx, cudaSetDevice(dev));
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, gp_noalloc_scratch);
     if (e != cudaSuccess || !p) return gp_cuda_fail(ctx, e != cudaSuccess ? e : cudaErrorInvalidSymbol,
@@ -277,6 +296,8 @@ extern "C" gp_status gp_step_dense_noalloc(gp_ctx* ctx, int32_t R, const float* 
                    "gp_step_dense_noalloc: B must be in [0, 1048576] (one scratch row per 256 records)");
   if (!d_dev || !loss_dev || !w || (B > 0 && !rec_dev))
     return gp_fail(ctx, GP_ERR_ARG, "gp_step_dense_noalloc: null pointer");
+  DeviceScope scope(ctx->device);
+  if (scope.err != cudaSuccess) return gp_cuda_fail(ctx, scope.err, "gp_step_dense_noalloc: cudaSetDevice");
   double* scratch = nullptr;
   gp_status st = na_scratch(ctx, &scratch);
   if (st) return st;

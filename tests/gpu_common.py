@@ -47,15 +47,35 @@ def assert_rel(got, want, tol=REL_TOL, what="value"):
     assert abs(got - want) <= tol * abs(want) + 1e-30, f"{what}: got {got!r}, want {want!r}"
 
 
-def assert_grad_close(g, ref, scale=None, tol=REL_TOL, what="grad"):
+def survey_failures(g, ref, tol=REL_TOL):
+    """Vertices outside the stricter per-vertex bound
+    |g_i - ref_i| <= tol * max(|ref_i|, 1e-3 max|ref|), reported beside the
+    contract (it ignores cancellation inside a vertex's sum)."""
+    g = np.asarray(g, np.float64)
+    ref = np.asarray(ref, np.float64)
+    if ref.size == 0:
+        return 0, 0.0
+    floor = np.maximum(np.abs(ref), 1e-3 * np.max(np.abs(ref)))
+    rel = np.abs(g - ref) / np.maximum(floor, 1e-300)
+    return int(np.count_nonzero(rel > tol)), float(rel.max())
+
+
+def assert_grad_close(g, ref, scale=None, tol=REL_TOL, what="grad", kappa_max=None):
     """Norm-wise relative error <= tol, and per vertex
     |g_i - ref_i| <= tol * scale_i, where scale_i is the oracle's conditioning
-    of that vertex's sum (the sizes of the products it adds up; >= |ref_i|).
-    Without a scale the per-vertex check uses max(|ref_i|, 1e-3 max|ref|)."""
+    of that vertex's sum (the sizes of the products it adds up; >= |ref_i| and
+    pinned to at most 64 times the absolute sum of its contributions).
+    Without a scale the per-vertex check uses max(|ref_i|, 1e-3 max|ref|).
+    Prints how many vertices miss that stricter bound and, when given, the
+    largest residual conditioning factor kappa of the records."""
     g = np.asarray(g, np.float64)
     ref = np.asarray(ref, np.float64)
     nrm = np.linalg.norm(ref)
     err = np.linalg.norm(g - ref)
+    nfail, worst_rel = survey_failures(g, ref, tol)
+    print(f"[{what}] norm err {err / max(nrm, 1e-300):.3e}; vertices over tol*max(|g*|, 1e-3 |g*|_inf): "
+          f"{nfail} of {ref.size} (worst {worst_rel:.3e})"
+          + (f"; kappa max {kappa_max:.3g}" if kappa_max is not None else ""))
     assert err <= tol * nrm, f"{what}: |g - ref| / |ref| = {err / max(nrm, 1e-300):.3e}"
     if scale is None:
         scale = np.maximum(np.abs(ref), 1e-3 * np.max(np.abs(ref)))

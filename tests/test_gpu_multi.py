@@ -125,7 +125,8 @@ def test_multi_steps_match_single_band_calls_and_oracle(gb, ctx, clouds, spatial
             assert np.min(np.abs(ref["per_query"]["fs"])) > 1e-3  # no rounding-decided sign
             keys = vertex_keys(ijk[exists], R)
             assert np.all(grad[~exists] == 0.0)
-            assert_grad_close(grad[exists], ref["grad"][keys], ref["abs_terms"][keys], what=f"cloud {k} step {t}")
+            assert_grad_close(grad[exists], ref["grad"][keys], ref["abs_terms"][keys], what=f"cloud {k} step {t}",
+                              kappa_max=ref["kappa_max"])
             # Adam at step t + 1 with the scheduled rate, on the GPU's own gradient.
             _, d1, _, _ = export_band(band)
             _, m1, v1 = [x.cpu().numpy().astype(np.float64) for x in gb.gp_band_values(band)]
@@ -180,7 +181,8 @@ def test_multi_tiny_clouds(gb, ctx):
                 assert_rel(L[k, slot], ref[key], what=f"cloud {k} step {t} {key}")
             grad = gb.gp_multi_buffers(multi, k)[2].cpu().numpy()
             keys = vertex_keys(ijk[exists], R)
-            assert_grad_close(grad[exists], ref["grad"][keys], ref["abs_terms"][keys], what=f"cloud {k} step {t}")
+            assert_grad_close(grad[exists], ref["grad"][keys], ref["abs_terms"][keys], what=f"cloud {k} step {t}",
+                              kappa_max=ref["kappa_max"])
     assert gb.gp_multi_get_info(multi)["error_bits"] == 0
     multi.close()
 

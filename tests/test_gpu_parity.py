@@ -386,7 +386,8 @@ def _check_step(gb, band, R, sets, q, s, weights, D, flags=0, d_override=None):
         return ref
     assert np.all(grad[~exists] == 0.0)
     keys = vertex_keys(ijk[exists], R)
-    assert_grad_close(grad[exists], ref["grad"][keys], ref["abs_terms"][keys])
+    assert_grad_close(grad[exists], ref["grad"][keys], ref["abs_terms"][keys], what=f"step R={R} flags={flags}",
+                      kappa_max=ref["kappa_max"])
     # Nothing outside the stored set receives gradient in the oracle.
     assert np.sum(np.abs(ref["grad"])) == pytest.approx(np.sum(np.abs(ref["grad"][keys])), rel=1e-12)
     return ref

@@ -257,6 +257,35 @@ def test_full_gradient_matches_central_differences(seed):
     assert np.all(res["grad"][other] == 0)
 
 
+@pytest.mark.parametrize("R,npts,nq,sig,seed,noise,M", [
+    (8, 60, 80, 0.1, 0, 0.05, 1), (8, 60, 80, 0.1, 1, 0.05, 1),
+    (64, 5000, 30000, 0.03, 1, 0.01, 2), (64, 5000, 30000, 0.03, 2, 0.0, 2), (64, 5000, 30000, 0.03, 3, 0.05, 2)])
+def test_tolerance_scale_is_bounded_on_both_sides(R, npts, nq, sig, seed, noise, M):
+    """The per-vertex tolerance scale S_i (abs_terms) is pinned from below and
+    from above by the plain absolute sum A_i = sum_k |c_k| of the contributions
+    c_k the gradient sum adds at vertex i:  |g_i| <= A_i <= S_i <= 64 A_i.
+    Measured on these cases: S_i / A_i reaches 5.9, 6.6, 25, 52 and 13 (median
+    1-1.7), with kappa = |q - s| / |r| up to 87 before its cap of 64, so a
+    scale inflated by a factor of two fails the bound on the exact sphere."""
+    rng = np.random.default_rng(seed)
+    pts = synth.sphere_cloud(npts, 0.45, seed=seed + 10)
+    sets = o.band_sets(pts, R, M, M)
+    keys = np.arange((R + 1) ** 3)
+    verts = -1.0 + o.grid_spacing(R) * o.key_to_vertex(keys, R)
+    D = np.linalg.norm(verts, axis=1) - 0.45 + noise * rng.normal(size=len(keys))
+    q, j = synth.gaussian_queries(pts, nq, sig, seed=seed + 20)
+    res = o.step_loss_grad(D, R, sets, q, pts[j], (1.0, 1.0, 0.005))
+    S, A, g = res["abs_terms"], res["abs_contrib"], res["grad"]
+    assert np.all(A >= np.abs(g) * (1 - 1e-12))
+    assert np.all(S >= A * (1 - 1e-12))
+    C = 64.0
+    m = A > 0
+    ratio = S[m] / A[m]
+    print(f"tolerance scale: max S/A = {ratio.max():.3g}, kappa max = {res['kappa_max']:.3g}")
+    assert ratio.max() <= C
+    assert np.all(S[~m] == 0)
+
+
 # ------------------------------------------------------ nearest point
 def test_nearest_point_matches_kdtree_and_breaks_ties_low():
     from scipy.spatial import cKDTree

@@ -1,8 +1,9 @@
 """gp_step_dense_noalloc: the query part of the step on a caller-owned dense
 grid, for callers that cannot allocate device memory (its scratch is a fixed
-array inside the library).  Checked through the C ABI against gp_step on a
-dense band (every cell in the pull band, L_TV left out), on two calls in a row
-so that the second call sees the scratch the first one left behind.
+array inside the library).  Checked through the C ABI against the float64
+oracle and against gp_step on a dense band (every cell in the pull band, L_TV
+left out), on two calls in a row so that the second call sees the scratch the
+first one left behind; the caller's current device is unchanged by the calls.
 
 This file is collected last on purpose: it must pass on its own in a fresh
 process and after every other test."""
@@ -46,7 +47,9 @@ def test_dense_noalloc_matches_gp_step_twice():
         gb.gp_step(band, rec, B, g_band, l_band, w, flags=gb.GP_STEP_NO_TV)
         g_na = torch.full((n1 ** 3,), 3.0, dtype=torch.float32, device="cuda")
         l_na = torch.full((8,), 3.0, dtype=torch.float32, device="cuda")
+        dev_before = torch.cuda.current_device()
         gb.gp_step_dense_noalloc(ctx, R, d_dense, rec, B, g_na, l_na, w)
+        assert torch.cuda.current_device() == dev_before
         torch.cuda.synchronize()
         lb, ln = l_band.cpu().numpy(), l_na.cpu().numpy()
         assert ln[gb.GP_LOSS_BV] == lb[gb.GP_LOSS_BV] == B - 50
@@ -54,10 +57,17 @@ def test_dense_noalloc_matches_gp_step_twice():
             assert_rel(ln[slot], lb[slot], what=f"call {call} slot {slot}")
         gn = g_na.cpu().numpy().astype(np.float64)
         gband = g_band.cpu().numpy().astype(np.float64)
-        # Both sides are float32 sums in different atomic orders: each may be
-        # off by the tolerance times the oracle's conditioning scale of the vertex.
+        # The float64 oracle on the same grid and records: the loss slots of
+        # this entry point against it directly, not only against gp_step.
         sets = {"pull_cells": np.arange(R ** 3), "tv": np.zeros(0, np.int64)}
         ref = o.step_loss_grad(dense.astype(np.float64), R, sets, q, pts[j], w)
+        assert ref["Bv"] == B - 50
+        for slot, want in ((gb.GP_LOSS_TOTAL, ref["loss"]), (gb.GP_LOSS_PULL, ref["l_pull"]),
+                           (gb.GP_LOSS_GRAD, ref["l_grad"]), (gb.GP_LOSS_SURF, ref["l_surf"])):
+            assert_rel(ln[slot], want, what=f"call {call} slot {slot} vs oracle")
+        assert_grad_close(gn[keys], ref["grad"][keys], ref["abs_terms"][keys], what=f"call {call} grad vs oracle")
+        # Both GPU sides are float32 sums in different atomic orders: each may be
+        # off by the tolerance times the oracle's conditioning scale of the vertex.
         assert_grad_close(gn[keys], gband[exists], 2 * ref["abs_terms"][keys], what=f"call {call} grad")
         assert np.all(gn[np.setdiff1d(np.arange(n1 ** 3), keys)] == 0)
 
