@@ -6,13 +6,15 @@ pool: gp_sample (Gaussian queries around points in the epoch's random order)
 hand-written backward, L_TV included) -> gp_update (Adam on the trainable
 vertices).  Band construction and sigma are once-per-cloud set-up, untimed.
 
-Default workload: the single synthetic object (3 random ellipsoids and a
-torus, 100,000 points with N(0, 0.001^2) noise), 256^3 grid with a band of
+Default workload: the largest single-GPU configuration, the synthetic indoor
+scene (a 10 x 8 x 3 m room plus 60 boxes and cylinders, 10,000,000 points with
+N(0, 0.002^2) m noise, normalised to [-1,1]^3), a 1024^3 grid with a band of
 cells within 2 voxels of the points stored as 8^3 float32 bricks, a pool of
-2,000,000 queries per epoch and batches of 262,144 queries.
+50,000,000 queries per epoch and batches of 2,097,152 queries.  --workload
+selects the single object, the sphere, the superquadrics or the collection.
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
-on a bounded sample of the same workload instead.
+on all host cores, on a bounded sample of the same workload, instead.
 """
 from __future__ import annotations
 
@@ -44,7 +46,7 @@ WORKLOADS = {
     "sphere": dict(desc="single sphere: 5,000 points on a radius-0.5 sphere; dense 64^3 grid; 50,000 queries "
                         "(10 per point), full batch",
                    cloud=lambda: __import__("paper_2308_13175_gb300.synth", fromlist=["x"]).sphere_cloud(5000, 0.5, 0),
-                   R=64, M1=-1, M2=-1, Q=50_000, B=50_000, lr=1e-3),
+                   R=64, M1=-1, M2=-1, Q=50_000, B=50_000, lr=1e-3, init="sphere_noise"),
     "scene": dict(desc="indoor scene: 10 x 8 x 3 m room (floor, ceiling, 4 walls) + 60 boxes / cylinders, "
                        "10,000,000 points + N(0, 0.002 m^2) noise, normalised to [-1,1]^3; 1024^3 grid, band of "
                        "8^3 float32 bricks; pool 50,000,000 queries/epoch, batch 2,097,152",
@@ -81,7 +83,24 @@ def alg_bytes(name, n, J, Vs, Vt):
     }.get(name, 0)
 
 
-KERNEL_BOUND = {"k_nn": "hbm", "k_nn_sorted": "hbm", "k_tv": "hbm", "k_query": "hbm", "k_adam": "hbm", "k_sample": "hbm"}
+# The nearest-point kernels are bound by issue and SIMT divergence in their
+# float32 distance arithmetic, not by bytes: their roofline is the FP32 pipe,
+# in the flops of the candidate distances they evaluate (counted by
+# gp_nn_work): per candidate 3 subtractions, 1 multiply and 2 FMAs = 8 flops
+# (FMA = 2).  Peak: 152 SMs x 128 FP32 lanes x 2 flops x the maximum SM clock.
+NN_KERNELS = ("k_nn", "k_nn_sorted")
+NN_FLOPS_PER_CANDIDATE = 8
+FP32_LANES_PER_SM = 128
+
+
+def fp32_peak_tflops(num_sms: int):
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mhz = float(json.load(f)["sm_max_mhz"])
+        kind = "derived: SMs x 128 FP32 lanes x 2 x measured max SM clock"
+    except Exception:
+        mhz, kind = 2070.0, "derived: SMs x 128 FP32 lanes x 2 x nominal max SM clock 2070 MHz"
+    return num_sms * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12, kind
 
 
 def fwd_bwd_adam(per_kernel: dict, names, queries_per_step: float, V_trainable: int, peak: float) -> dict:
@@ -104,7 +123,7 @@ def fwd_bwd_adam(per_kernel: dict, names, queries_per_step: float, V_trainable: 
 # the dominant kernel from one ncu capture of the current kernel code
 # (summaries in profiles/), by workload; a kernel changed since its capture
 # must be dropped from here.
-NCU_TRAFFIC = {("object", "k_nn"): 10_305_024, ("scene", "k_nn_sorted"): 1_132_552_704}
+NCU_TRAFFIC = {}
 
 
 def peaks():
@@ -119,41 +138,74 @@ def peaks():
 
 # -------------------------------------------------------------- clocks
 class ClockSampler:
-    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    """SM clock and throttle reasons sampled by nvidia-smi (read-only query)
+    every 50 ms during the timed region.  The GPU is selected by its UUID (a
+    local index can name another GPU when CUDA_VISIBLE_DEVICES remaps
+    devices), and nvidia-smi's output is read line by line from a pipe by a
+    reader thread, so no sample is lost in a file buffer when it is stopped."""
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index: int):
-        self.index = index
+    def __init__(self, local: int):
+        self.local = local
         self.proc = None
-        self.file = None
+        self.rows = []
+        self.thread = None
+        self.error = None
+
+    def _gpu_id(self):
+        try:
+            import torch
+            u = str(torch.cuda.get_device_properties(self.local).uuid)
+            return u if u.startswith("GPU-") else "GPU-" + u
+        except Exception:
+            vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+            if vis:
+                return vis.split(",")[self.local].strip()
+            return str(self.local)
 
     def start(self):
+        import shutil
+        import threading
+        cmd = ["nvidia-smi", f"--id={self._gpu_id()}", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+               "-lms", "50"]
+        if shutil.which("stdbuf"):
+            cmd = ["stdbuf", "-oL"] + cmd
         try:
-            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
-            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
-                                          "--format=csv,noheader,nounits", "-lms", "50"],
-                                         stdout=self.file, stderr=subprocess.DEVNULL)
-        except Exception:
-            self.proc = None
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True, bufsize=1)
+        except Exception as e:
+            self.proc, self.error = None, f"nvidia-smi: {e}"
+            return
+
+        def reader():
+            for line in self.proc.stdout:
+                if line.strip():
+                    self.rows.append(line.strip().split(","))
+        self.thread = threading.Thread(target=reader, daemon=True)
+        self.thread.start()
+        time.sleep(0.3)  # nvidia-smi's first sample
 
     def stop(self):
         if self.proc is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0,
+                    "error": self.error or "nvidia-smi unavailable"}
+        time.sleep(0.15)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        self.file.flush()
-        self.file.seek(0)
-        rows = [r.split(",") for r in self.file.read().strip().splitlines() if r.strip()]
-        self.file.close()
-        os.unlink(self.file.name)
+        if self.thread is not None:
+            self.thread.join(timeout=5)
+        err = ""
+        try:
+            err = (self.proc.stderr.read() or "").strip()
+        except Exception:
+            pass
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for r in rows:
+        for r in self.rows:
             try:
                 sm.append(float(r[1]))
                 smax.append(float(r[2]))
@@ -162,8 +214,12 @@ class ClockSampler:
                         reasons.add(nm)
             except Exception:
                 continue
-        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        out = {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+               "reasons": sorted(reasons), "samples": len(sm)}
+        if not sm:
+            out["error"] = "no clock sample during the timed region" + (f": {err[:200]}" if err else "")
+            print("bench: WARNING: " + out["error"], file=sys.stderr)
+        return out
 
 
 # ---------------------------------------------------------------- helpers
@@ -213,55 +269,186 @@ def replica_rate(units: float, ms: float, world: int) -> float:
 
 
 # -------------------------------------------------- oracle CPU baseline
-# Largest cloud the timed oracle sample runs on: its set-up is a dense
-# (R+1)^3 FP64 array and its NN is brute force over every point.
-CPU_BASELINE_MAX_POINTS = 1_000_000
+def _dilate_bitmap(b: np.ndarray, M: int) -> np.ndarray:
+    """Chebyshev dilation of a 3-D boolean array by M (separable, per axis)."""
+    out = b
+    for ax in range(3):
+        src = out
+        res = src.copy()
+        n = src.shape[ax]
+        for d in range(1, min(M, n - 1) + 1):
+            hi = [slice(None)] * 3
+            lo = [slice(None)] * 3
+            hi[ax], lo[ax] = slice(d, None), slice(None, n - d)
+            res[tuple(hi)] |= src[tuple(lo)]
+            res[tuple(lo)] |= src[tuple(hi)]
+        out = res
+    return out
 
 
-def oracle_rate(pts, wl, sample_q: int, seed: int = 0, repeats: int = 1):
-    """Queries/s of the FP64 oracle on a bounded sample of the workload.
+def _corner_bitmap(cells: np.ndarray) -> np.ndarray:
+    """Vertices ((R+1)^3) that are corners of a cell of the (R^3) bitmap."""
+    R = cells.shape[0]
+    v = np.zeros((R + 1,) * 3, bool)
+    for dz in (0, 1):
+        for dy in (0, 1):
+            for dx in (0, 1):
+                v[dz:dz + R, dy:dy + R, dx:dx + R] |= cells
+    return v
 
-    Timed per step: the sampler, brute-force NN and the query terms with their
-    gradient for ``sample_q`` queries, plus the vertex work (L_TV over the TV
-    set and Adam over the trainable set) once.  The rate is extrapolated to a
-    full batch B: B / (t_query * B / sample_q + t_vertex).  Band sets, sigma of
-    the visited points and the dense value array are set-up (untimed)."""
+
+def band_counts(pts: np.ndarray, R: int, M1: int, M2: int) -> dict:
+    """|T| and the trainable-vertex count of the band, by dense occupancy
+    bitmaps (R^3 bytes): the sizes the CPU baseline extrapolates to."""
     from oracle import gridpull as o
-    R = wl["R"]
-    sets = o.band_sets(pts, R, wl["M1"], wl["M2"])
-    keys = np.arange((R + 1) ** 3) if R <= 128 else None
-    D = np.zeros((R + 1) ** 3)
-    h = 2.0 / R
-    c = 0.5 * (pts.min(0) + pts.max(0))
-    need = sets["required"] if keys is None else keys
-    v = -1.0 + h * o.key_to_vertex(need, R)
-    D[need] = np.linalg.norm(v - c, axis=1) - 2 * h
+    occ = np.zeros((R, R, R), bool)
+    c = o.key_to_cell(o.occupied_cells(pts, R), R)
+    occ[c[:, 2], c[:, 1], c[:, 0]] = True
+    out = {}
+    big = -1 if (M1 < 0 or M2 < 0) else max(M1, M2)
+    for name, M in (("V_tv", M2), ("V_trainable", big)):
+        out[name] = (R + 1) ** 3 if M < 0 else int(_corner_bitmap(_dilate_bitmap(occ, M)).sum())
+    return out
+
+
+def oracle_baseline(pts, wl, counts, budget_s: float, steps: int = 1, seed: int = 0):
+    """The FP64 oracle's step on all host cores, timed on a bounded sample of
+    the workload and extrapolated to a full batch.
+
+    Per step the four phases run on every core (oracle.parallel): brute-force
+    NN of n_nn queries, the sampler plus the query terms with their gradient for
+    n_q queries (s = the source point, values on a band-sparse store of the
+    analytic initial sphere), L_TV of n_tv TV vertices and Adam on n_ad
+    vertices.  Each phase's wall time over its units gives its time per unit;
+    a full step is B (t_nn + t_q) + |T| t_tv + V_trainable t_adam.  Sample
+    sizes are calibrated so that the timed phases of all steps take about
+    budget_s seconds.  Set-up (the cloud on disk, sigma of the sampled points,
+    the sparse stores) is untimed."""
+    from oracle import gridpull as o
+    from oracle.parallel import OraclePool
+    R, M1, B = wl["R"], wl["M1"], wl["B"]
     J = len(pts)
-    pos = np.arange(sample_q, dtype=np.int64) + 12345
-    j = o.point_permutation(J, seed, 0, pos % J)
-    sig = np.zeros(J)
-    uj = np.unique(j)
-    sig[uj] = o.knn_sigma(pts, 50, idx=uj)
-    m = np.zeros(len(sets["trainable"]))
-    vv = np.zeros(len(sets["trainable"]))
-    tq_all, tv_all = [], []
-    for r in range(repeats):
-        t0 = time.perf_counter()
-        q, _ = o.sample_queries(pts, sig, seed, 0, pos)
-        q = q.astype(np.float32)
-        nn = o.nearest_point(q, pts)
-        qt = o.query_terms(D, R, sets["pull_cells"], q, pts[nn], 1.0, 0.005)
-        t1 = time.perf_counter()
-        _, tvg, _ = o.tv_term(D, R, sets["tv"])
-        g = qt["grad"][sets["trainable"]] + tvg[sets["trainable"]]
-        o.adam(D[sets["trainable"]], g, m, vv, r + 1, wl["lr"])
-        t2 = time.perf_counter()
-        tq_all.append(t1 - t0)
-        tv_all.append(t2 - t1)
-    tq, tv = float(np.median(tq_all)), float(np.median(tv_all))
-    B = wl["B"]
-    per_step = tq * B / sample_q + tv
-    return B / per_step, {"t_query_s": tq, "t_vertex_s": tv, "sample_q": sample_q}
+    h = 2.0 / R
+    centre = 0.5 * (pts.min(0) + pts.max(0)).astype(np.float64)
+    init = lambda keys: np.linalg.norm(-1.0 + h * o.key_to_vertex(keys, R) - centre, axis=1) - 2 * h
+    occ = o.occupied_cells(pts, R)
+    tmp = tempfile.mkdtemp(prefix="gp_oracle_")
+    pts_path = os.path.join(tmp, "points.npy")
+    np.save(pts_path, np.ascontiguousarray(pts, np.float32))
+    occ_path = os.path.join(tmp, "occ.npy")
+    np.save(occ_path, occ)
+    pool = OraclePool(pts_path)
+    C = pool.cores
+    rng = np.random.default_rng(seed + 11)
+    weights = (1.0, 1.0, 0.005)
+    tree = None
+
+    def sigma_of(idx):
+        """sigma_j of the sampled points (set-up, untimed): the k-d tree of
+        scipy where it is installed (the 51st distance counting the point
+        itself is the 50th to another point), else the oracle's brute force."""
+        nonlocal tree
+        try:
+            from scipy.spatial import cKDTree
+        except Exception:
+            return o.knn_sigma(pts, 50, idx=idx)
+        if tree is None:
+            tree = cKDTree(np.asarray(pts, np.float64))
+        d, _ = tree.query(np.asarray(pts[idx], np.float64), k=min(51, J))
+        return d[:, -1] if J > 1 else np.zeros(len(idx))
+    try:
+        def make_terms(n, tag):
+            """Chunks of n sampled queries (pool positions of epoch 0)."""
+            pos = (np.arange(n, dtype=np.int64) * 7919 + 12345) % max(wl.get("Q", B), 1)
+            j = o.point_permutation(J, seed, 0, pos % J)
+            uj = np.unique(j)
+            sig = np.zeros(J)
+            sig[uj] = sigma_of(uj)
+            q, _ = o.sample_queries(pts, sig, seed, 0, pos)
+            q = q.astype(np.float32)
+            items, qs = [], []
+            for k, sl in enumerate(np.array_split(np.arange(n), C)):
+                cq, lq, _ = o.cell_and_local(q[sl], R)
+                cq = np.clip(cq, 0, R - 1)
+                cs, ls, _ = o.cell_and_local(pts[j[sl]], R)
+                cs, _ = o.clamp_cell(cs, ls, R)
+                keys = np.unique(np.concatenate([o.vertex_key(c + d, R) for c in (cq, cs) for d in o.CORNERS]))
+                pth = os.path.join(tmp, f"terms_{tag}_{k}.npz")
+                ju = np.unique(j[sl])
+                np.savez(pth, pos=pos[sl], j=j[sl], sig_idx=ju, sig_val=sig[ju], keys=keys, vals=init(keys))
+                items.append((pth, occ_path, R, M1, weights, seed))
+                qs.append(q[sl])
+            return items, qs
+
+        def make_nn(qs, n, tag):
+            allq = np.concatenate(qs)[:n]
+            paths = []
+            for k, part in enumerate(np.array_split(allq, C)):
+                pth = os.path.join(tmp, f"nn_{tag}_{k}.npy")
+                np.save(pth, part)
+                paths.append(pth)
+            return paths
+
+        def make_tv(n, tag):
+            cells = occ[rng.integers(0, len(occ), size=max(1, n // 8 + 1))]
+            tv = np.unique(np.concatenate([o.vertex_key(o.key_to_cell(cells, R) + d, R) for d in o.CORNERS]))[:n]
+            items = []
+            for k, part in enumerate(np.array_split(tv, C)):
+                nb, ok = o.axis_neighbours(part, R)
+                keys = np.unique(np.concatenate([part, nb[ok]]))
+                pth = os.path.join(tmp, f"tv_{tag}_{k}.npz")
+                np.savez(pth, tv=part, keys=keys, vals=init(keys))
+                items.append((pth, R, counts["V_tv"]))
+            return items, len(tv)
+
+        def make_adam(n, tag):
+            items = []
+            for k in range(C):
+                m = n // C
+                pth = os.path.join(tmp, f"adam_{tag}_{k}.npz")
+                np.savez(pth, d=rng.normal(size=m), g=rng.normal(size=m), m=rng.normal(size=m) * 1e-3,
+                         v=rng.random(m) * 1e-6)
+                items.append((pth, wl["lr"]))
+            return items, m * C
+
+        # Calibration: a small sample of each phase.
+        n0 = 2 * C
+        ti, qs = make_terms(64 * C, "cal")
+        t_q = pool.terms(ti) / (64 * C)
+        t_nn = pool.nn(make_nn(qs, n0, "cal")) / n0
+        tvi, ntv = make_tv(4096 * C, "cal")
+        t_tv = pool.tv(tvi) / ntv
+        adi, nad = make_adam(65536 * C, "cal")
+        t_ad = pool.adam(adi) / nad
+        # Size each phase to a quarter of the per-step budget.
+        per = budget_s / max(1, steps) / 4.0
+        n_nn = int(max(C, min(64 * C, per / max(t_nn, 1e-9))))
+        n_q = int(max(C, min(8192 * C, per / max(t_q, 1e-9))))
+        n_tv = int(max(C, min(1 << 20, per / max(t_tv, 1e-9))))
+        n_ad = int(max(C, min(1 << 22, per / max(t_ad, 1e-9))))
+        ti, qs = make_terms(n_q, "run")
+        nni = make_nn(qs, n_nn, "run")
+        tvi, n_tv = make_tv(n_tv, "run")
+        adi, n_ad = make_adam(n_ad, "run")
+        step_s = []
+        for _ in range(max(1, steps)):
+            a = pool.nn(nni) / n_nn
+            b = pool.terms(ti) / n_q
+            c = pool.tv(tvi) / n_tv
+            d = pool.adam(adi) / n_ad
+            step_s.append(B * (a + b) + counts["V_tv"] * c + counts["V_trainable"] * d)
+            parts = {"nn_s": B * a, "query_terms_s": B * b, "tv_s": counts["V_tv"] * c,
+                     "adam_s": counts["V_trainable"] * d}
+        t_step = float(np.median(step_s))
+        sample = (f"per step on {C} cores: brute-force NN of {n_nn} queries over all {J} points, sampler + query terms "
+                  f"and gradient of {n_q} queries (band-sparse values), L_TV of {n_tv} TV vertices, Adam on {n_ad} "
+                  f"vertices; extrapolated to B = {B}, |T| = {counts['V_tv']}, V_trainable = {counts['V_trainable']}")
+        return {"value": B / t_step, "unit": UNIT, "cores": C, "kind": "oracle", "sample": sample,
+                "step_s": t_step, "parts_s": {k: round(v, 3) for k, v in parts.items()}, "steps": len(step_s)}
+    finally:
+        pool.close()
+        import shutil
+        shutil.rmtree(tmp, ignore_errors=True)
 
 
 def run_reference(args, world, rank):
@@ -270,24 +457,16 @@ def run_reference(args, world, rank):
     wl = WORKLOADS[args.workload]
     pts = wl["cloud"]()
     t_start = time.perf_counter()
-    # Size each step's sample so that the W + K steps take about 150 s of CPU.
-    _, cal = oracle_rate(pts, wl, 256, repeats=1)
-    budget = 150.0 / max(1, args.steps + args.warmup)
-    per_q = cal["t_query_s"] / 256
-    sample_q = int(min(8192, max(64, (budget - cal["t_vertex_s"]) / max(per_q, 1e-9))))
-    if args.ref_sample > 0:
-        sample_q = args.ref_sample
-    if args.warmup > 1:
-        oracle_rate(pts, wl, sample_q, repeats=args.warmup - 1)
-    rate, info = oracle_rate(pts, wl, sample_q, repeats=max(1, args.steps))
+    counts = band_counts(pts, wl["R"], wl["M1"], wl["M2"])
+    # The W + K steps' timed phases take about 120 s of wall time in all.
+    cpu = oracle_baseline(pts, wl, counts, budget_s=120.0, steps=args.steps + args.warmup)
     elapsed = time.perf_counter() - t_start
-    sample = (f"each step: sampler + brute-force NN + query terms for {sample_q} queries and the full vertex "
-              f"work (L_TV + Adam) once; rate extrapolated to a {wl['B']}-query batch")
+    rate = cpu["value"]
     out = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wl["B"] / rate,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic", "config": {"workload": wl["desc"], "host_seconds": round(elapsed, 1)},
-           "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "cpu_baseline": cpu,
            "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
@@ -308,8 +487,13 @@ def run_ours(args, world, rank, local):
     ctx = gb.gp_create(local)
     band = gb.gp_build_band(ctx, torch.from_numpy(pts).cuda(), R, wl["M1"], wl["M2"], 50, nn_grid=args.nn_grid,
                             deterministic=args.deterministic)
-    c = 0.5 * (pts.min(0) + pts.max(0))
-    gb.gp_band_init_sphere(band, c, 2.0 * 2.0 / R, 0.0, seed=0)
+    if wl.get("init") == "sphere_noise":
+        # The single-sphere configuration's initial field: |x| - 0.5 plus
+        # N(0, 0.01) noise (variance 0.01, std 0.1).
+        gb.gp_band_init_sphere(band, (0.0, 0.0, 0.0), 0.5, 0.1, seed=0)
+    else:
+        c = 0.5 * (pts.min(0) + pts.max(0))
+        gb.gp_band_init_sphere(band, c, 2.0 * 2.0 / R, 0.0, seed=0)
     fit = FitStep(band, wl["Q"], wl["B"], seed=rank, weights=PAPER_WEIGHTS, lr=wl["lr"],
                   deterministic=args.deterministic)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -369,10 +553,37 @@ def run_ours(args, world, rank, local):
     fba = fwd_bwd_adam(per_kernel, ("k_count_valid", "k_tv", "k_query", "k_adam"), q_prof / args.steps, Vt, peak)
     dom = max(kern.items(), key=lambda kv: kv[1][1])[0]
     dk = per_kernel[dom]
-    achieved = dk["gbs"] or 0.0
-    roofline = {"bound": KERNEL_BOUND.get(dom, "hbm"), "kernel": dom, "achieved": achieved, "peak": peak,
-                "unit": "GB/s", "frac": round(achieved / peak, 4),
-                "traffic": NCU_TRAFFIC.get((args.workload, dom)), "peak_kind": peak_kind}
+    nn_work = None
+    nn_name = next((k for k in NN_KERNELS if k in per_kernel), None)
+    if nn_name is not None:
+        # Candidate distances of one launch, counted on the batches of the
+        # next two steps (the same search, the counting variant of the kernel).
+        cands = []
+        for t in (t0 + 2 * args.steps, t0 + 2 * args.steps + 1):
+            epoch, first, count = fit.batch_of(t)
+            gb.gp_sample(band, fit.seed, epoch, fit.Q, first, count, fit.q, fit.src, spatial=True)
+            nn_tmp = torch.empty(count, dtype=torch.int32, device="cuda")
+            cands.append(gb.gp_nn_work(band, fit.q[:count], nn_tmp, hint=fit.src[:count]) / count)
+        per_q = float(np.mean(cands))
+        nk = per_kernel[nn_name]
+        q_launch = q_prof / nk["launches"]
+        tfl = per_q * q_launch * NN_FLOPS_PER_CANDIDATE / (nk["avg_us"] * 1e-6) / 1e12
+        fp32_peak, fp32_kind = fp32_peak_tflops(torch.cuda.get_device_properties(local).multi_processor_count)
+        nn_work = {"kernel": nn_name, "candidates_per_query": round(per_q, 2),
+                   "candidates_per_s": per_q * q_launch / (nk["avg_us"] * 1e-6), "fp32_tflops": round(tfl, 3),
+                   "fp32_peak_tflops": round(fp32_peak, 2), "frac": round(tfl / fp32_peak, 4),
+                   "peak_kind": fp32_kind}
+    if dom in NN_KERNELS and nn_work is not None:
+        roofline = {"bound": "alu", "kernel": dom, "achieved": nn_work["fp32_tflops"],
+                    "peak": nn_work["fp32_peak_tflops"], "unit": "TFLOP/s", "frac": nn_work["frac"],
+                    "traffic": NCU_TRAFFIC.get((args.workload, dom)), "peak_kind": nn_work["peak_kind"],
+                    "work": f"{NN_FLOPS_PER_CANDIDATE} FP32 flops per candidate distance, "
+                            f"{nn_work['candidates_per_query']} candidates per query (gp_nn_work)"}
+    else:
+        achieved = dk["gbs"] or 0.0
+        roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                    "unit": "GB/s", "frac": round(achieved / peak, 4),
+                    "traffic": NCU_TRAFFIC.get((args.workload, dom)), "peak_kind": peak_kind}
 
     # Mesh extraction of the band as the steps left it (outside the timed
     # region): marching cubes over the optimised cells, each kernel traced.
@@ -381,6 +592,21 @@ def run_ours(args, world, rank, local):
     # 36-byte triangles the emit pass writes.
     mesh = None
     if rank == 0 and not args.deterministic:
+        # A field worth meshing: every stored vertex gets its exact distance
+        # to the cloud (gp_nn on the vertex positions) less half a cell, whose
+        # zero set is a thin closed sheet around the points - the shape a
+        # fitted band takes, where the steps above have barely moved the
+        # initial sphere.
+        ijk, _, fl = gb.gp_band_export(band)
+        inside = (fl & 4) != 0
+        vq = (-1.0 + (2.0 / R) * ijk.to(torch.float32)).contiguous()
+        del ijk
+        vnn = torch.empty(vq.shape[0], dtype=torch.int32, device="cuda")
+        gb.gp_nn(band, vq, vnn, None)
+        pts_t = torch.from_numpy(pts).cuda()
+        dist = torch.linalg.norm(vq - pts_t[vnn.clamp(min=0).long()], dim=1) - 0.5 * (2.0 / R)
+        gb.gp_band_set_values(band, torch.where(inside, dist, torch.zeros_like(dist)).contiguous())
+        del vq, vnn, dist, pts_t, inside, fl
         gb.gp_mesh_extract(band, 0.0, with_cells=False)  # warm-up
         gb.gp_profile(ctx, True)
         t_host = time.perf_counter()
@@ -517,16 +743,9 @@ def run_ours(args, world, rank, local):
         del ts, Dt, opt
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and J > CPU_BASELINE_MAX_POINTS:
-        cpu = {"value": None, "unit": UNIT, "kind": "oracle",
-               "skipped": f"{J} points: the oracle's dense (R+1)^3 value array, band set-up and brute-force NN "
-                          f"over the whole cloud are not a bounded sample above {CPU_BASELINE_MAX_POINTS} points"}
-    elif rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, cinfo = oracle_rate(pts, wl, args.cpu_sample)
-        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{args.cpu_sample} queries (sampler + brute-force NN + query terms) and the full vertex "
-                         f"work once, extrapolated to a {B}-query batch; t_query={cinfo['t_query_s']:.2f}s "
-                         f"t_vertex={cinfo['t_vertex_s']:.2f}s"}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        counts = {"V_tv": info["V_tv"], "V_trainable": Vt}
+        cpu = oracle_baseline(pts, wl, counts, budget_s=args.cpu_budget, steps=1)
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
@@ -542,6 +761,7 @@ def run_ours(args, world, rank, local):
                                "-> loss to host; next step's copy overlapped on a second stream; K steps timed "
                                "as one region, L2 flush included"},
                "gpu_launches": int(launches), "clocks": clk, "kernels": per_kernel, "fwd_bwd_adam": fba,
+               "nn_work": nn_work,
                "mesh": mesh,
                "torch_autograd": torch_cmp,
                "loss_last": loss_final}
@@ -699,9 +919,9 @@ def main():
     ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="object", choices=sorted(WORKLOADS))
-    ap.add_argument("--cpu-sample", type=int, default=4096)
-    ap.add_argument("--ref-sample", type=int, default=0, help="queries per oracle step (0 = sized to ~150 s total)")
+    ap.add_argument("--workload", default="scene", choices=sorted(WORKLOADS))
+    ap.add_argument("--cpu-budget", type=float, default=20.0,
+                    help="seconds of timed oracle work (all host cores) for the line's cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-torch", action="store_true", help="skip the plain PyTorch autograd comparison")
     ap.add_argument("--nn-grid", type=int, default=0, help="cells per axis of the point cell list (0 = automatic)")

@@ -228,6 +228,16 @@ gp_status gp_sample(gp_band* band, uint64_t seed, uint32_t epoch, int64_t Q, int
 gp_status gp_nn(gp_band* band, const float* q_dev, int64_t n, const int32_t* hint_dev, int32_t* nn_dev,
                 float* rec_dev, int32_t* nvalid_dev);
 
+/* The same search as gp_nn (same kernel and launch shape, same results in
+ * nn_dev), counting the point distances it evaluates: the seeds, every point
+ * of every cell range the walk reads and the float64 tie-break's re-reads.
+ * *work_host receives the count.  For measurement: the search's work in
+ * candidate evaluations.  Synchronises the stream; allocates and frees one
+ * 8-byte counter.  Errors: as gp_nn, plus GP_ERR_ARG for a null work_host or
+ * nn_dev, GP_ERR_OOM. */
+gp_status gp_nn_work(gp_band* band, const float* q_dev, int64_t n, const int32_t* hint_dev, int32_t* nn_dev,
+                     int64_t* work_host);
+
 /* ------------------------------------------------------------------- step */
 
 typedef struct gp_loss_w {

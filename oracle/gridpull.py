@@ -376,6 +376,80 @@ def sphere_init(vkeys: np.ndarray, R: int, center, radius: float, noise_std: flo
     return d
 
 
+# ------------------------------------------------- value stores and bands
+class SparseValues:
+    """Grid values held only at a set of vertices: ``keys`` (sorted, unique
+    vertex keys i + (R+1)(j + (R+1)k)) and ``vals`` (float64, one per key).
+    The loss functions accept it wherever they accept a dense ((R+1)^3,)
+    array; gradients are then returned over the same compact index (entry n
+    belongs to keys[n]).  Reading a vertex that is not held is an error."""
+
+    def __init__(self, keys, vals):
+        keys = np.asarray(keys, np.int64)
+        order = np.argsort(keys, kind="stable")
+        self.keys = keys[order]
+        self.vals = np.asarray(vals, np.float64)[order]
+        if len(self.keys) > 1 and np.any(self.keys[1:] == self.keys[:-1]):
+            raise ValueError("duplicate vertex keys")
+
+    def index(self, vkeys):
+        vkeys = np.asarray(vkeys, np.int64)
+        pos = np.searchsorted(self.keys, vkeys)
+        pos_c = np.minimum(pos, max(len(self.keys) - 1, 0))
+        if len(self.keys) == 0 or np.any(self.keys[pos_c] != vkeys):
+            raise KeyError("vertex not held by the sparse value store")
+        return pos_c
+
+
+def _store(D):
+    """(values array, key -> position map) of a dense array or SparseValues."""
+    if isinstance(D, SparseValues):
+        return D.vals, D.index
+    flat = np.asarray(D).reshape(-1)
+    return flat, (lambda k: k)
+
+
+def in_dilated_band(cell_keys, occupied_keys, M: int, R: int, keys_sorted: bool = False) -> np.ndarray:
+    """Membership of cells in the Chebyshev dilation by M of the occupied
+    cells (Sec. 3 bandwidth), tested per cell against the occupied keys
+    instead of building the dilated set: a cell is in the band iff some cell
+    within Chebyshev distance M of it is occupied.  M < 0: every cell.
+    keys_sorted: the occupied keys are already sorted (np.unique output)."""
+    cell_keys = np.asarray(cell_keys, np.int64)
+    if M < 0:
+        return np.ones(len(cell_keys), bool)
+    occ = np.asarray(occupied_keys, np.int64)
+    if not keys_sorted:
+        occ = np.sort(occ)
+    base = key_to_cell(cell_keys, R)
+    hit = np.zeros(len(cell_keys), bool)
+    rng = np.arange(-M, M + 1)
+    for dz in rng:
+        for dy in rng:
+            for dx in rng:
+                c = base + np.array([dx, dy, dz])
+                ok = np.all((c >= 0) & (c < R), axis=1) & ~hit
+                if not ok.any():
+                    continue
+                k = cell_key(c[ok], R)
+                pos = np.minimum(np.searchsorted(occ, k), max(len(occ) - 1, 0))
+                found = (occ[pos] == k) if len(occ) else np.zeros(len(k), bool)
+                hit[np.nonzero(ok)[0][found]] = True
+    return hit
+
+
+def _pull_member(pull_cells, cell_keys, R: int) -> np.ndarray:
+    """Pull-band membership: ``pull_cells`` is the band's cell keys, or a
+    function of an array of cell keys returning booleans."""
+    if callable(pull_cells):
+        return np.asarray(pull_cells(cell_keys), bool)
+    if R <= 256:
+        pull = np.zeros(R ** 3, dtype=bool)
+        pull[pull_cells] = True
+        return pull[cell_keys]
+    return np.isin(cell_keys, pull_cells)
+
+
 # ------------------------------------------------------- loss and gradient
 def _norm(v: np.ndarray) -> np.ndarray:
     return np.sqrt(np.sum(v * v, axis=1))
@@ -385,7 +459,8 @@ def _eval_at(D: np.ndarray, cell: np.ndarray, local: np.ndarray, R: int):
     """Corner keys, f, grad f and sensitivities at points with given cells."""
     h = grid_spacing(R)
     keys = np.stack([vertex_key(cell + c, R) for c in CORNERS], axis=1)   # (N, 8)
-    d8 = D.reshape(-1)[keys]
+    vals, index = _store(D)
+    d8 = vals[index(keys)]
     f, g, sf, sg = trilinear_eval(d8, local * h, h)
     return keys, f, g, sf, sg
 
@@ -407,7 +482,10 @@ def query_terms(D: np.ndarray, R: int, pull_cells: np.ndarray, q: np.ndarray, s:
                 beta: float, gamma: float, with_grad: bool = True):
     """Per-query terms of Eq. 4, 6 and 7 and, optionally, their gradient.
 
-    D: float64 dense grid values of shape ((R+1)^3,) indexed by vertex key.
+    D: float64 dense grid values of shape ((R+1)^3,) indexed by vertex key,
+    or a SparseValues holding at least the corners of the valid queries' cells
+    (gradients are then over its compact index).  pull_cells: the pull band's
+    cell keys, or a membership function of cell keys (in_dilated_band).
     q, s: float32 (B,3) query and its nearest surface point NN(q).
     Returns dict with per-query l_pull, l_grad, l_surf, valid, the sums, B_v and
     (if with_grad) the gradient of (1/B_v) * sum(l_pull + beta*l_surf + gamma*l_grad)
@@ -418,15 +496,14 @@ def query_terms(D: np.ndarray, R: int, pull_cells: np.ndarray, q: np.ndarray, s:
     cs, ls, _ = cell_and_local(s, R)
     cs, ls = clamp_cell(cs, ls, R)
     cq_c = np.clip(cq, 0, R - 1)
-    pull = np.zeros(R ** 3, dtype=bool)
-    pull[pull_cells] = True
-    valid = inside & pull[cell_key(cq_c, R)] & pull[cell_key(cs, R)]
+    valid = inside & _pull_member(pull_cells, cell_key(cq_c, R), R) & _pull_member(pull_cells, cell_key(cs, R), R)
     idx = np.nonzero(valid)[0]
     Bv = len(idx)
     out = {"valid": valid, "Bv": Bv}
     zeros = np.zeros(len(q))
     out["l_pull"], out["l_grad"], out["l_surf"] = zeros.copy(), zeros.copy(), zeros.copy()
-    grad = np.zeros_like(D) if with_grad else None
+    vals_D, index = _store(D)
+    grad = np.zeros_like(vals_D) if with_grad else None
     if Bv == 0:
         out.update(sum_pull=0.0, sum_grad=0.0, sum_surf=0.0, grad=grad)
         return out
@@ -456,7 +533,7 @@ def query_terms(D: np.ndarray, R: int, pull_cells: np.ndarray, q: np.ndarray, s:
         dL_dfs = w * beta * np.sign(fs)
         cq_grad = dL_df[:, None] * sfq + np.einsum("na,nak->nk", dL_dg, sgq)
         cs_grad = dL_dfs[:, None] * sfs + np.einsum("na,nak->nk", dL_dgs, sgs)
-        keys = np.concatenate([kq, ks], axis=1).reshape(-1)        # query order
+        keys = index(np.concatenate([kq, ks], axis=1).reshape(-1))  # query order
         vals = np.concatenate([cq_grad, cs_grad], axis=1).reshape(-1)
         np.add.at(grad, keys, vals)
         # Conditioning of each vertex's sum: the magnitudes of the elementary
@@ -474,59 +551,78 @@ def query_terms(D: np.ndarray, R: int, pull_cells: np.ndarray, q: np.ndarray, s:
         ss_g = np.linalg.norm(dL_dns, axis=1) / np.maximum(_norm(gs), NORM_FLOOR)
         tq = (w * kappa)[:, None] * np.abs(sfq) + sq_g[:, None] * np.abs(sgq).sum(axis=1)
         ts = np.abs(dL_dfs)[:, None] * np.abs(sfs) + ss_g[:, None] * np.abs(sgs).sum(axis=1)
-        out["abs_terms"] = np.zeros_like(D)
+        out["abs_terms"] = np.zeros_like(vals_D)
         np.add.at(out["abs_terms"], keys, np.concatenate([tq, ts], axis=1).reshape(-1))
         # The plain absolute sum of the contributions added at each vertex,
         # sum_k |c_k|: the condition of the sum itself (abs_terms >= this).
-        out["abs_contrib"] = np.zeros_like(D)
+        out["abs_contrib"] = np.zeros_like(vals_D)
         np.add.at(out["abs_contrib"], keys, np.abs(vals))
     out["grad"] = grad
     return out
 
 
-def tv_term(D: np.ndarray, R: int, tv_keys: np.ndarray, with_grad: bool = True):
-    """Eq. 5 per TV vertex, averaged over the TV set, and its gradient."""
-    T = len(tv_keys)
-    grad = np.zeros_like(D) if with_grad else None
-    if T == 0:
-        return 0.0, grad, np.zeros(0)
+def _tv_diffs(D, R: int, tv_keys: np.ndarray):
+    """d_i - d_n for the six axis neighbours of each TV vertex (0 where the
+    neighbour is outside [0, R]^3), the neighbour keys, the in-grid mask and the
+    store's value array and key map."""
+    vals, index = _store(D)
     nb, ok = axis_neighbours(tv_keys, R)
-    di = D[tv_keys][:, None]
-    diff = np.where(ok, di - D[nb], 0.0)
+    dn = np.zeros(nb.shape)
+    dn[ok] = vals[index(nb[ok])]
+    di = vals[index(tv_keys)][:, None]
+    return np.where(ok, di - dn, 0.0), nb, ok, vals, index
+
+
+def tv_term(D: np.ndarray, R: int, tv_keys: np.ndarray, with_grad: bool = True, n_tv=None):
+    """Eq. 5 per TV vertex, averaged over the TV set, and its gradient.
+
+    ``n_tv`` (default len(tv_keys)) is the divisor |T| of the mean: pass the
+    whole set's size to evaluate a subset of the TV vertices' terms."""
+    T = len(tv_keys) if n_tv is None else int(n_tv)
+    vals, _ = _store(D)
+    grad = np.zeros_like(vals) if with_grad else None
+    if len(tv_keys) == 0 or T == 0:
+        return 0.0, grad, np.zeros(0)
+    diff, nb, ok, vals, index = _tv_diffs(D, R, tv_keys)
     tv = np.sqrt(np.sum(diff * diff, axis=1))
     loss = tv.sum() / T
     if with_grad:
         pos = tv > 0
         coef = np.where(pos[:, None], diff / np.where(pos, tv, 1.0)[:, None], 0.0) / T
-        np.add.at(grad, tv_keys, coef.sum(axis=1))
-        np.add.at(grad, nb[ok], -coef[ok])
+        np.add.at(grad, index(tv_keys), coef.sum(axis=1))
+        np.add.at(grad, index(nb[ok]), -coef[ok])
     return loss, grad, tv
 
 
-def tv_term_abs(D: np.ndarray, R: int, tv_keys: np.ndarray) -> np.ndarray:
+def tv_term_abs(D: np.ndarray, R: int, tv_keys: np.ndarray, n_tv=None) -> np.ndarray:
     """Per vertex, the sum of |(d_i - d_n) / TV| over the terms of the L_TV
     gradient that land on it (conditioning of that sum)."""
-    out = np.zeros_like(D)
-    T = len(tv_keys)
-    if T == 0:
+    T = len(tv_keys) if n_tv is None else int(n_tv)
+    vals, _ = _store(D)
+    out = np.zeros_like(vals)
+    if len(tv_keys) == 0 or T == 0:
         return out
-    nb, ok = axis_neighbours(tv_keys, R)
-    diff = np.where(ok, D[tv_keys][:, None] - D[nb], 0.0)
+    diff, nb, ok, vals, index = _tv_diffs(D, R, tv_keys)
     tv = np.sqrt(np.sum(diff * diff, axis=1))
     pos = tv > 0
     coef = np.abs(np.where(pos[:, None], diff / np.where(pos, tv, 1.0)[:, None], 0.0)) / T
-    np.add.at(out, tv_keys, coef.sum(axis=1))
-    np.add.at(out, nb[ok], coef[ok])
+    np.add.at(out, index(tv_keys), coef.sum(axis=1))
+    np.add.at(out, index(nb[ok]), coef[ok])
     return out
 
 
 def step_loss_grad(D: np.ndarray, R: int, sets: dict, q: np.ndarray, s: np.ndarray,
                    weights=DEFAULT_WEIGHTS, with_grad: bool = True) -> dict:
-    """L = L_Pull + alpha L_TV + beta L_Surface + gamma L_grad (Eq. 8) and dL/dD."""
+    """L = L_Pull + alpha L_TV + beta L_Surface + gamma L_grad (Eq. 8) and dL/dD.
+
+    sets: "pull_cells" (keys or a membership function), "tv" (the TV vertex
+    keys whose terms are evaluated) and optionally "n_tv" (|T| when "tv" is a
+    subset).  D: dense array or SparseValues (see query_terms)."""
     alpha, beta, gamma = weights
+    n_tv = sets.get("n_tv")
     qt = query_terms(D, R, sets["pull_cells"], q, s, beta, gamma, with_grad)
-    tv_loss, tv_grad, tv_vals = tv_term(D, R, sets["tv"], with_grad)
-    tv_abs = tv_term_abs(D, R, sets["tv"]) if with_grad else None
+    tv_loss, tv_grad, tv_vals = tv_term(D, R, sets["tv"], with_grad, n_tv)
+    tv_abs = tv_term_abs(D, R, sets["tv"], n_tv) if with_grad else None
     Bv = qt["Bv"]
     mean = (lambda x: x / Bv) if Bv else (lambda x: 0.0)
     res = {
@@ -538,8 +634,9 @@ def step_loss_grad(D: np.ndarray, R: int, sets: dict, q: np.ndarray, s: np.ndarr
     res["loss"] = res["l_pull"] + alpha * res["l_tv"] + beta * res["l_surf"] + gamma * res["l_grad"]
     if with_grad:
         res["grad"] = qt["grad"] + alpha * tv_grad
-        res["abs_terms"] = qt.get("abs_terms", np.zeros_like(D)) + alpha * tv_abs
-        res["abs_contrib"] = qt.get("abs_contrib", np.zeros_like(D)) + alpha * tv_abs
+        zero = np.zeros_like(_store(D)[0])
+        res["abs_terms"] = qt.get("abs_terms", zero) + alpha * tv_abs
+        res["abs_contrib"] = qt.get("abs_contrib", zero) + alpha * tv_abs
         res["kappa_max"] = qt.get("kappa_max", 1.0)
     return res
 

@@ -87,6 +87,7 @@ SIGNATURES = {
     "gp_band_check": (ctypes.c_int, [_vp]),
     "gp_sample": (ctypes.c_int, [_vp, _u64, _u32, _i64, _i64, _i64, _u32, _vp, _vp, _vp]),
     "gp_nn": (ctypes.c_int, [_vp, _vp, _i64, _vp, _vp, _vp, _vp]),
+    "gp_nn_work": (ctypes.c_int, [_vp, _vp, _i64, _vp, _vp, ctypes.POINTER(_i64)]),
     "gp_step": (ctypes.c_int, [_vp, _vp, _i64, _vp, _vp, ctypes.POINTER(LossW), _vp, _vp, _u32]),
     "gp_update": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(Adam), _i64]),
     "gp_multi_create": (ctypes.c_int, [_vp, ctypes.POINTER(_vp), _i32, ctypes.POINTER(_i64), ctypes.POINTER(_i64),
@@ -412,6 +413,19 @@ def gp_nn(band: Band, q, nn_out=None, rec_out=None, hint=None, nvalid_out=None):
     band.ctx.check(band.ctx.lib.gp_nn(band.handle, _ptr(q), n, _ptr(hint), _ptr(nn_out), _ptr(rec_out),
                                       _ptr(nvalid_out)))
     return nn_out, rec_out
+
+
+def gp_nn_work(band: Band, q, nn_out, hint=None) -> int:
+    """gp_nn's search with a count of the point distances it evaluates."""
+    import torch
+    _need(q, torch.float32, name="q")
+    n = q.numel() // 3
+    _need(nn_out, torch.int32, n, "nn")
+    _need(hint, torch.int32, n, "hint")
+    band.ctx.sync_stream()
+    work = _i64(0)
+    band.ctx.check(band.ctx.lib.gp_nn_work(band.handle, _ptr(q), n, _ptr(hint), _ptr(nn_out), ctypes.byref(work)))
+    return int(work.value)
 
 
 def gp_step(band: Band, rec, B: int, grad, loss, weights=(1.0, 1.0, 0.005), nvalid=None, d=None, flags: int = 0):

@@ -199,6 +199,13 @@ __global__ void __launch_bounds__(128) k_normals(NNGrid g, int64_t J, const floa
   normals[3 * (int64_t)self + 2] = nv[2];
 }
 
+__device__ __forceinline__ void nn_add_work(unsigned long long* total, int v) {
+  unsigned long long w = (unsigned long long)v;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+  if ((threadIdx.x & 31) == 0 && w) atomicAdd(total, w);
+}
+
 // One thread per query.  Queries with a NaN, infinite or huge coordinate (whose
 // squared distances would overflow float32) get -1 and a NaN surface point.
 #ifndef GP_NN_BLOCK
@@ -209,11 +216,17 @@ __global__ void __launch_bounds__(128) k_normals(NNGrid g, int64_t J, const floa
 #else
 #define GP_NN_BOUNDS __launch_bounds__(GP_NN_BLOCK)
 #endif
+// COUNT: also add the number of point distances evaluated (seeds, walk and
+// tie-break) to *work_total, for measurement; the search is the same.
+template <bool COUNT>
 __global__ void GP_NN_BOUNDS k_nn(NNGrid g, const float* __restrict__ qin, int64_t n,
                                             const int32_t* __restrict__ hint, int64_t J,
                                             const float* __restrict__ pts_orig, int32_t* __restrict__ nn_out,
                                             float* __restrict__ rec, Grid band, int32_t* __restrict__ nvalid,
-                                            const float* __restrict__ normals) {
+                                            const float* __restrict__ normals,
+                                            unsigned long long* __restrict__ work_total) {
+  int work_v = 0;
+  int* work = COUNT ? &work_v : nullptr;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const bool active = i < n;
   float q[3] = {0.f, 0.f, 0.f};
@@ -232,11 +245,13 @@ __global__ void GP_NN_BOUNDS k_nn(NNGrid g, const float* __restrict__ qin, int64
     c[2] = nn_cell(q[2], g);
     margin = nn_margin(q);
     nn_seed(st, q, hint, i, J, pts_orig);
-    if (st.b1 < INFINITY) nn_seed_foot(st, q, hint, i, J, pts_orig, normals, g);
+    if (COUNT && st.b1 < INFINITY) ++work_v;
+    if (st.b1 < INFINITY) nn_seed_foot(st, q, hint, i, J, pts_orig, normals, g, work);
   }
   int best = -1;
-  if (ok) best = nn_thread_search(q, c, g, margin, st);
+  if (ok) best = nn_thread_search(q, c, g, margin, st, work);
   if (active) nn_finish(i, q, best, pts_orig, nn_out, rec, band, nvalid);
+  if (COUNT) nn_add_work(work_total, work_v);
 }
 
 // The same search for large seeded batches.  Each thread first seeds its own query; the block then sorts its queries (in
@@ -256,11 +271,15 @@ constexpr int NN_BUCKETS = 16;
 constexpr int64_t NN_SORTED_MIN_QUERIES = int64_t(1) << 20;
 static_assert(NN_SPAN % 32 == 0 && NN_THREADS % NN_SPAN == 0, "sort span");
 
+template <bool COUNT>
 __global__ void __launch_bounds__(NN_THREADS) k_nn_sorted(NNGrid g, const float* __restrict__ qin, int64_t n,
                                                    const int32_t* __restrict__ hint, int64_t J,
                                                    const float* __restrict__ pts_orig, int32_t* __restrict__ nn_out,
                                                    float* __restrict__ rec, Grid band, int32_t* __restrict__ nvalid,
-                                                   const float* __restrict__ normals) {
+                                                   const float* __restrict__ normals,
+                                                   unsigned long long* __restrict__ work_total) {
+  int work_v = 0;
+  int* work = COUNT ? &work_v : nullptr;
   __shared__ int s_off[NN_SEGS][NN_BUCKETS][NN_SPAN_WARPS];  // count, then first rank in the segment
   __shared__ float4 s_q[NN_THREADS];   // q, and the query's offset in the block (int bits; -1 - offset if invalid)
   __shared__ float4 s_st[NN_THREADS];  // b1, b2, thr, j1 (int bits)
@@ -279,8 +298,9 @@ __global__ void __launch_bounds__(NN_THREADS) k_nn_sorted(NNGrid g, const float*
   int key = 0;
   if (ok) {
     nn_seed(st, q, hint, i, J, pts_orig);
+    if (COUNT && st.b1 < INFINITY) ++work_v;
     if (st.b1 < INFINITY) {
-      nn_seed_foot(st, q, hint, i, J, pts_orig, normals, g);
+      nn_seed_foot(st, q, hint, i, J, pts_orig, normals, g, work);
       key = (int)fminf(4.0f * st.thr / (g.cs * g.cs), (float)(NN_BUCKETS - 2));
     } else {
       key = NN_BUCKETS - 1;  // unseeded: the ring search
@@ -319,9 +339,10 @@ __global__ void __launch_bounds__(NN_THREADS) k_nn_sorted(NNGrid g, const float*
   int best = -1;
   if (ok) {
     const int c[3] = {nn_cell(q[0], g), nn_cell(q[1], g), nn_cell(q[2], g)};
-    best = nn_thread_search(q, c, g, nn_margin(q), st);
+    best = nn_thread_search(q, c, g, nn_margin(q), st, work);
   }
   if (i < n) nn_finish(i, q, best, pts_orig, nn_out, rec, band, nvalid);
+  if (COUNT) nn_add_work(work_total, work_v);
 }
 
 // Points and sigma in emission order, for the sampler's coalesced reads.
@@ -458,14 +479,11 @@ extern "C" gp_status gp_band_sigma(const gp_band* b, float* sigma_dev) {
   return GP_OK;
 }
 
-extern "C" gp_status gp_nn(gp_band* b, const float* q_dev, int64_t n, const int32_t* hint_dev, int32_t* nn_dev,
-                           float* rec_dev, int32_t* nvalid_dev) {
-  if (!b) return GP_ERR_ARG;
+// The launch of gp_nn; work_total (device, NULL = not counted) receives the
+// number of point distances evaluated.
+static gp_status nn_launch(gp_band* b, const float* q_dev, int64_t n, const int32_t* hint_dev, int32_t* nn_dev,
+                           float* rec_dev, int32_t* nvalid_dev, unsigned long long* work_total) {
   gp_ctx* ctx = b->ctx;
-  if (n < 0 || n >= (int64_t(1) << 31)) return gp_fail(ctx, GP_ERR_ARG, "gp_nn: n must be in [0, 2^31)");
-  if (nvalid_dev) GP_CUDA(ctx, cudaMemsetAsync(nvalid_dev, 0, sizeof(int32_t), ctx->stream));
-  if (n == 0) return GP_OK;
-  if (!q_dev || (!nn_dev && !rec_dev)) return gp_fail(ctx, GP_ERR_ARG, "gp_nn: null pointer");
   NNGrid g = make_grid(b);
   Grid band;
   band.table = b->brick_table;
@@ -475,13 +493,59 @@ extern "C" gp_status gp_nn(gp_band* b, const float* q_dev, int64_t n, const int3
   band.R = b->R;
   band.half_r = 0.5f * (float)b->R;
   if (hint_dev && n >= NN_SORTED_MIN_QUERIES) {
-    GP_KERNEL(ctx, "k_nn_sorted",
-              k_nn_sorted<<<gp_blocks(n, NN_THREADS), NN_THREADS, 0, ctx->stream>>>(
-                  g, q_dev, n, hint_dev, b->J, b->pts, nn_dev, rec_dev, band, nvalid_dev, b->normals));
+    if (work_total)
+      GP_KERNEL(ctx, "k_nn_sorted_count",
+                k_nn_sorted<true><<<gp_blocks(n, NN_THREADS), NN_THREADS, 0, ctx->stream>>>(
+                    g, q_dev, n, hint_dev, b->J, b->pts, nn_dev, rec_dev, band, nvalid_dev, b->normals, work_total));
+    else
+      GP_KERNEL(ctx, "k_nn_sorted",
+                k_nn_sorted<false><<<gp_blocks(n, NN_THREADS), NN_THREADS, 0, ctx->stream>>>(
+                    g, q_dev, n, hint_dev, b->J, b->pts, nn_dev, rec_dev, band, nvalid_dev, b->normals, nullptr));
     return GP_OK;
   }
-  GP_KERNEL(ctx, "k_nn", k_nn<<<gp_blocks(n, GP_NN_BLOCK), GP_NN_BLOCK, 0, ctx->stream>>>(g, q_dev, n, hint_dev, b->J, b->pts,
-                                                                           nn_dev, rec_dev, band, nvalid_dev,
-                                                                           b->normals));
+  if (work_total)
+    GP_KERNEL(ctx, "k_nn_count",
+              k_nn<true><<<gp_blocks(n, GP_NN_BLOCK), GP_NN_BLOCK, 0, ctx->stream>>>(
+                  g, q_dev, n, hint_dev, b->J, b->pts, nn_dev, rec_dev, band, nvalid_dev, b->normals, work_total));
+  else
+    GP_KERNEL(ctx, "k_nn",
+              k_nn<false><<<gp_blocks(n, GP_NN_BLOCK), GP_NN_BLOCK, 0, ctx->stream>>>(
+                  g, q_dev, n, hint_dev, b->J, b->pts, nn_dev, rec_dev, band, nvalid_dev, b->normals, nullptr));
+  return GP_OK;
+}
+
+extern "C" gp_status gp_nn(gp_band* b, const float* q_dev, int64_t n, const int32_t* hint_dev, int32_t* nn_dev,
+                           float* rec_dev, int32_t* nvalid_dev) {
+  if (!b) return GP_ERR_ARG;
+  gp_ctx* ctx = b->ctx;
+  if (n < 0 || n >= (int64_t(1) << 31)) return gp_fail(ctx, GP_ERR_ARG, "gp_nn: n must be in [0, 2^31)");
+  if (nvalid_dev) GP_CUDA(ctx, cudaMemsetAsync(nvalid_dev, 0, sizeof(int32_t), ctx->stream));
+  if (n == 0) return GP_OK;
+  if (!q_dev || (!nn_dev && !rec_dev)) return gp_fail(ctx, GP_ERR_ARG, "gp_nn: null pointer");
+  return nn_launch(b, q_dev, n, hint_dev, nn_dev, rec_dev, nvalid_dev, nullptr);
+}
+
+extern "C" gp_status gp_nn_work(gp_band* b, const float* q_dev, int64_t n, const int32_t* hint_dev,
+                                int32_t* nn_dev, int64_t* work_host) {
+  if (!b) return GP_ERR_ARG;
+  gp_ctx* ctx = b->ctx;
+  if (n < 0 || n >= (int64_t(1) << 31)) return gp_fail(ctx, GP_ERR_ARG, "gp_nn_work: n must be in [0, 2^31)");
+  if (!work_host || !nn_dev || (n > 0 && !q_dev)) return gp_fail(ctx, GP_ERR_ARG, "gp_nn_work: null pointer");
+  *work_host = 0;
+  if (n == 0) return GP_OK;
+  unsigned long long* dev = nullptr;
+  gp_status st = gp_alloc(ctx, &dev, 1, "gp_nn_work counter");
+  if (st) return st;
+  cudaError_t e = cudaMemsetAsync(dev, 0, sizeof(unsigned long long), ctx->stream);
+  if (e == cudaSuccess) {
+    st = nn_launch(b, q_dev, n, hint_dev, nn_dev, nullptr, nullptr, dev);
+    unsigned long long h = 0;
+    if (!st) e = cudaMemcpyAsync(&h, dev, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream);
+    if (!st && e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    *work_host = (int64_t)h;
+  }
+  cudaFree(dev);
+  if (st) return st;
+  if (e != cudaSuccess) return gp_cuda_fail(ctx, e, "gp_nn_work");
   return GP_OK;
 }

@@ -267,13 +267,14 @@ __device__ __forceinline__ void nn_ball_walk(const float q[3], const int c[3], c
 // point within the margin by its float64 distance and index.  Rings 0..r_end
 // (or, for r_end < 0, the ball walk) cover every row within the pruning radius.
 __device__ __forceinline__ int nn_break_tie(const float q[3], const int c[3], const NNGrid& g, float margin,
-                                            const NNState& st, int r_end) {
+                                            const NNState& st, int r_end, int* work = nullptr) {
   const float tie = st.b1 * (1.0f + 2.0f * NN_EPS) + NN_TINY;
   if (st.b2 > tie) return st.j1;
   double bd = INFINITY;
   int bj = 0x7fffffff;
   const float thr = st.thr;
   auto rank = [&](int a, int b) {
+    if (work) *work += b > a ? b - a : 0;
     for (int p = a; p < b; ++p) {
       float4 P = g.pts[p];
       float dx = q[0] - P.x, dy = q[1] - P.y, dz = q[2] - P.z;
@@ -296,14 +297,16 @@ __device__ __forceinline__ int nn_break_tie(const float q[3], const int c[3], co
 
 // The whole search for one query by one thread, from whatever seed st holds.
 // Returns the nearest point's index, or -1 if none compares below +inf.
+// work (optional): incremented by the number of point distances evaluated.
 __device__ __forceinline__ int nn_thread_search(const float q[3], const int c[3], const NNGrid& g, float margin,
-                                                NNState& st) {
+                                                NNState& st, int* work = nullptr) {
   auto one = [&](float4 P) {
     float dx = q[0] - P.x, dy = q[1] - P.y, dz = q[2] - P.z;
     nn_update(st, dx * dx + dy * dy + dz * dz, __float_as_int(P.w));
   };
   // Points of a range, four loads in flight at a time (same visiting order).
   auto scan = [&](int a, int b) {
+    if (work) *work += b > a ? b - a : 0;
     int p = a;
     for (; p + 4 <= b; p += 4) {
       float4 P0 = __ldg(g.pts + p), P1 = __ldg(g.pts + p + 1), P2 = __ldg(g.pts + p + 2), P3 = __ldg(g.pts + p + 3);
@@ -320,7 +323,7 @@ __device__ __forceinline__ int nn_thread_search(const float q[3], const int c[3]
   else
     r_end = nn_ball_scan(q, c, g, margin, st.thr, st.b1, scan);
   if (st.j1 == 0x7fffffff) return -1;
-  return nn_break_tie(q, c, g, margin, st, r_end);
+  return nn_break_tie(q, c, g, margin, st, r_end, work);
 }
 
 __device__ __forceinline__ void nn_finish(int64_t i, const float q[3], int best, const float* __restrict__ pts_orig,
@@ -356,7 +359,8 @@ __device__ __forceinline__ bool nn_query_ok(const float q[3]) {
 // to lie near f, much closer to q than s is, which shrinks the ball to walk.
 __device__ __forceinline__ void nn_seed_foot(NNState& st, const float q[3], const int32_t* __restrict__ hint,
                                              int64_t i, int64_t J, const float* __restrict__ pts_orig,
-                                             const float* __restrict__ normals, const NNGrid& g) {
+                                             const float* __restrict__ normals, const NNGrid& g,
+                                             int* work = nullptr) {
   if (!hint || !normals) return;
   const int j = hint[i];
   if (j < 0 || j >= J) return;
@@ -366,6 +370,7 @@ __device__ __forceinline__ void nn_seed_foot(NNState& st, const float q[3], cons
   const int cx = nn_cell(q[0] - h * n0, g), cy = nn_cell(q[1] - h * n1, g), cz = nn_cell(q[2] - h * n2, g);
   const int64_t cell = ((int64_t)cz * g.G + cy) * g.G + cx;
   const int a = __ldg(g.start + cell), b = __ldg(g.start + cell + 1);
+  if (work) *work += b > a ? b - a : 0;
   for (int p = a; p < b; ++p) {
     float4 P = __ldg(g.pts + p);
     float dx = q[0] - P.x, dy = q[1] - P.y, dz = q[2] - P.z;

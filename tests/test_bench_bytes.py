@@ -28,7 +28,8 @@ def _launched(files):
 
 def test_every_step_kernel_has_algorithmic_bytes():
     launched = _launched(["gp_sample.cu", "gp_nn.cu", "gp_step.cu"])
-    setup = {"k_knn_sigma", "k_normals", "k_emit_pts"}  # band set-up, untimed
+    setup = {"k_knn_sigma", "k_normals", "k_emit_pts",   # band set-up, untimed
+             "k_nn_count", "k_nn_sorted_count"}           # gp_nn_work's counting launches, outside the step
     assert STEP_KERNELS <= launched
     for name in launched - setup - UNCOUNTED:
         assert bench.alg_bytes(name, 1000, 100, 512, 300) > 0, name
@@ -42,3 +43,26 @@ def test_byte_counts_are_the_arrays_touched_once():
     assert bench.alg_bytes("k_adam", n, J, Vs, Vt) == 28 * Vt               # D, g, m, v read; D, m, v written
     assert bench.alg_bytes("k_tv", n, J, Vs, Vt) == 8 * Vs                  # D read, grad written
     assert bench.alg_bytes("k_unknown", n, J, Vs, Vt) == 0
+
+
+def test_nn_roofline_is_fp32_candidate_arithmetic():
+    """The nearest-point kernels are rated against the FP32 pipe: 8 flops per
+    candidate distance (3 subtractions, 1 multiply, 2 FMAs at 2 flops each)
+    against SMs x 128 lanes x 2 flops x the maximum clock."""
+    assert bench.NN_FLOPS_PER_CANDIDATE == 8
+    peak, kind = bench.fp32_peak_tflops(152)
+    assert "derived" in kind
+    assert 70.0 < peak < 90.0      # 152 x 128 x 2 x ~2.07 GHz = 80.5 TFLOP/s
+
+
+def test_band_counts_match_the_oracle_sets():
+    """The dense-bitmap counts the CPU baseline extrapolates to equal the
+    oracle's band sets."""
+    import numpy as np
+    from oracle import gridpull as o
+    from paper_2308_13175_gb300 import synth
+    pts = synth.sphere_cloud(700, 0.4, seed=3)
+    for R, M1, M2 in ((32, 2, 2), (32, 1, 3), (16, 0, 0), (16, 2, -1)):
+        sets = o.band_sets(pts, R, M1, M2)
+        c = bench.band_counts(pts, R, M1, M2)
+        assert c["V_tv"] == len(sets["tv"]) and c["V_trainable"] == len(sets["trainable"]), (R, M1, M2)

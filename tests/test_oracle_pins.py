@@ -443,3 +443,46 @@ def test_oracle_matches_plain_torch_autograd(M):
         assert abs(float(parts[k]) - ref[k]) <= 1e-12 * max(1.0, abs(ref[k])), k
     g = Dt.grad.numpy()
     assert np.max(np.abs(g - ref["grad"])) <= 1e-11 * np.max(np.abs(ref["grad"]))
+
+
+# ------------------------------------------------ band-sparse value store
+def test_sparse_store_and_band_membership_equal_the_dense_forms():
+    """The band-sparse forms the large-config tests and the CPU baseline use
+    give bit-identical results to the dense forms: SparseValues over the
+    required vertices in place of the (R+1)^3 array, the per-cell dilation
+    test in place of the dilated cell set, and a TV subset with the full |T|
+    as divisor summing to the whole."""
+    R = 32
+    pts = synth.sphere_cloud(400, 0.45, seed=5)
+    sets = o.band_sets(pts, R, 2, 3)
+    rng = np.random.default_rng(5)
+    D = np.zeros((R + 1) ** 3)
+    req = sets["required"]
+    D[req] = np.linalg.norm(-1.0 + o.grid_spacing(R) * o.key_to_vertex(req, R), axis=1) - 0.45 \
+        + 0.02 * rng.normal(size=len(req))
+    all_cells = np.arange(R ** 3)
+    assert np.array_equal(o.in_dilated_band(all_cells, sets["occupied"], 2, R),
+                          np.isin(all_cells, sets["pull_cells"]))
+    assert np.array_equal(o.in_dilated_band(all_cells, sets["occupied"], 0, R),
+                          np.isin(all_cells, sets["occupied"]))
+    q, j = synth.gaussian_queries(pts, 3000, 0.05, seed=6)
+    w = (1.0, 1.0, 0.005)
+    dense = o.step_loss_grad(D, R, sets, q, pts[j], w)
+    sp = o.SparseValues(req[::-1], D[req[::-1]])
+    member = lambda c: o.in_dilated_band(c, sets["occupied"], 2, R)
+    sparse = o.step_loss_grad(sp, R, {"pull_cells": member, "tv": sets["tv"]}, q, pts[j], w)
+    for k in ("loss", "l_pull", "l_grad", "l_surf", "l_tv", "Bv"):
+        assert sparse[k] == dense[k], k
+    assert np.array_equal(sparse["grad"], dense["grad"][sp.keys])
+    assert np.array_equal(sparse["abs_terms"], dense["abs_terms"][sp.keys])
+    assert np.all(dense["grad"][np.setdiff1d(np.arange(len(D)), req)] == 0)
+    # A TV subset with the whole set's size as divisor: the two halves add up.
+    T = len(sets["tv"])
+    a, b = sets["tv"][: T // 3], sets["tv"][T // 3:]
+    la, ga, _ = o.tv_term(sp, R, a, n_tv=T)
+    lb, gbb, _ = o.tv_term(sp, R, b, n_tv=T)
+    assert abs(la + lb - dense["l_tv"]) <= 1e-14 * dense["l_tv"]
+    _, gfull, _ = o.tv_term(D, R, sets["tv"])
+    assert np.allclose(ga + gbb, gfull[sp.keys], rtol=0, atol=1e-15 * np.abs(gfull).max())
+    with pytest.raises(KeyError):
+        sp.index(np.array([np.setdiff1d(np.arange(len(D)), req)[0]]))
