@@ -90,6 +90,9 @@ SIGNATURES = {
     "gp_nn_work": (ctypes.c_int, [_vp, _vp, _i64, _vp, _vp, ctypes.POINTER(_i64)]),
     "gp_step": (ctypes.c_int, [_vp, _vp, _i64, _vp, _vp, ctypes.POINTER(LossW), _vp, _vp, _u32]),
     "gp_update": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(Adam), _i64]),
+    "gp_band_set_query_tiles": (ctypes.c_int, [_vp, _i32, _i32]),
+    "gp_band_autotune": (ctypes.c_int, [_vp, _vp, _i64, _vp, ctypes.POINTER(LossW), ctypes.POINTER(_i32),
+                                        ctypes.POINTER(_i32)]),
     "gp_multi_create": (ctypes.c_int, [_vp, ctypes.POINTER(_vp), _i32, ctypes.POINTER(_i64), ctypes.POINTER(_i64),
                                        _u64, _u32, ctypes.POINTER(_vp)]),
     "gp_multi_step": (ctypes.c_int, [_vp, ctypes.POINTER(LossW), ctypes.POINTER(Adam), _f, _i64, _vp]),
@@ -439,6 +442,24 @@ def gp_step(band: Band, rec, B: int, grad, loss, weights=(1.0, 1.0, 0.005), nval
     band.ctx.sync_stream()
     band.ctx.check(band.ctx.lib.gp_step(band.handle, _ptr(rec), int(B), _ptr(nvalid), _ptr(d), ctypes.byref(w),
                                         _ptr(grad), _ptr(loss), int(flags)))
+
+
+def gp_band_autotune(band: Band, rec, B: int, weights=(1.0, 1.0, 0.005), nvalid=None) -> dict:
+    """Times the fused step kernel's launch shapes on these records and keeps
+    the fastest in the band; returns {"records_per_tile", "blocks_per_sm"}."""
+    import torch
+    _need(rec, torch.float32, 6 * B, "records")
+    _need(nvalid, torch.int32, 1, "nvalid")
+    w = LossW(*[float(x) for x in weights])
+    rpt, bps = _i32(0), _i32(0)
+    band.ctx.sync_stream()
+    band.ctx.check(band.ctx.lib.gp_band_autotune(band.handle, _ptr(rec), int(B), _ptr(nvalid), ctypes.byref(w),
+                                                 ctypes.byref(rpt), ctypes.byref(bps)))
+    return {"records_per_tile": 256 * rpt.value, "blocks_per_sm": bps.value}
+
+
+def gp_band_set_query_tiles(band: Band, records_per_thread: int, blocks_per_sm: int):
+    band.ctx.check(band.ctx.lib.gp_band_set_query_tiles(band.handle, int(records_per_thread), int(blocks_per_sm)))
 
 
 def gp_update(band: Band, grad, lr: float, step: int, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8):

@@ -92,6 +92,11 @@ struct gp_band {
   uint64_t perm_seed = 0;
   uint32_t perm_epoch = 0;
 
+  // Launch shape of the tiled query kernel (records per thread of a tile,
+  // resident blocks per SM), set by gp_band_autotune.
+  int q_rpt = 2;
+  int q_bps = 3;
+
   // Scratch for reductions and counters.
   double* partials = nullptr;      // GP_MAX_PARTIAL_BLOCKS x 8
   int32_t* dev_ints = nullptr;     // GP_DI_COUNT

@@ -16,6 +16,7 @@
 // L_TV (Eq. 5): TV_i = sqrt(sum over in-grid axis neighbours (d_i - d_n)^2)
 // over the TV set T, averaged; its gradient is gathered per vertex,
 //   dTV/dd_i = [i in T] sum_n (d_i - d_n)/TV_i + sum_{n in T} (d_i - d_n)/TV_n.
+#include <algorithm>
 #include <cmath>
 
 #include "gp_internal.cuh"
@@ -145,6 +146,69 @@ __global__ void __launch_bounds__(Q_THREADS, Q_BLOCKS_PER_SM) k_query(Grid G, co
   }
   block_store3(partials, sp, sg, ss);
   if (LAST) finish_if_last(partials, fa);
+}
+
+// The fused forward + backward over tiles of QT_THREADS * RPT consecutive
+// records (a persistent grid strides over the tiles): each thread takes RPT
+// records of the tile, their 16 corner contributions are aggregated per quad
+// in the block's shared-memory table (TableSink) and the table is flushed
+// to the gradient once per tile.  DET: the table and the gradient sums are
+// the two-word fixed point, so the result does not depend on the order of
+// the additions.
+template <bool DET, bool LAST, int RPT>
+__global__ void __launch_bounds__(QT_THREADS, DET ? 2 : 3) k_query_tile(Grid G, const float* __restrict__ rec, int64_t B,
+                                                           const int32_t* __restrict__ bv, float beta, float gamma,
+                                                           float* __restrict__ grad,
+                                                           unsigned long long* __restrict__ acc,
+                                                           double* __restrict__ partials, int32_t* __restrict__ err,
+                                                           FinalArgs fa) {
+  extern __shared__ __align__(16) unsigned char qt_smem[];
+  float sp = 0.f, sg = 0.f, ss = 0.f;
+  const int bvv = *bv;
+  const float w = DET ? 1.0f : (bvv > 0 ? 1.0f / (float)bvv : 0.f);
+  constexpr int TILE = QT_THREADS * RPT;
+  const int64_t ntiles = (B + TILE - 1) / TILE;
+  auto run = [&](auto& sink) {
+    sink.init();
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+#pragma unroll
+      for (int r = 0; r < RPT; ++r) {
+        const int64_t i = tile * TILE + r * QT_THREADS + threadIdx.x;
+        if (i < B) {
+          float q[3], s[3];
+          load_rec(rec, i, q, s);
+          query_record_to<true>(G, q, s, w, beta, gamma, sink, err, sp, sg, ss);
+        }
+      }
+      sink.flush();
+    }
+  };
+  if constexpr (DET) {
+    TableSink<true> sink{G, acc, err, *reinterpret_cast<QTableD*>(qt_smem)};
+    run(sink);
+  } else {
+    TableSink<false> sink{G, grad, *reinterpret_cast<QTableF*>(qt_smem)};
+    run(sink);
+  }
+  block_store3(partials, sp, sg, ss);
+  if (LAST) finish_if_last(partials, fa);
+}
+
+template <bool DET, bool LAST, int RPT>
+cudaError_t launch_query_tile(unsigned grid, cudaStream_t s, Grid G, const float* rec, int64_t B, const int32_t* bv,
+                              float beta, float gamma, float* grad, unsigned long long* acc, double* partials,
+                              int32_t* err, FinalArgs fa) {
+  const size_t smem = DET ? sizeof(QTableD) : sizeof(QTableF);
+  static bool configured = false;  // per instantiation
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(k_query_tile<DET, LAST, RPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  k_query_tile<DET, LAST, RPT><<<grid, QT_THREADS, smem, s>>>(G, rec, B, bv, beta, gamma, grad, acc, partials, err,
+                                                              fa);
+  return cudaGetLastError();
 }
 
 // The L_TV sweep over the band's bricks (tv_sweep: one brick at a time per
@@ -317,18 +381,36 @@ extern "C" gp_status gp_step(gp_band* b, const float* rec_dev, int64_t B, const 
     GP_LAUNCH_CHECK(ctx, "k_tv");
     return GP_OK;
   };
+  // The tiled query kernel's grid: one resident wave (blocks per SM as tuned,
+  // at most 3 - the register cap of the float table's kernel - and 2 for the
+  // fixed-point table's).
+  const int rpt = det ? 1 : b->q_rpt;
+  const int bps = det ? std::min(b->q_bps, 2) : std::min(b->q_bps, 3);
+  const int64_t qtiles = (B + (int64_t)QT_THREADS * rpt - 1) / ((int64_t)QT_THREADS * rpt);
+  const unsigned qtb = (unsigned)std::max<int64_t>(1, std::min<int64_t>(qtiles, (int64_t)ctx->num_sms * bps));
+  if (grad_on) fa.q_blocks = (int)qtb;
   auto launch_q = [&]() -> gp_status {
     gp_prof_pre(ctx);
-    if (det && grad_on)
-      k_query<true, true, false><<<qb, Q_THREADS, 0, s>>>(G, rec_dev, B, bv, w->beta, w->gamma, grad_dev, b->acc,
-                                                          b->partials, err, fa);
-    else if (grad_on)
-      k_query<false, true, true><<<qb, Q_THREADS, 0, s>>>(G, rec_dev, B, bv, w->beta, w->gamma, grad_dev, b->acc,
-                                                          b->partials, err, fa);
-    else
+    cudaError_t e = cudaSuccess;
+    if (det && grad_on) {
+      e = launch_query_tile<true, false, 1>(qtb, s, G, rec_dev, B, bv, w->beta, w->gamma, grad_dev, b->acc,
+                                            b->partials, err, fa);
+    } else if (grad_on) {
+      if (rpt == 1)
+        e = launch_query_tile<false, true, 1>(qtb, s, G, rec_dev, B, bv, w->beta, w->gamma, grad_dev, b->acc,
+                                              b->partials, err, fa);
+      else if (rpt == 4)
+        e = launch_query_tile<false, true, 4>(qtb, s, G, rec_dev, B, bv, w->beta, w->gamma, grad_dev, b->acc,
+                                              b->partials, err, fa);
+      else
+        e = launch_query_tile<false, true, 2>(qtb, s, G, rec_dev, B, bv, w->beta, w->gamma, grad_dev, b->acc,
+                                              b->partials, err, fa);
+    } else {
       k_query<false, false, true><<<qb, Q_THREADS, 0, s>>>(G, rec_dev, B, bv, w->beta, w->gamma, grad_dev, b->acc,
                                                            b->partials, err, fa);
+    }
     gp_prof_post(ctx, "k_query");
+    if (e != cudaSuccess) return gp_cuda_fail(ctx, e, "k_query");
     GP_LAUNCH_CHECK(ctx, "k_query");
     return GP_OK;
   };
@@ -356,5 +438,113 @@ extern "C" gp_status gp_update(gp_band* b, const float* grad_dev, const gp_adam*
   GP_KERNEL(ctx, "k_adam", k_adam<<<gp_blocks(b->n_active * 128, 256, cap), 256, 0, ctx->stream>>>(b->active, b->n_active, b->masks, grad_dev, b->D,
                                                                   b->m, b->v, hp->lr, hp->beta1, hp->beta2, hp->eps,
                                                                   (float)bc1, (float)bc2));
+  return GP_OK;
+}
+
+// Times the tiled query kernel's launch shapes on the given records and keeps
+// the fastest in the band: records per thread of a tile (1, 2, 4: tiles of
+// 256, 512 or 1024 records) and resident blocks per SM (2 or 3).  The band's
+// values are read, nothing of the band is written; a scratch gradient and
+// loss are allocated and freed.
+extern "C" gp_status gp_band_autotune(gp_band* b, const float* rec_dev, int64_t B, const int32_t* nvalid_dev,
+                                      const gp_loss_w* w, int32_t* rpt_out, int32_t* bps_out) {
+  if (!b) return GP_ERR_ARG;
+  gp_ctx* ctx = b->ctx;
+  if (B <= 0 || B >= (int64_t(1) << 31) || !rec_dev || !w)
+    return gp_fail(ctx, GP_ERR_ARG, "gp_band_autotune: need 0 < B < 2^31 records and weights");
+  if (((uintptr_t)rec_dev & 7u) != 0) return gp_fail(ctx, GP_ERR_ARG, "gp_band_autotune: records must be 8-byte aligned");
+  cudaStream_t s = ctx->stream;
+  float* grad = nullptr;
+  float* loss = nullptr;
+  gp_status st = gp_alloc(ctx, &grad, b->V_stored(), "autotune gradient");
+  if (st) return st;
+  if ((st = gp_alloc(ctx, &loss, 8, "autotune loss"))) {
+    cudaFree(grad);
+    return st;
+  }
+  Grid G;
+  G.table = b->brick_table;
+  G.masks = b->masks;
+  G.D = b->D;
+  G.nb = b->nb;
+  G.R = b->R;
+  G.half_r = 0.5f * (float)b->R;
+  int32_t* err = b->dev_ints + GP_DI_ERROR;
+  const int32_t* bv = nvalid_dev;
+  cudaError_t e = cudaSuccess;
+  if (!bv) {
+    int32_t* cnt = b->dev_ints + GP_DI_NVALID;
+    e = cudaMemsetAsync(cnt, 0, sizeof(int32_t), s);
+    if (e == cudaSuccess) {
+      k_count_valid<<<q_grid(ctx, B), Q_THREADS, 0, s>>>(G, rec_dev, B, cnt);
+      e = cudaGetLastError();
+    }
+    bv = cnt;
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  int best_rpt = b->q_rpt, best_bps = b->q_bps;
+  float best = INFINITY;
+  const int rpts[3] = {1, 2, 4}, bpss[2] = {2, 3};
+  for (int ri = 0; ri < 3 && e == cudaSuccess; ++ri) {
+    for (int bi = 0; bi < 2 && e == cudaSuccess; ++bi) {
+      const int rpt = rpts[ri], bps = bpss[bi];
+      const int64_t tiles = (B + (int64_t)QT_THREADS * rpt - 1) / ((int64_t)QT_THREADS * rpt);
+      const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)ctx->num_sms * bps));
+      FinalArgs fa;
+      fa.done = b->dev_ints + GP_DI_DONE;
+      fa.q_blocks = (int)grid;
+      fa.tv_blocks = 0;
+      fa.bv = bv;
+      fa.n_tv = b->V_tv;
+      fa.alpha = w->alpha;
+      fa.beta = w->beta;
+      fa.gamma = w->gamma;
+      fa.tv_on = 0;
+      fa.loss = loss;
+      auto launch = [&]() -> cudaError_t {
+        if (rpt == 1)
+          return launch_query_tile<false, true, 1>(grid, s, G, rec_dev, B, bv, w->beta, w->gamma, grad, nullptr,
+                                                   b->partials, err, fa);
+        if (rpt == 2)
+          return launch_query_tile<false, true, 2>(grid, s, G, rec_dev, B, bv, w->beta, w->gamma, grad, nullptr,
+                                                   b->partials, err, fa);
+        return launch_query_tile<false, true, 4>(grid, s, G, rec_dev, B, bv, w->beta, w->gamma, grad, nullptr,
+                                                 b->partials, err, fa);
+      };
+      e = launch();  // warm-up
+      if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+      for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = launch();
+      if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e == cudaSuccess && ms < best) {
+        best = ms;
+        best_rpt = rpt;
+        best_bps = bps;
+      }
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaStreamSynchronize(s);
+  cudaFree(grad);
+  cudaFree(loss);
+  if (e != cudaSuccess) return gp_cuda_fail(ctx, e, "gp_band_autotune");
+  b->q_rpt = best_rpt;
+  b->q_bps = best_bps;
+  if (rpt_out) *rpt_out = best_rpt;
+  if (bps_out) *bps_out = best_bps;
+  return GP_OK;
+}
+
+extern "C" gp_status gp_band_set_query_tiles(gp_band* b, int32_t rpt, int32_t bps) {
+  if (!b) return GP_ERR_ARG;
+  if (!(rpt == 1 || rpt == 2 || rpt == 4) || bps < 1 || bps > 3)
+    return gp_fail(b->ctx, GP_ERR_ARG, "gp_band_set_query_tiles: rpt must be 1, 2 or 4 and bps in [1, 3]");
+  b->q_rpt = rpt;
+  b->q_bps = bps;
   return GP_OK;
 }

@@ -7,11 +7,12 @@
 #include "gp_internal.cuh"
 
 constexpr float NORM_FLOOR = 1e-12f;
-// Deterministic sums: each contribution v is split into two integers,
-// hi = round(v * 2^20) and lo = round((v - hi * 2^-20) * 2^60), accumulated
-// with 64-bit integer atomics (exact, so the order of the additions does not
-// matter).  The sum is hi * 2^-20 + lo * 2^-60: a resolution of 2^-60, no
-// overflow below 2^42 per contribution and 2^23 contributions per vertex.
+// Deterministic sums: each contribution v is split into two integers, hi in
+// units of 2^-20 and lo in units of 2^-60 (fix_split), accumulated with 64-bit
+// integer atomics (exact, so the order of the additions does not matter).
+// The sum is hi * 2^-20 + lo * 2^-60: a resolution of 2^-60; a contribution
+// of magnitude 2^42 (FIX_LIMIT) or more, or a non-finite one, raises
+// GP_EF_NUMERIC instead.
 constexpr double FIX_HI = 1048576.0;                     // 2^20
 constexpr double FIX_LO = 1152921504606846976.0;         // 2^60
 constexpr double FIX_LIMIT = 4398046511104.0;            // 2^42
@@ -21,11 +22,33 @@ struct Eval {
   float gt[3];  // df/dt (t = local coordinate in cell units)
 };
 
+// The 8 corner values of cell c (corner k = dx + 2 dy + 4 dz).  Inside a
+// brick the two corners (x, x + 1) of each of the cell's four x edges are
+// adjacent floats: one 8-byte load per edge at even x, one aligned 16-byte
+// load from x - 1 at x = 1 mod 4, two 4-byte loads at x = 3 mod 4.  A cell
+// whose corners span bricks looks each corner's brick up.
 __device__ __forceinline__ void load_corners(const Grid& G, const int c[3], int slot, float d[8], bool& ok) {
   if ((c[0] & 7) != 7 && (c[1] & 7) != 7 && (c[2] & 7) != 7) {
     const float* base = G.D + gp_vaddr(slot, c[0], c[1], c[2]);
+    const int xm = c[0] & 3;
+    if ((xm & 1) == 0) {
 #pragma unroll
-    for (int k = 0; k < 8; ++k) d[k] = __ldg(base + (k & 1) + ((k >> 1) & 1) * 8 + (k >> 2) * 64);
+      for (int e = 0; e < 4; ++e) {
+        const float2 v = __ldg(reinterpret_cast<const float2*>(base + (e & 1) * 8 + (e >> 1) * 64));
+        d[2 * e] = v.x;
+        d[2 * e + 1] = v.y;
+      }
+    } else if (xm == 1) {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float4 v = __ldg(reinterpret_cast<const float4*>(base - 1 + (e & 1) * 8 + (e >> 1) * 64));
+        d[2 * e] = v.y;
+        d[2 * e + 1] = v.z;
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) d[k] = __ldg(base + (k & 1) + ((k >> 1) & 1) * 8 + (k >> 2) * 64);
+    }
     return;
   }
 #pragma unroll
@@ -75,6 +98,44 @@ __device__ __forceinline__ void red_add_v4(float* addr, float a, float b, float 
                : "memory");
 }
 
+// Deterministic sums: each contribution v is taken exactly (to 2^-60) into
+// two integers, hi in units of 2^-20 and lo in units of 2^-60 with
+// hi 2^40 + lo = v 2^60 rounded toward zero below 2^-60, by integer
+// arithmetic on v's bits.  Integer sums do not depend on the order of the
+// additions.  Returns false for a non-finite v or |v| >= 2^42 (FIX_LIMIT).
+__device__ __forceinline__ bool fix_split(float v, long long& hi, long long& lo) {
+  const uint32_t u = __float_as_uint(v);
+  const int ex = (int)((u >> 23) & 0xffu);
+  if (ex == 0xff) return false;
+  long long m = (long long)(u & 0x7fffffu);
+  int e;
+  if (ex == 0) {
+    e = -149;
+  } else {
+    m |= 0x800000ll;
+    e = ex - 150;
+  }
+  hi = 0;
+  lo = 0;
+  if (m == 0) return true;
+  const int sh = e + 60;  // v 2^60 = m 2^sh
+  if (sh >= 82) return false;  // |v| >= 2^42
+  if (sh >= 40) {
+    hi = m << (sh - 40);
+  } else if (sh >= 0) {
+    const long long val = m << sh;  // < 2^63
+    hi = val >> 40;
+    lo = val & ((1ll << 40) - 1);
+  } else if (sh > -64) {
+    lo = m >> (-sh);
+  }
+  if (u >> 31) {
+    hi = -hi;
+    lo = -lo;
+  }
+  return true;
+}
+
 // Scatter of one cell's 8 corner contributions.
 template <bool DET>
 __device__ __forceinline__ void scatter8(const Grid& G, float* __restrict__ grad, unsigned long long* __restrict__ acc,
@@ -122,21 +183,243 @@ __device__ __forceinline__ void scatter8(const Grid& G, float* __restrict__ grad
       addr = gp_vaddr(s, i, j, kk);
     }
     if (DET) {
-      double x = (double)val;
-      if (!(fabs(x) < FIX_LIMIT)) {
+      long long hi, lo;
+      if (!fix_split(val, hi, lo)) {
         atomicOr(err, GP_EF_NUMERIC);
         continue;
       }
-      double hi = rint(x * FIX_HI);
-      double lo = rint((x - hi / FIX_HI) * FIX_LO);
-      atomicAdd(acc + 2 * addr, (unsigned long long)(long long)hi);
-      atomicAdd(acc + 2 * addr + 1, (unsigned long long)(long long)lo);
+      if (hi) atomicAdd(acc + 2 * addr, (unsigned long long)hi);
+      if (lo) atomicAdd(acc + 2 * addr + 1, (unsigned long long)lo);
     } else {
       atomicAdd(grad + addr, val);
     }
   }
 }
 
+
+// dL/dd_c of the cell's corner c = dx + 2 dy + 4 dz from dL/df = A and
+// dL/dt = Gt at local coordinate t: A w_c(t) + sum_a Gt_a dw_c/dt_a.
+__device__ __forceinline__ void corner_values(const float t[3], float A, const float Gt[3], float v[8]) {
+  const float wx[2] = {1.f - t[0], t[0]}, wy[2] = {1.f - t[1], t[1]}, wz[2] = {1.f - t[2], t[2]};
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int dx = k & 1, dy = (k >> 1) & 1, dz = k >> 2;
+    const float sx = dx ? 1.f : -1.f, sy = dy ? 1.f : -1.f, sz = dz ? 1.f : -1.f;
+    const float wyz = wy[dy] * wz[dz];
+    v[k] = A * wx[dx] * wyz + Gt[0] * sx * wyz + Gt[1] * wx[dx] * sy * wz[dz] + Gt[2] * wx[dx] * wy[dy] * sz;
+  }
+}
+
+// Where a record's corner contributions go: straight to the gradient with
+// global reductions (float atomics, or the two-word fixed point).
+template <bool DET>
+struct GlobalSink {
+  const Grid& G;
+  float* __restrict__ grad;
+  unsigned long long* __restrict__ acc;
+  int32_t* __restrict__ err;
+  __device__ __forceinline__ void cell(const int c[3], int slot, const float t[3], float A, const float Gt[3]) {
+    scatter8<DET>(G, grad, acc, err, c, slot, t, A, Gt);
+  }
+};
+
+// Block-level aggregation of the corner contributions of a tile of records
+// in a shared-memory hash table whose entries are quads: the 4 consecutive
+// vertices 4n .. 4n + 3 of a brick row (key n = vertex address / 4).  A
+// record's 16 contributions become shared-memory atomics on about 8 quads;
+// when the tile is done every quad used is added to the gradient with one
+// 16-byte vector reduction (float) or up to 8 integer atomics (fixed point)
+// and reset.  Records of a spatially ordered batch share most quads, so the
+// global reductions drop by the sharing factor.  An insertion that finds no
+// free entry within QT_PROBES probes goes straight to the gradient.
+constexpr uint32_t QT_EMPTY = 0xffffffffu;
+constexpr int QT_PROBES = 16;
+constexpr int QT_BITS_F = 11;  // float table: 2048 quads
+constexpr int QT_BITS_D = 10;  // fixed-point table: 1024 quads
+constexpr int QT_THREADS = 256;
+
+struct QTableF {
+  float4 val[1 << QT_BITS_F];
+  uint32_t key[1 << QT_BITS_F];
+  uint16_t used[1 << QT_BITS_F];
+  int n_used;
+};
+struct QTableD {
+  unsigned long long hi[1 << QT_BITS_D][4];
+  unsigned long long lo[1 << QT_BITS_D][4];
+  uint32_t key[1 << QT_BITS_D];
+  uint16_t used[1 << QT_BITS_D];
+  int n_used;
+};
+
+template <int BITS>
+__device__ __forceinline__ int qt_find(uint32_t* keys, uint16_t* used, int* n_used, uint32_t key) {
+  uint32_t h = (key * 2654435761u) >> (32 - BITS);
+#pragma unroll 1
+  for (int p = 0; p < QT_PROBES; ++p) {
+    const uint32_t k = *(volatile uint32_t*)&keys[h];
+    if (k == key) return (int)h;
+    if (k == QT_EMPTY) {
+      const uint32_t old = atomicCAS(&keys[h], QT_EMPTY, key);
+      if (old == QT_EMPTY) {
+        used[atomicAdd(n_used, 1)] = (uint16_t)h;
+        return (int)h;
+      }
+      if (old == key) return (int)h;
+    }
+    h = (h + 1) & ((1u << BITS) - 1u);
+  }
+  return -1;
+}
+
+template <bool DET>
+struct TableSink;
+
+template <>
+struct TableSink<false> {
+  const Grid& G;
+  float* __restrict__ grad;
+  QTableF& T;
+  __device__ __forceinline__ void add(uint32_t addr, float v) {
+    const int h = qt_find<QT_BITS_F>(T.key, T.used, &T.n_used, addr >> 2);
+    if (h >= 0)
+      atomicAdd(reinterpret_cast<float*>(&T.val[h]) + (addr & 3u), v);
+    else
+      atomicAdd(grad + addr, v);
+  }
+  __device__ __forceinline__ void add2(uint32_t addr, float v0, float v1) {  // addr & 3 != 3
+    const int h = qt_find<QT_BITS_F>(T.key, T.used, &T.n_used, addr >> 2);
+    if (h >= 0) {
+      float* e = reinterpret_cast<float*>(&T.val[h]) + (addr & 3u);
+      atomicAdd(e, v0);
+      atomicAdd(e + 1, v1);
+    } else {
+      atomicAdd(grad + addr, v0);
+      atomicAdd(grad + addr + 1, v1);
+    }
+  }
+  __device__ __forceinline__ void cell(const int c[3], int slot, const float t[3], float A, const float Gt[3]) {
+    float v[8];
+    corner_values(t, A, Gt, v);
+    if ((c[0] & 7) != 7 && (c[1] & 7) != 7 && (c[2] & 7) != 7) {
+      const uint32_t base = (uint32_t)gp_vaddr(slot, c[0], c[1], c[2]);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const uint32_t a = base + (e & 1) * 8 + (e >> 1) * 64;
+        if ((a & 3u) != 3u) {
+          add2(a, v[2 * e], v[2 * e + 1]);
+        } else {
+          add(a, v[2 * e]);
+          add(a + 1, v[2 * e + 1]);
+        }
+      }
+      return;
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int i = c[0] + (k & 1), j = c[1] + ((k >> 1) & 1), kk = c[2] + (k >> 2);
+      const int sl = gp_brick_slot(G.table, G.nb, i, j, kk);
+      if (sl >= 0) add((uint32_t)gp_vaddr(sl, i, j, kk), v[k]);
+    }
+  }
+  // Add every quad of the tile to the gradient and reset the table; called
+  // by the whole block after the tile's inserts (synchronises).
+  __device__ __forceinline__ void flush() {
+    __syncthreads();
+    const int n = T.n_used;
+    __syncthreads();
+    if (threadIdx.x == 0) T.n_used = 0;
+    for (int u = threadIdx.x; u < n; u += blockDim.x) {
+      const int h = T.used[u];
+      const float4 q = T.val[h];
+      red_add_v4(grad + 4 * (size_t)T.key[h], q.x, q.y, q.z, q.w);
+      T.key[h] = QT_EMPTY;
+      T.val[h] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    __syncthreads();
+  }
+  __device__ __forceinline__ void init() {
+    for (int h = threadIdx.x; h < (1 << QT_BITS_F); h += blockDim.x) {
+      T.key[h] = QT_EMPTY;
+      T.val[h] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    if (threadIdx.x == 0) T.n_used = 0;
+    __syncthreads();
+  }
+};
+
+template <>
+struct TableSink<true> {
+  const Grid& G;
+  unsigned long long* __restrict__ acc;
+  int32_t* __restrict__ err;
+  QTableD& T;
+  __device__ __forceinline__ void add(uint32_t addr, float v) {
+    long long hi, lo;
+    if (!fix_split(v, hi, lo)) {
+      atomicOr(err, GP_EF_NUMERIC);
+      return;
+    }
+    if (!hi && !lo) return;
+    const int h = qt_find<QT_BITS_D>(T.key, T.used, &T.n_used, addr >> 2);
+    if (h >= 0) {
+      if (hi) atomicAdd(&T.hi[h][addr & 3u], (unsigned long long)hi);
+      if (lo) atomicAdd(&T.lo[h][addr & 3u], (unsigned long long)lo);
+    } else {
+      if (hi) atomicAdd(acc + 2 * (size_t)addr, (unsigned long long)hi);
+      if (lo) atomicAdd(acc + 2 * (size_t)addr + 1, (unsigned long long)lo);
+    }
+  }
+  __device__ __forceinline__ void cell(const int c[3], int slot, const float t[3], float A, const float Gt[3]) {
+    float v[8];
+    corner_values(t, A, Gt, v);
+    if ((c[0] & 7) != 7 && (c[1] & 7) != 7 && (c[2] & 7) != 7) {
+      const uint32_t base = (uint32_t)gp_vaddr(slot, c[0], c[1], c[2]);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) add(base + (k & 1) + ((k >> 1) & 1) * 8 + (k >> 2) * 64, v[k]);
+      return;
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int i = c[0] + (k & 1), j = c[1] + ((k >> 1) & 1), kk = c[2] + (k >> 2);
+      const int sl = gp_brick_slot(G.table, G.nb, i, j, kk);
+      if (sl >= 0) add((uint32_t)gp_vaddr(sl, i, j, kk), v[k]);
+    }
+  }
+  __device__ __forceinline__ void flush() {
+    __syncthreads();
+    const int n = T.n_used;
+    __syncthreads();
+    if (threadIdx.x == 0) T.n_used = 0;
+    for (int u = threadIdx.x; u < 4 * n; u += blockDim.x) {
+      const int h = T.used[u >> 2], l = u & 3;
+      const unsigned long long hi = T.hi[h][l], lo = T.lo[h][l];
+      const size_t addr = 4 * (size_t)T.key[h] + l;
+      if (hi) atomicAdd(acc + 2 * addr, hi);
+      if (lo) atomicAdd(acc + 2 * addr + 1, lo);
+    }
+    __syncthreads();
+    for (int u = threadIdx.x; u < 4 * n; u += blockDim.x) {
+      const int h = T.used[u >> 2], l = u & 3;
+      T.hi[h][l] = 0ull;
+      T.lo[h][l] = 0ull;
+      if (l == 0) T.key[h] = QT_EMPTY;
+    }
+    __syncthreads();
+  }
+  __device__ __forceinline__ void init() {
+    for (int h = threadIdx.x; h < (1 << QT_BITS_D); h += blockDim.x) {
+      T.key[h] = QT_EMPTY;
+#pragma unroll
+      for (int l = 0; l < 4; ++l) {
+        T.hi[h][l] = 0ull;
+        T.lo[h][l] = 0ull;
+      }
+    }
+    if (threadIdx.x == 0) T.n_used = 0;
+    __syncthreads();
+  }
+};
 
 // One step record: classify it, evaluate Eq. 3 at q and at s, add its loss
 // terms to sp / sg / ss and (GRAD) scatter its gradient to the 8 + 8 corners,
@@ -146,11 +429,10 @@ __device__ __forceinline__ void scatter8(const Grid& G, float* __restrict__ grad
 // for latency: both brick slots are read together, then both pull-mask words
 // and all 16 corner values together (the corners of a record that turns out
 // invalid are read for nothing).
-template <bool DET, bool GRAD>
-__device__ __forceinline__ bool query_record(const Grid& G, const float q[3], const float s[3], float w, float beta,
-                                             float gamma, float* __restrict__ grad,
-                                             unsigned long long* __restrict__ acc, int32_t* __restrict__ err,
-                                             float& sp, float& sg, float& ss) {
+template <bool GRAD, class Sink>
+__device__ __forceinline__ bool query_record_to(const Grid& G, const float q[3], const float s[3], float w,
+                                                float beta, float gamma, Sink& sink, int32_t* __restrict__ err,
+                                                float& sp, float& sg, float& ss) {
   Cells C;
   if (!classify_cells(G, q, s, C)) return false;
   C.slot_q = gp_brick_slot(G.table, G.nb, C.cq[0], C.cq[1], C.cq[2]);
@@ -207,10 +489,21 @@ __device__ __forceinline__ bool query_record(const Grid& G, const float q[3], co
     Gs[a] = dgs * G.half_r;
   }
   float dfs = fs > 0.f ? w * beta : (fs < 0.f ? -w * beta : 0.f);
-  scatter8<DET>(G, grad, acc, err, C.cq, C.slot_q, C.tq, dfq, Gq);
-  scatter8<DET>(G, grad, acc, err, C.cs, C.slot_s, C.ts, dfs, Gs);
+  sink.cell(C.cq, C.slot_q, C.tq, dfq, Gq);
+  sink.cell(C.cs, C.slot_s, C.ts, dfs, Gs);
   return true;
 }
+
+// The record with its contributions reduced straight into the gradient.
+template <bool DET, bool GRAD>
+__device__ __forceinline__ bool query_record(const Grid& G, const float q[3], const float s[3], float w, float beta,
+                                             float gamma, float* __restrict__ grad,
+                                             unsigned long long* __restrict__ acc, int32_t* __restrict__ err,
+                                             float& sp, float& sg, float& ss) {
+  GlobalSink<DET> sink{G, grad, acc, err};
+  return query_record_to<GRAD>(G, q, s, w, beta, gamma, sink, err, sp, sg, ss);
+}
+
 constexpr int HS = 12;            // staged edge: brick (8) + 2 on each side
 constexpr int HN = HS * HS * HS;  // 1728
 constexpr int IS = 10;            // TV edge: brick + 1 on each side

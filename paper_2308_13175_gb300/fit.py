@@ -46,6 +46,16 @@ class FitStep:
             return self.lr * self.lr_decay ** (t // self.lr_every)
         return self.lr
 
+    def autotune(self, t: int = 0) -> dict:
+        """Draws step t's batch and its nearest points and lets gp_band_autotune
+        choose the fused step kernel's tile size and blocks per SM on it
+        (set-up: call before timing or graph capture).  Returns the choice."""
+        band = self.band
+        epoch, first, count = self.batch_of(t)
+        gb.gp_sample(band, self.seed, epoch, self.Q, first, count, self.q, self.src, spatial=True)
+        gb.gp_nn(band, self.q[:count], None, self.rec, hint=self.src[:count], nvalid_out=self.nvalid)
+        return gb.gp_band_autotune(band, self.rec, count, self.weights, nvalid=self.nvalid)
+
     def run(self, t: int):
         """Step t (0-based); returns the loss buffer (device, 8 floats)."""
         band = self.band

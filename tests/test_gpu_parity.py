@@ -477,6 +477,85 @@ def test_step_deterministic_is_bitwise_repeatable(gb, ctx, object100k):
     assert ref["Bv"] > 90_000
 
 
+def _spatial_order(q, R):
+    """Records sorted by the cell key of q (neighbouring records share cells,
+    as in the sampler's spatial batches)."""
+    cq = np.clip(np.floor((q.astype(np.float64) + 1) * R / 2).astype(np.int64), 0, R - 1)
+    return np.argsort(cq[:, 0] + R * (cq[:, 1] + R * cq[:, 2]), kind="stable")
+
+
+@pytest.mark.parametrize("rpt,bps", [(1, 2), (2, 3), (4, 3), (4, 1)])
+def test_step_tile_shapes_match_oracle(gb, ctx, object100k, rpt, bps):
+    """The fused step kernel's shared-memory aggregation at every launch shape
+    the autotuner can pick, on spatially ordered records (heavy sharing of
+    corners within a tile) and on records in random order (tiles of 1024
+    records touch more distinct quads than the table holds, so insertions
+    overflow to direct reductions)."""
+    R = 256
+    band = _band(gb, ctx, object100k, R, 2, 2, knn_k=0)
+    c = 0.5 * (object100k.min(0) + object100k.max(0))
+    sets, q, s = _step_inputs(object100k, R, 2, 2, 60_000, 2.0 / R, seed=11, use_nn=False)
+    D, _ = _set_field(gb, band, sets, R, 0.3, 2e-3, seed=12, center=c)
+    gb.gp_band_set_query_tiles(band, rpt, bps)
+    order = _spatial_order(q, R)
+    _check_step(gb, band, R, sets, q[order], s[order], (1.0, 1.0, 0.005), D)
+    _check_step(gb, band, R, sets, q, s, (2.0, 0.5, 0.3), D)
+
+
+def test_step_records_in_one_cell(gb, ctx, sphere5k):
+    """Thousands of records whose q and NN(q) share one cell: every
+    contribution of a tile lands on the same 8 vertices."""
+    R = 64
+    band = _band(gb, ctx, sphere5k, R, 2, 2, knn_k=0)
+    sets = o.band_sets(sphere5k, R, 2, 2)
+    D, _ = _set_field(gb, band, sets, R, 0.5, 0.05, seed=21)
+    h = 2.0 / R
+    p0 = sphere5k[0].astype(np.float64)
+    cell = np.floor((p0 + 1) / h)
+    rng = np.random.default_rng(22)
+    q = (-1 + h * (cell + rng.uniform(0.05, 0.95, size=(6000, 3)))).astype(np.float32)
+    s = np.repeat(sphere5k[:1], len(q), axis=0)
+    ref = _check_step(gb, band, R, sets, q, s, (1.0, 1.0, 0.005), D)
+    assert ref["Bv"] > 5000
+    gb.gp_band_set_query_tiles(band, 4, 3)
+    _check_step(gb, band, R, sets, q, s, (1.0, 1.0, 0.005), D)
+
+
+def test_step_deterministic_overflow_raises_numeric(gb, ctx, sphere5k):
+    """A constant field has grad f = 0, so the normal is taken against the
+    1e-12 floor and a record's corner contributions reach ~1e13, beyond the
+    fixed-point sums' limit of 2^42: the step raises GP_ERR_NUMERIC (read by
+    gp_band_check) instead of wrapping around."""
+    import torch
+    R = 64
+    band = _band(gb, ctx, sphere5k, R, -1, -1, knn_k=0, deterministic=True)
+    gb.gp_band_set_values(band, torch.ones(band.V_stored, dtype=torch.float32, device="cuda"))
+    q = (sphere5k[:64] * 1.01).astype(np.float32)
+    gb.gp_band_check(band)  # clean before the step
+    _run_step(gb, band, q, sphere5k[:64], (1.0, 1.0, 0.005), gb.GP_STEP_DETERMINISTIC)
+    with pytest.raises(gb.GridPullError, match="GP_ERR_NUMERIC|numeric"):
+        gb.gp_band_check(band)
+    gb.gp_band_check(band)  # the flag was cleared by the read
+
+
+def test_autotune_picks_a_shape_and_leaves_the_band(gb, ctx, object100k):
+    import torch
+    R = 256
+    band = _band(gb, ctx, object100k, R, 2, 2, knn_k=0)
+    sets, q, s = _step_inputs(object100k, R, 2, 2, 50_000, 2.0 / R, seed=13, use_nn=False)
+    c = 0.5 * (object100k.min(0) + object100k.max(0))
+    D, vals = _set_field(gb, band, sets, R, 0.3, 2e-3, seed=14, center=c)
+    order = _spatial_order(q, R)
+    rec = torch.from_numpy(np.ascontiguousarray(np.concatenate([q[order], s[order]], axis=1), np.float32)).cuda()
+    before = gb.gp_band_values(band)[0].clone()
+    tune = gb.gp_band_autotune(band, rec, len(q))
+    assert tune["records_per_tile"] in (256, 512, 1024) and tune["blocks_per_sm"] in (2, 3)
+    assert torch.equal(before, gb.gp_band_values(band)[0])
+    _check_step(gb, band, R, sets, q[order], s[order], (1.0, 1.0, 0.005), D)
+    with pytest.raises(gb.GridPullError):
+        gb.gp_band_set_query_tiles(band, 3, 2)
+
+
 def test_step_rejects_misaligned_buffers(gb, ctx, sphere5k):
     import torch
     band = _band(gb, ctx, sphere5k, 32, 1, 1, knn_k=0)
