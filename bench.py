@@ -756,7 +756,7 @@ def run_ours(args, world, rank, local):
                           "V_stored": Vs, "V_trainable": Vt, "V_tv": info["V_tv"], "J": J,
                           "gradient_sum": "deterministic two-word fixed point" if args.deterministic
                           else "float atomics",
-                          "query_tiles": tuned if not args.deterministic else {"records_per_tile": 256},
+                          "query_tiles": tuned,
                           "brick": 8},
                "roofline": roofline, "cpu_baseline": cpu,
                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 16 * B, "d2h_bytes_per_step": 32,

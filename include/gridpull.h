@@ -278,24 +278,23 @@ gp_status gp_step(gp_band* band, const float* rec_dev, int64_t B, const int32_t*
                   const float* d_dev, const gp_loss_w* w, float* grad_dev, float* loss_dev,
                   uint32_t flags);
 
-/* Chooses the launch shape of gp_step's fused forward + backward kernel, which
- * aggregates the corner contributions of a tile of consecutive records in a
- * shared-memory table before adding them to the gradient: the records per
- * tile (256, 512 or 1024; *rpt_out = 1, 2 or 4 records per thread) and the
- * resident blocks per SM (*bps_out = 2 or 3), by timing each candidate with
+/* Chooses the launch shape of gp_step's fused forward + backward kernel: the
+ * records each thread keeps in flight (*rpt_out = 1 or 2; with 2, both
+ * records' gathers of one level are issued before either is waited for) and
+ * the resident blocks per SM it is compiled for (*bps_out = 2, 3 or 4, i.e. a
+ * cap of 128, 80 or 64 registers per thread), by timing each candidate with
  * CUDA events on the B records rec_dev (a representative batch, e.g. from
  * gp_nn; nvalid_dev as for gp_step, NULL = counted here).  The choice is kept
- * in the band and used by later gp_step calls (atomic mode; the deterministic
- * mode always takes 256-record tiles).  Reads the band's values, writes
- * nothing of the band but the choice; allocates and frees a scratch gradient;
- * synchronises.  rpt_out, bps_out may be NULL.  Errors: GP_ERR_ARG (B outside
- * (0, 2^31), null records or weights, misaligned records), GP_ERR_OOM,
- * GP_ERR_CUDA. */
+ * in the band and used by later gp_step calls.  Reads the band's values,
+ * writes nothing of the band but the choice; allocates and frees a scratch
+ * gradient; synchronises.  rpt_out, bps_out may be NULL.  Errors: GP_ERR_ARG
+ * (B outside (0, 2^31), null records or weights, misaligned records),
+ * GP_ERR_OOM, GP_ERR_CUDA. */
 gp_status gp_band_autotune(gp_band* band, const float* rec_dev, int64_t B, const int32_t* nvalid_dev,
                            const gp_loss_w* w, int32_t* rpt_out, int32_t* bps_out);
 
-/* Sets that launch shape directly: rpt records per thread (1, 2 or 4) and bps
- * resident blocks per SM (1 to 3).  Errors: GP_ERR_ARG. */
+/* Sets that launch shape directly: rpt records per thread (1 or 2) and bps
+ * blocks per SM (2, 3 or 4).  Errors: GP_ERR_ARG. */
 gp_status gp_band_set_query_tiles(gp_band* band, int32_t rpt, int32_t bps);
 
 /* ----------------------------------------------------------------- update */

@@ -446,7 +446,7 @@ def gp_step(band: Band, rec, B: int, grad, loss, weights=(1.0, 1.0, 0.005), nval
 
 def gp_band_autotune(band: Band, rec, B: int, weights=(1.0, 1.0, 0.005), nvalid=None) -> dict:
     """Times the fused step kernel's launch shapes on these records and keeps
-    the fastest in the band; returns {"records_per_tile", "blocks_per_sm"}."""
+    the fastest in the band; returns {"records_per_thread", "blocks_per_sm"}."""
     import torch
     _need(rec, torch.float32, 6 * B, "records")
     _need(nvalid, torch.int32, 1, "nvalid")
@@ -455,7 +455,7 @@ def gp_band_autotune(band: Band, rec, B: int, weights=(1.0, 1.0, 0.005), nvalid=
     band.ctx.sync_stream()
     band.ctx.check(band.ctx.lib.gp_band_autotune(band.handle, _ptr(rec), int(B), _ptr(nvalid), ctypes.byref(w),
                                                  ctypes.byref(rpt), ctypes.byref(bps)))
-    return {"records_per_tile": 256 * rpt.value, "blocks_per_sm": bps.value}
+    return {"records_per_thread": rpt.value, "blocks_per_sm": bps.value}
 
 
 def gp_band_set_query_tiles(band: Band, records_per_thread: int, blocks_per_sm: int):

@@ -92,9 +92,9 @@ struct gp_band {
   uint64_t perm_seed = 0;
   uint32_t perm_epoch = 0;
 
-  // Launch shape of the tiled query kernel (records per thread of a tile,
-  // resident blocks per SM), set by gp_band_autotune.
-  int q_rpt = 2;
+  // Launch shape of the fused step kernel (records in flight per thread,
+  // resident blocks per SM it is compiled for), set by gp_band_autotune.
+  int q_rpt = 1;
   int q_bps = 3;
 
   // Scratch for reductions and counters.

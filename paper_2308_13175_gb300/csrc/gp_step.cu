@@ -148,67 +148,74 @@ __global__ void __launch_bounds__(Q_THREADS, Q_BLOCKS_PER_SM) k_query(Grid G, co
   if (LAST) finish_if_last(partials, fa);
 }
 
-// The fused forward + backward over tiles of QT_THREADS * RPT consecutive
-// records (a persistent grid strides over the tiles): each thread takes RPT
-// records of the tile, their 16 corner contributions are aggregated per quad
-// in the block's shared-memory table (TableSink) and the table is flushed
-// to the gradient once per tile.  DET: the table and the gradient sums are
-// the two-word fixed point, so the result does not depend on the order of
-// the additions.
-template <bool DET, bool LAST, int RPT>
-__global__ void __launch_bounds__(QT_THREADS, DET ? 2 : 3) k_query_tile(Grid G, const float* __restrict__ rec, int64_t B,
-                                                           const int32_t* __restrict__ bv, float beta, float gamma,
-                                                           float* __restrict__ grad,
-                                                           unsigned long long* __restrict__ acc,
-                                                           double* __restrict__ partials, int32_t* __restrict__ err,
-                                                           FinalArgs fa) {
-  extern __shared__ __align__(16) unsigned char qt_smem[];
-  float sp = 0.f, sg = 0.f, ss = 0.f;
+// The fused forward + backward with RPT records per thread and iteration:
+// record i and i + stride (stride = the grid's threads) go through the
+// phases together, so that the loads of one level of both records are in
+// flight at once (the step is bound by the latency of these dependent
+// gathers).  The 16 corner contributions of a record go to the gradient as
+// vector reductions (GlobalSink; DET: the two-word fixed point).  MINB, the
+// resident blocks per SM the kernel is compiled for, caps its registers.
+template <bool DET, bool LAST, int RPT, int MINB>
+__global__ void __launch_bounds__(Q_THREADS, MINB) k_query_ilp(Grid G, const float* __restrict__ rec, int64_t B,
+                                                               const int32_t* __restrict__ bv, float beta,
+                                                               float gamma, float* __restrict__ grad,
+                                                               unsigned long long* __restrict__ acc,
+                                                               double* __restrict__ partials,
+                                                               int32_t* __restrict__ err, FinalArgs fa) {
   const int bvv = *bv;
   const float w = DET ? 1.0f : (bvv > 0 ? 1.0f / (float)bvv : 0.f);
-  constexpr int TILE = QT_THREADS * RPT;
-  const int64_t ntiles = (B + TILE - 1) / TILE;
-  auto run = [&](auto& sink) {
-    sink.init();
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  float sp = 0.f, sg = 0.f, ss = 0.f;
+  GlobalSink<DET> sink{G, grad, acc, err};
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < B; i0 += RPT * stride) {
+    RecState R[RPT];
 #pragma unroll
-      for (int r = 0; r < RPT; ++r) {
-        const int64_t i = tile * TILE + r * QT_THREADS + threadIdx.x;
-        if (i < B) {
-          float q[3], s[3];
-          load_rec(rec, i, q, s);
-          query_record_to<true>(G, q, s, w, beta, gamma, sink, err, sp, sg, ss);
-        }
-      }
-      sink.flush();
+    for (int r = 0; r < RPT; ++r) {
+      const int64_t i = i0 + r * stride;
+      float q[3] = {0.f, 0.f, 0.f}, s[3] = {0.f, 0.f, 0.f};
+      if (i < B) load_rec(rec, i, q, s);
+      rec_phase_a(G, q, s, i < B, R[r]);
     }
-  };
-  if constexpr (DET) {
-    TableSink<true> sink{G, acc, err, *reinterpret_cast<QTableD*>(qt_smem)};
-    run(sink);
-  } else {
-    TableSink<false> sink{G, grad, *reinterpret_cast<QTableF*>(qt_smem)};
-    run(sink);
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) rec_phase_b(G, R[r]);
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) rec_phase_c<true>(G, R[r], w, beta, gamma, sink, err, sp, sg, ss);
   }
   block_store3(partials, sp, sg, ss);
   if (LAST) finish_if_last(partials, fa);
 }
 
-template <bool DET, bool LAST, int RPT>
-cudaError_t launch_query_tile(unsigned grid, cudaStream_t s, Grid G, const float* rec, int64_t B, const int32_t* bv,
-                              float beta, float gamma, float* grad, unsigned long long* acc, double* partials,
-                              int32_t* err, FinalArgs fa) {
-  const size_t smem = DET ? sizeof(QTableD) : sizeof(QTableF);
-  static bool configured = false;  // per instantiation
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_query_tile<DET, LAST, RPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
-  k_query_tile<DET, LAST, RPT><<<grid, QT_THREADS, smem, s>>>(G, rec, B, bv, beta, gamma, grad, acc, partials, err,
-                                                              fa);
+template <bool DET, bool LAST, int RPT, int MINB>
+cudaError_t launch_query_ilp(gp_ctx* ctx, int64_t B, cudaStream_t s, Grid G, const float* rec, const int32_t* bv,
+                             float beta, float gamma, float* grad, unsigned long long* acc, double* partials,
+                             int32_t* err, FinalArgs& fa) {
+  const unsigned grid = gp_blocks(B, Q_THREADS * RPT,
+                                  std::min<int64_t>((int64_t)ctx->num_sms * MINB, GP_MAX_PARTIAL_BLOCKS));
+  fa.q_blocks = (int)grid;
+  k_query_ilp<DET, LAST, RPT, MINB><<<grid, Q_THREADS, 0, s>>>(G, rec, B, bv, beta, gamma, grad, acc, partials, err,
+                                                               fa);
   return cudaGetLastError();
+}
+
+// The tuned launch shape: RPT in {1, 2} records per thread, MINB in {2, 3, 4}.
+template <bool DET, bool LAST>
+cudaError_t launch_query_tuned(const gp_band* b, int64_t B, cudaStream_t s, Grid G, const float* rec,
+                               const int32_t* bv, float beta, float gamma, float* grad, double* partials,
+                               int32_t* err, FinalArgs& fa) {
+  gp_ctx* ctx = b->ctx;
+  unsigned long long* acc = b->acc;
+  if (b->q_rpt == 2) {
+    if (b->q_bps == 2)
+      return launch_query_ilp<DET, LAST, 2, 2>(ctx, B, s, G, rec, bv, beta, gamma, grad, acc, partials, err, fa);
+    if (b->q_bps == 4)
+      return launch_query_ilp<DET, LAST, 2, 4>(ctx, B, s, G, rec, bv, beta, gamma, grad, acc, partials, err, fa);
+    return launch_query_ilp<DET, LAST, 2, 3>(ctx, B, s, G, rec, bv, beta, gamma, grad, acc, partials, err, fa);
+  }
+  if (b->q_bps == 2)
+    return launch_query_ilp<DET, LAST, 1, 2>(ctx, B, s, G, rec, bv, beta, gamma, grad, acc, partials, err, fa);
+  if (b->q_bps == 4)
+    return launch_query_ilp<DET, LAST, 1, 4>(ctx, B, s, G, rec, bv, beta, gamma, grad, acc, partials, err, fa);
+  return launch_query_ilp<DET, LAST, 1, 3>(ctx, B, s, G, rec, bv, beta, gamma, grad, acc, partials, err, fa);
 }
 
 // The L_TV sweep over the band's bricks (tv_sweep: one brick at a time per
@@ -236,10 +243,10 @@ __global__ void __launch_bounds__(TV_THREADS, TV_BLOCKS_PER_SM) k_tv(Grid G, con
                                                    int32_t* __restrict__ err, FinalArgs fa) {
   __shared__ TvShared sh;
   float tsum = 0.f;
-  double qscale = 0.0;
+  float qscale_f = 0.f;
   if (DET) {
     int b = *bv;
-    qscale = b > 0 ? 1.0 / (double)b : 0.0;
+    qscale_f = b > 0 ? 1.0f / (float)b : 0.f;
   }
   const int l = threadIdx.x;
   auto emit = [&](int64_t addr, float gv) {
@@ -248,8 +255,10 @@ __global__ void __launch_bounds__(TV_THREADS, TV_BLOCKS_PER_SM) k_tv(Grid G, con
       long long hi = (long long)acc[2 * addr], lo = (long long)acc[2 * addr + 1];
       acc[2 * addr] = 0ull;
       acc[2 * addr + 1] = 0ull;
-      double q = ((double)hi / FIX_HI + (double)lo / FIX_LO) * qscale;
-      gv = (float)((double)gv + q);
+      // hi 2^-20 + lo 2^-60 in float32 (the scales are exact powers of two):
+      // the same operations on the same integers, so still bit-reproducible.
+      const float qv = __fmaf_rn(__ll2float_rn(hi), 9.5367431640625e-07f, __ll2float_rn(lo) * 8.673617379884035e-19f);
+      gv = __fmaf_rn(qv, qscale_f, gv);
     }
     grad[addr] = gv;
   };
@@ -381,30 +390,15 @@ extern "C" gp_status gp_step(gp_band* b, const float* rec_dev, int64_t B, const 
     GP_LAUNCH_CHECK(ctx, "k_tv");
     return GP_OK;
   };
-  // The tiled query kernel's grid: one resident wave (blocks per SM as tuned,
-  // at most 3 - the register cap of the float table's kernel - and 2 for the
-  // fixed-point table's).
-  const int rpt = det ? 1 : b->q_rpt;
-  const int bps = det ? std::min(b->q_bps, 2) : std::min(b->q_bps, 3);
-  const int64_t qtiles = (B + (int64_t)QT_THREADS * rpt - 1) / ((int64_t)QT_THREADS * rpt);
-  const unsigned qtb = (unsigned)std::max<int64_t>(1, std::min<int64_t>(qtiles, (int64_t)ctx->num_sms * bps));
-  if (grad_on) fa.q_blocks = (int)qtb;
   auto launch_q = [&]() -> gp_status {
     gp_prof_pre(ctx);
     cudaError_t e = cudaSuccess;
     if (det && grad_on) {
-      e = launch_query_tile<true, false, 1>(qtb, s, G, rec_dev, B, bv, w->beta, w->gamma, grad_dev, b->acc,
-                                            b->partials, err, fa);
+      e = launch_query_tuned<true, false>(b, B, s, G, rec_dev, bv, w->beta, w->gamma, grad_dev, b->partials, err,
+                                          fa);
     } else if (grad_on) {
-      if (rpt == 1)
-        e = launch_query_tile<false, true, 1>(qtb, s, G, rec_dev, B, bv, w->beta, w->gamma, grad_dev, b->acc,
-                                              b->partials, err, fa);
-      else if (rpt == 4)
-        e = launch_query_tile<false, true, 4>(qtb, s, G, rec_dev, B, bv, w->beta, w->gamma, grad_dev, b->acc,
-                                              b->partials, err, fa);
-      else
-        e = launch_query_tile<false, true, 2>(qtb, s, G, rec_dev, B, bv, w->beta, w->gamma, grad_dev, b->acc,
-                                              b->partials, err, fa);
+      e = launch_query_tuned<false, true>(b, B, s, G, rec_dev, bv, w->beta, w->gamma, grad_dev, b->partials, err,
+                                          fa);
     } else {
       k_query<false, false, true><<<qb, Q_THREADS, 0, s>>>(G, rec_dev, B, bv, w->beta, w->gamma, grad_dev, b->acc,
                                                            b->partials, err, fa);
@@ -441,9 +435,10 @@ extern "C" gp_status gp_update(gp_band* b, const float* grad_dev, const gp_adam*
   return GP_OK;
 }
 
-// Times the tiled query kernel's launch shapes on the given records and keeps
-// the fastest in the band: records per thread of a tile (1, 2, 4: tiles of
-// 256, 512 or 1024 records) and resident blocks per SM (2 or 3).  The band's
+// Times the fused step kernel's launch shapes on the given records and keeps
+// the fastest in the band: records in flight per thread (1 or 2) and the
+// resident blocks per SM it is compiled for (2, 3 or 4, i.e. a cap of 128, 80
+// or 64 registers per thread).  The band's
 // values are read, nothing of the band is written; a scratch gradient and
 // loss are allocated and freed.
 extern "C" gp_status gp_band_autotune(gp_band* b, const float* rec_dev, int64_t B, const int32_t* nvalid_dev,
@@ -486,15 +481,15 @@ extern "C" gp_status gp_band_autotune(gp_band* b, const float* rec_dev, int64_t 
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
   int best_rpt = b->q_rpt, best_bps = b->q_bps;
   float best = INFINITY;
-  const int rpts[3] = {1, 2, 4}, bpss[2] = {2, 3};
-  for (int ri = 0; ri < 3 && e == cudaSuccess; ++ri) {
-    for (int bi = 0; bi < 2 && e == cudaSuccess; ++bi) {
-      const int rpt = rpts[ri], bps = bpss[bi];
-      const int64_t tiles = (B + (int64_t)QT_THREADS * rpt - 1) / ((int64_t)QT_THREADS * rpt);
-      const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)ctx->num_sms * bps));
+  const int rpts[2] = {1, 2}, bpss[3] = {2, 3, 4};
+  const int save_rpt = b->q_rpt, save_bps = b->q_bps;
+  for (int ri = 0; ri < 2 && e == cudaSuccess; ++ri) {
+    for (int bi = 0; bi < 3 && e == cudaSuccess; ++bi) {
+      b->q_rpt = rpts[ri];
+      b->q_bps = bpss[bi];
       FinalArgs fa;
       fa.done = b->dev_ints + GP_DI_DONE;
-      fa.q_blocks = (int)grid;
+      fa.q_blocks = 0;
       fa.tv_blocks = 0;
       fa.bv = bv;
       fa.n_tv = b->V_tv;
@@ -504,14 +499,8 @@ extern "C" gp_status gp_band_autotune(gp_band* b, const float* rec_dev, int64_t 
       fa.tv_on = 0;
       fa.loss = loss;
       auto launch = [&]() -> cudaError_t {
-        if (rpt == 1)
-          return launch_query_tile<false, true, 1>(grid, s, G, rec_dev, B, bv, w->beta, w->gamma, grad, nullptr,
-                                                   b->partials, err, fa);
-        if (rpt == 2)
-          return launch_query_tile<false, true, 2>(grid, s, G, rec_dev, B, bv, w->beta, w->gamma, grad, nullptr,
-                                                   b->partials, err, fa);
-        return launch_query_tile<false, true, 4>(grid, s, G, rec_dev, B, bv, w->beta, w->gamma, grad, nullptr,
-                                                 b->partials, err, fa);
+        return launch_query_tuned<false, true>(b, B, s, G, rec_dev, bv, w->beta, w->gamma, grad, b->partials, err,
+                                               fa);
       };
       e = launch();  // warm-up
       if (e == cudaSuccess) e = cudaEventRecord(e0, s);
@@ -522,11 +511,13 @@ extern "C" gp_status gp_band_autotune(gp_band* b, const float* rec_dev, int64_t 
       if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
       if (e == cudaSuccess && ms < best) {
         best = ms;
-        best_rpt = rpt;
-        best_bps = bps;
+        best_rpt = rpts[ri];
+        best_bps = bpss[bi];
       }
     }
   }
+  b->q_rpt = save_rpt;
+  b->q_bps = save_bps;
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   cudaStreamSynchronize(s);
@@ -542,8 +533,8 @@ extern "C" gp_status gp_band_autotune(gp_band* b, const float* rec_dev, int64_t 
 
 extern "C" gp_status gp_band_set_query_tiles(gp_band* b, int32_t rpt, int32_t bps) {
   if (!b) return GP_ERR_ARG;
-  if (!(rpt == 1 || rpt == 2 || rpt == 4) || bps < 1 || bps > 3)
-    return gp_fail(b->ctx, GP_ERR_ARG, "gp_band_set_query_tiles: rpt must be 1, 2 or 4 and bps in [1, 3]");
+  if (!(rpt == 1 || rpt == 2) || bps < 2 || bps > 4)
+    return gp_fail(b->ctx, GP_ERR_ARG, "gp_band_set_query_tiles: rpt must be 1 or 2 and bps 2, 3 or 4");
   b->q_rpt = rpt;
   b->q_bps = bps;
   return GP_OK;

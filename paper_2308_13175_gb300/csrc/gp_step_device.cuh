@@ -223,204 +223,6 @@ struct GlobalSink {
   }
 };
 
-// Block-level aggregation of the corner contributions of a tile of records
-// in a shared-memory hash table whose entries are quads: the 4 consecutive
-// vertices 4n .. 4n + 3 of a brick row (key n = vertex address / 4).  A
-// record's 16 contributions become shared-memory atomics on about 8 quads;
-// when the tile is done every quad used is added to the gradient with one
-// 16-byte vector reduction (float) or up to 8 integer atomics (fixed point)
-// and reset.  Records of a spatially ordered batch share most quads, so the
-// global reductions drop by the sharing factor.  An insertion that finds no
-// free entry within QT_PROBES probes goes straight to the gradient.
-constexpr uint32_t QT_EMPTY = 0xffffffffu;
-constexpr int QT_PROBES = 16;
-constexpr int QT_BITS_F = 11;  // float table: 2048 quads
-constexpr int QT_BITS_D = 10;  // fixed-point table: 1024 quads
-constexpr int QT_THREADS = 256;
-
-struct QTableF {
-  float4 val[1 << QT_BITS_F];
-  uint32_t key[1 << QT_BITS_F];
-  uint16_t used[1 << QT_BITS_F];
-  int n_used;
-};
-struct QTableD {
-  unsigned long long hi[1 << QT_BITS_D][4];
-  unsigned long long lo[1 << QT_BITS_D][4];
-  uint32_t key[1 << QT_BITS_D];
-  uint16_t used[1 << QT_BITS_D];
-  int n_used;
-};
-
-template <int BITS>
-__device__ __forceinline__ int qt_find(uint32_t* keys, uint16_t* used, int* n_used, uint32_t key) {
-  uint32_t h = (key * 2654435761u) >> (32 - BITS);
-#pragma unroll 1
-  for (int p = 0; p < QT_PROBES; ++p) {
-    const uint32_t k = *(volatile uint32_t*)&keys[h];
-    if (k == key) return (int)h;
-    if (k == QT_EMPTY) {
-      const uint32_t old = atomicCAS(&keys[h], QT_EMPTY, key);
-      if (old == QT_EMPTY) {
-        used[atomicAdd(n_used, 1)] = (uint16_t)h;
-        return (int)h;
-      }
-      if (old == key) return (int)h;
-    }
-    h = (h + 1) & ((1u << BITS) - 1u);
-  }
-  return -1;
-}
-
-template <bool DET>
-struct TableSink;
-
-template <>
-struct TableSink<false> {
-  const Grid& G;
-  float* __restrict__ grad;
-  QTableF& T;
-  __device__ __forceinline__ void add(uint32_t addr, float v) {
-    const int h = qt_find<QT_BITS_F>(T.key, T.used, &T.n_used, addr >> 2);
-    if (h >= 0)
-      atomicAdd(reinterpret_cast<float*>(&T.val[h]) + (addr & 3u), v);
-    else
-      atomicAdd(grad + addr, v);
-  }
-  __device__ __forceinline__ void add2(uint32_t addr, float v0, float v1) {  // addr & 3 != 3
-    const int h = qt_find<QT_BITS_F>(T.key, T.used, &T.n_used, addr >> 2);
-    if (h >= 0) {
-      float* e = reinterpret_cast<float*>(&T.val[h]) + (addr & 3u);
-      atomicAdd(e, v0);
-      atomicAdd(e + 1, v1);
-    } else {
-      atomicAdd(grad + addr, v0);
-      atomicAdd(grad + addr + 1, v1);
-    }
-  }
-  __device__ __forceinline__ void cell(const int c[3], int slot, const float t[3], float A, const float Gt[3]) {
-    float v[8];
-    corner_values(t, A, Gt, v);
-    if ((c[0] & 7) != 7 && (c[1] & 7) != 7 && (c[2] & 7) != 7) {
-      const uint32_t base = (uint32_t)gp_vaddr(slot, c[0], c[1], c[2]);
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const uint32_t a = base + (e & 1) * 8 + (e >> 1) * 64;
-        if ((a & 3u) != 3u) {
-          add2(a, v[2 * e], v[2 * e + 1]);
-        } else {
-          add(a, v[2 * e]);
-          add(a + 1, v[2 * e + 1]);
-        }
-      }
-      return;
-    }
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const int i = c[0] + (k & 1), j = c[1] + ((k >> 1) & 1), kk = c[2] + (k >> 2);
-      const int sl = gp_brick_slot(G.table, G.nb, i, j, kk);
-      if (sl >= 0) add((uint32_t)gp_vaddr(sl, i, j, kk), v[k]);
-    }
-  }
-  // Add every quad of the tile to the gradient and reset the table; called
-  // by the whole block after the tile's inserts (synchronises).
-  __device__ __forceinline__ void flush() {
-    __syncthreads();
-    const int n = T.n_used;
-    __syncthreads();
-    if (threadIdx.x == 0) T.n_used = 0;
-    for (int u = threadIdx.x; u < n; u += blockDim.x) {
-      const int h = T.used[u];
-      const float4 q = T.val[h];
-      red_add_v4(grad + 4 * (size_t)T.key[h], q.x, q.y, q.z, q.w);
-      T.key[h] = QT_EMPTY;
-      T.val[h] = make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-    __syncthreads();
-  }
-  __device__ __forceinline__ void init() {
-    for (int h = threadIdx.x; h < (1 << QT_BITS_F); h += blockDim.x) {
-      T.key[h] = QT_EMPTY;
-      T.val[h] = make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-    if (threadIdx.x == 0) T.n_used = 0;
-    __syncthreads();
-  }
-};
-
-template <>
-struct TableSink<true> {
-  const Grid& G;
-  unsigned long long* __restrict__ acc;
-  int32_t* __restrict__ err;
-  QTableD& T;
-  __device__ __forceinline__ void add(uint32_t addr, float v) {
-    long long hi, lo;
-    if (!fix_split(v, hi, lo)) {
-      atomicOr(err, GP_EF_NUMERIC);
-      return;
-    }
-    if (!hi && !lo) return;
-    const int h = qt_find<QT_BITS_D>(T.key, T.used, &T.n_used, addr >> 2);
-    if (h >= 0) {
-      if (hi) atomicAdd(&T.hi[h][addr & 3u], (unsigned long long)hi);
-      if (lo) atomicAdd(&T.lo[h][addr & 3u], (unsigned long long)lo);
-    } else {
-      if (hi) atomicAdd(acc + 2 * (size_t)addr, (unsigned long long)hi);
-      if (lo) atomicAdd(acc + 2 * (size_t)addr + 1, (unsigned long long)lo);
-    }
-  }
-  __device__ __forceinline__ void cell(const int c[3], int slot, const float t[3], float A, const float Gt[3]) {
-    float v[8];
-    corner_values(t, A, Gt, v);
-    if ((c[0] & 7) != 7 && (c[1] & 7) != 7 && (c[2] & 7) != 7) {
-      const uint32_t base = (uint32_t)gp_vaddr(slot, c[0], c[1], c[2]);
-#pragma unroll
-      for (int k = 0; k < 8; ++k) add(base + (k & 1) + ((k >> 1) & 1) * 8 + (k >> 2) * 64, v[k]);
-      return;
-    }
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const int i = c[0] + (k & 1), j = c[1] + ((k >> 1) & 1), kk = c[2] + (k >> 2);
-      const int sl = gp_brick_slot(G.table, G.nb, i, j, kk);
-      if (sl >= 0) add((uint32_t)gp_vaddr(sl, i, j, kk), v[k]);
-    }
-  }
-  __device__ __forceinline__ void flush() {
-    __syncthreads();
-    const int n = T.n_used;
-    __syncthreads();
-    if (threadIdx.x == 0) T.n_used = 0;
-    for (int u = threadIdx.x; u < 4 * n; u += blockDim.x) {
-      const int h = T.used[u >> 2], l = u & 3;
-      const unsigned long long hi = T.hi[h][l], lo = T.lo[h][l];
-      const size_t addr = 4 * (size_t)T.key[h] + l;
-      if (hi) atomicAdd(acc + 2 * addr, hi);
-      if (lo) atomicAdd(acc + 2 * addr + 1, lo);
-    }
-    __syncthreads();
-    for (int u = threadIdx.x; u < 4 * n; u += blockDim.x) {
-      const int h = T.used[u >> 2], l = u & 3;
-      T.hi[h][l] = 0ull;
-      T.lo[h][l] = 0ull;
-      if (l == 0) T.key[h] = QT_EMPTY;
-    }
-    __syncthreads();
-  }
-  __device__ __forceinline__ void init() {
-    for (int h = threadIdx.x; h < (1 << QT_BITS_D); h += blockDim.x) {
-      T.key[h] = QT_EMPTY;
-#pragma unroll
-      for (int l = 0; l < 4; ++l) {
-        T.hi[h][l] = 0ull;
-        T.lo[h][l] = 0ull;
-      }
-    }
-    if (threadIdx.x == 0) T.n_used = 0;
-    __syncthreads();
-  }
-};
-
 // One step record: classify it, evaluate Eq. 3 at q and at s, add its loss
 // terms to sp / sg / ss and (GRAD) scatter its gradient to the 8 + 8 corners,
 // scaled by w (1/B_v; 1 for the fixed-point sums, scaled at the end).
@@ -429,29 +231,67 @@ struct TableSink<true> {
 // for latency: both brick slots are read together, then both pull-mask words
 // and all 16 corner values together (the corners of a record that turns out
 // invalid are read for nothing).
-template <bool GRAD, class Sink>
-__device__ __forceinline__ bool query_record_to(const Grid& G, const float q[3], const float s[3], float w,
-                                                float beta, float gamma, Sink& sink, int32_t* __restrict__ err,
-                                                float& sp, float& sg, float& ss) {
+// A record between the phases of its evaluation.  The three phases issue
+// the record's dependent loads level by level - the brick slots (phase a),
+// then the pull-mask words and the 16 corner values (phase b) - so that a
+// thread working on several records issues all of one level's loads before it
+// waits for any of them.
+struct RecState {
+  float q[3], s[3];
   Cells C;
-  if (!classify_cells(G, q, s, C)) return false;
-  C.slot_q = gp_brick_slot(G.table, G.nb, C.cq[0], C.cq[1], C.cq[2]);
-  C.slot_s = gp_brick_slot(G.table, G.nb, C.cs[0], C.cs[1], C.cs[2]);
-  if (C.slot_q < 0 || C.slot_s < 0) return false;
-  const int lq = gp_local(C.cq[0], C.cq[1], C.cq[2]), ls = gp_local(C.cs[0], C.cs[1], C.cs[2]);
-  const uint32_t wq = __ldg(G.masks + (int64_t)C.slot_q * 48 + 32 + (lq >> 5));
-  const uint32_t ws = __ldg(G.masks + (int64_t)C.slot_s * 48 + 32 + (ls >> 5));
-  bool ok = true;
+  int lq, ls;
+  uint32_t wq, ws;
   float dq[8], ds[8];
-  load_corners(G, C.cq, C.slot_q, dq, ok);
-  load_corners(G, C.cs, C.slot_s, ds, ok);
-  if (!((wq >> (lq & 31)) & 1u) || !((ws >> (ls & 31)) & 1u)) return false;
-  if (!ok) {
+  bool ok;       // still a candidate for a valid record
+  bool corners;  // every corner was found in the band
+};
+
+__device__ __forceinline__ void rec_phase_a(const Grid& G, const float q[3], const float s[3], bool active,
+                                            RecState& R) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    R.q[a] = q[a];
+    R.s[a] = s[a];
+  }
+  R.ok = active && classify_cells(G, q, s, R.C);
+  if (!R.ok) return;
+  R.C.slot_q = gp_brick_slot(G.table, G.nb, R.C.cq[0], R.C.cq[1], R.C.cq[2]);
+  R.C.slot_s = gp_brick_slot(G.table, G.nb, R.C.cs[0], R.C.cs[1], R.C.cs[2]);
+}
+
+__device__ __forceinline__ void rec_phase_b(const Grid& G, RecState& R) {
+  if (!R.ok) return;
+  if (R.C.slot_q < 0 || R.C.slot_s < 0) {
+    R.ok = false;
+    return;
+  }
+  R.lq = gp_local(R.C.cq[0], R.C.cq[1], R.C.cq[2]);
+  R.ls = gp_local(R.C.cs[0], R.C.cs[1], R.C.cs[2]);
+  R.wq = __ldg(G.masks + (int64_t)R.C.slot_q * 48 + 32 + (R.lq >> 5));
+  R.ws = __ldg(G.masks + (int64_t)R.C.slot_s * 48 + 32 + (R.ls >> 5));
+  R.corners = true;
+  load_corners(G, R.C.cq, R.C.slot_q, R.dq, R.corners);
+  load_corners(G, R.C.cs, R.C.slot_s, R.ds, R.corners);
+}
+
+// Validity (cell(q) and cell(s) in the pull band, Sec. 3), the forward terms
+// and, with GRAD, the backward pass into the sink.  Returns whether the
+// record is valid.
+template <bool GRAD, class Sink>
+__device__ __forceinline__ bool rec_phase_c(const Grid& G, RecState& R, float w, float beta, float gamma,
+                                            Sink& sink, int32_t* __restrict__ err, float& sp, float& sg,
+                                            float& ss) {
+  if (!R.ok) return false;
+  if (!((R.wq >> (R.lq & 31)) & 1u) || !((R.ws >> (R.ls & 31)) & 1u)) return false;
+  if (!R.corners) {
     atomicOr(err, GP_EF_RANGE);
     return false;
   }
-  Eval eq = trilerp(dq, C.tq);
-  Eval es = trilerp(ds, C.ts);
+  const float* q = R.q;
+  const float* s = R.s;
+  const Cells& C = R.C;
+  Eval eq = trilerp(R.dq, C.tq);
+  Eval es = trilerp(R.ds, C.ts);
   float g[3] = {eq.gt[0] * G.half_r, eq.gt[1] * G.half_r, eq.gt[2] * G.half_r};
   float gs[3] = {es.gt[0] * G.half_r, es.gt[1] * G.half_r, es.gt[2] * G.half_r};
   float gl = sqrtf(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
@@ -492,6 +332,16 @@ __device__ __forceinline__ bool query_record_to(const Grid& G, const float q[3],
   sink.cell(C.cq, C.slot_q, C.tq, dfq, Gq);
   sink.cell(C.cs, C.slot_s, C.ts, dfs, Gs);
   return true;
+}
+
+template <bool GRAD, class Sink>
+__device__ __forceinline__ bool query_record_to(const Grid& G, const float q[3], const float s[3], float w,
+                                                float beta, float gamma, Sink& sink, int32_t* __restrict__ err,
+                                                float& sp, float& sg, float& ss) {
+  RecState R;
+  rec_phase_a(G, q, s, true, R);
+  rec_phase_b(G, R);
+  return rec_phase_c<GRAD>(G, R, w, beta, gamma, sink, err, sp, sg, ss);
 }
 
 // The record with its contributions reduced straight into the gradient.
