@@ -210,6 +210,45 @@ def band_sets(points: np.ndarray, R: int, M1: int, M2: int) -> dict:
             "required": required}
 
 
+def _dilate_cells_bitmap(b: np.ndarray, M: int) -> np.ndarray:
+    """Chebyshev dilation by M of a boolean cell array (per axis: separable)."""
+    out = b
+    for ax in range(3):
+        src, res = out, out.copy()
+        n = src.shape[ax]
+        for d in range(1, min(M, n - 1) + 1):
+            hi, lo = [slice(None)] * 3, [slice(None)] * 3
+            hi[ax], lo[ax] = slice(d, None), slice(None, n - d)
+            res[tuple(hi)] |= src[tuple(lo)]
+            res[tuple(lo)] |= src[tuple(hi)]
+        out = res
+    return out
+
+
+def band_vertex_sets_bitmap(points: np.ndarray, R: int, M1: int, M2: int) -> dict:
+    """The TV and trainable vertex sets of band_sets (corners of the M2 and
+    max(M1, M2) dilations of the occupied cells) as sorted keys, built on dense
+    boolean arrays indexed [k, j, i] instead of sets of keys: the same
+    definition, for grids where 125 shifted copies of the occupied set would not
+    fit in memory.  Also returns the occupied cell keys."""
+    occ_keys = occupied_cells(points, R)
+    occ = np.zeros((R, R, R), bool)
+    c = key_to_cell(occ_keys, R)
+    occ[c[:, 2], c[:, 1], c[:, 0]] = True
+    out = {"occupied": occ_keys}
+    big = -1 if (M1 < 0 or M2 < 0) else max(M1, M2)
+    for name, M in (("tv", M2), ("trainable", big)):
+        cells = np.ones_like(occ) if M < 0 else _dilate_cells_bitmap(occ, M)
+        v = np.zeros((R + 1,) * 3, bool)
+        for dz in (0, 1):
+            for dy in (0, 1):
+                for dx in (0, 1):
+                    v[dz:dz + R, dy:dy + R, dx:dx + R] |= cells
+        out[name] = np.flatnonzero(v.reshape(-1)).astype(np.int64)  # i fastest: the vertex key order
+        del v, cells
+    return out
+
+
 # ----------------------------------------------------- nearest neighbour
 def sq_dist64(q: np.ndarray, s: np.ndarray) -> np.ndarray:
     """((qx-sx)^2 + (qy-sy)^2) + (qz-sz)^2 in float64 for all pairs (Nq, Ns)."""

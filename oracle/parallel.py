@@ -35,6 +35,11 @@ def _nn(path: str):
     return time.perf_counter() - t
 
 
+def _nn_idx(path: str):
+    """Brute-force NN(q) indices of one chunk of queries."""
+    return o.nearest_point(np.load(path), np.asarray(_POINTS), chunk=8)
+
+
 def _sigma(args):
     path, k = args
     idx = np.load(path)
@@ -116,6 +121,10 @@ class OraclePool:
 
     def nn(self, paths):
         return self.timed_map(_nn, paths)
+
+    def nn_indices(self, paths):
+        """Brute-force NN indices of the chunks, in order."""
+        return np.concatenate(self.pool.map(_nn_idx, paths, chunksize=1))
 
     def terms(self, items):
         return self.timed_map(_terms, items)

@@ -2,10 +2,13 @@
 
 ``FitStep.run(t)`` performs step t of the fit over one batch of the epoch's
 query pool: gp_sample (Gaussian queries around points visited in the epoch's
-random order, emitted grouped by source point in the cloud's cell order) -> gp_nn (NN(q), step records; each search seeded with the
-query's own source point) -> gp_step (Eq. 8 forward and
-hand-written backward) -> gp_update (Adam).  All device buffers are allocated
-once here; the calls themselves never allocate."""
+random order, emitted grouped by source point in the cloud's cell order) ->
+gp_nn (NN(q), step records; each search seeded with the query's own source
+point) -> gp_step (Eq. 8 forward and hand-written backward) -> gp_update
+(Adam).  ``FitStep.run_pipelined(t0, K)`` runs K such steps with each next
+batch's sampling and nearest points overlapped on a second stream.  All
+device buffers are allocated once here; the calls themselves never
+allocate."""
 from __future__ import annotations
 
 import math
@@ -29,12 +32,18 @@ class FitStep:
         self.flags = gb.GP_STEP_DETERMINISTIC if deterministic else 0
         self.batches_per_epoch = math.ceil(self.Q / self.B)
         dev = torch.device("cuda", band.ctx.device)
-        self.q = torch.empty((self.B, 3), dtype=torch.float32, device=dev)
-        self.src = torch.empty(self.B, dtype=torch.int32, device=dev)
-        self.rec = torch.empty((self.B, 6), dtype=torch.float32, device=dev)
+        self.device = dev
+        # Two sets of per-batch buffers: the pipelined form fills one while the
+        # step reads the other; run(t) uses the first.
+        self.bufs = [{"q": torch.empty((self.B, 3), dtype=torch.float32, device=dev),
+                      "src": torch.empty(self.B, dtype=torch.int32, device=dev),
+                      "rec": torch.empty((self.B, 6), dtype=torch.float32, device=dev),
+                      "nvalid": torch.zeros(1, dtype=torch.int32, device=dev)} for _ in range(2)]
+        self.q, self.src = self.bufs[0]["q"], self.bufs[0]["src"]
+        self.rec, self.nvalid = self.bufs[0]["rec"], self.bufs[0]["nvalid"]
         self.grad = torch.empty(band.V_stored, dtype=torch.float32, device=dev)
         self.loss = torch.zeros(8, dtype=torch.float32, device=dev)
-        self.nvalid = torch.zeros(1, dtype=torch.int32, device=dev)
+        self._streams = None
 
     def batch_of(self, t: int):
         epoch, b = divmod(int(t), self.batches_per_epoch)
@@ -56,14 +65,66 @@ class FitStep:
         gb.gp_nn(band, self.q[:count], None, self.rec, hint=self.src[:count], nvalid_out=self.nvalid)
         return gb.gp_band_autotune(band, self.rec, count, self.weights, nvalid=self.nvalid)
 
+    def _draw(self, t: int, buf: dict):
+        """Sampling and nearest points of step t's batch into buf (neither
+        reads the grid values)."""
+        epoch, first, count = self.batch_of(t)
+        gb.gp_sample(self.band, self.seed, epoch, self.Q, first, count, buf["q"], buf["src"], spatial=True)
+        gb.gp_nn(self.band, buf["q"][:count], None, buf["rec"], hint=buf["src"][:count], nvalid_out=buf["nvalid"])
+        return count
+
+    def _descend(self, t: int, buf: dict, count: int):
+        """Eq. 8 forward and backward on buf's records, then Adam."""
+        gb.gp_step(self.band, buf["rec"], count, self.grad, self.loss, self.weights, nvalid=buf["nvalid"],
+                   flags=self.flags)
+        gb.gp_update(self.band, self.grad, self.lr_at(t), t + 1)
+
     def run(self, t: int):
         """Step t (0-based); returns the loss buffer (device, 8 floats)."""
-        band = self.band
-        epoch, first, count = self.batch_of(t)
-        gb.gp_sample(band, self.seed, epoch, self.Q, first, count, self.q, self.src, spatial=True)
-        gb.gp_nn(band, self.q[:count], None, self.rec, hint=self.src[:count], nvalid_out=self.nvalid)
-        gb.gp_step(band, self.rec, count, self.grad, self.loss, self.weights, nvalid=self.nvalid, flags=self.flags)
-        gb.gp_update(band, self.grad, self.lr_at(t), t + 1)
+        count = self._draw(t, self.bufs[0])
+        self._descend(t, self.bufs[0], count)
+        return self.loss
+
+    def run_pipelined(self, t0: int, K: int):
+        """Steps t0 .. t0 + K - 1, the same as run(t0), ..., run(t0 + K - 1),
+        with the next batch's sampling and nearest points on a second stream
+        while the current batch's step and update run on a third: the draw
+        does not read the grid values, so only the record buffers need
+        ordering (two of them, alternating).  The calling stream waits for
+        everything before this returns (asynchronously, as every call here).
+        Returns the loss buffer of the last step."""
+        if K <= 0:
+            return self.loss
+        if self._streams is None:
+            lo, hi = torch.cuda.Stream.priority_range()
+            self._streams = (torch.cuda.Stream(self.device), torch.cuda.Stream(self.device, priority=hi))
+            self._events = [[torch.cuda.Event() for _ in range(2)] for _ in range(2)]
+        sa, sb = self._streams
+        drawn, stepped = self._events
+        cur = torch.cuda.current_stream(self.device)
+        sa.wait_stream(cur)
+        sb.wait_stream(cur)
+        counts = {}
+
+        def draw(t):
+            p = t % 2
+            with torch.cuda.stream(sa):
+                if t - 2 >= t0:
+                    sa.wait_event(stepped[p])  # step t - 2 has read buffer p
+                counts[t] = self._draw(t, self.bufs[p])
+                drawn[p].record(sa)
+
+        draw(t0)
+        for t in range(t0, t0 + K):
+            if t + 1 < t0 + K:
+                draw(t + 1)
+            p = t % 2
+            with torch.cuda.stream(sb):
+                sb.wait_event(drawn[p])
+                self._descend(t, self.bufs[p], counts[t])
+                stepped[p].record(sb)
+        cur.wait_stream(sa)
+        cur.wait_stream(sb)
         return self.loss
 
 

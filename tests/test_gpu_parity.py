@@ -623,3 +623,34 @@ def test_fit_steps_reduce_the_loss(gb, ctx, sphere5k):
     assert all(np.isfinite(losses))
     assert losses[-1] < losses[0]
     gb.gp_band_check(band)
+
+
+def test_pipelined_steps_equal_sequential_steps(gb, ctx, sphere5k):
+    """FitStep.run_pipelined overlaps each next batch's sampling and nearest
+    points with the current step; with the deterministic sums it must give
+    the same values, moments and loss, bit for bit, as running the steps one
+    after the other - across epoch boundaries and a short last batch."""
+    import torch
+    from paper_2308_13175_gb300.fit import FitStep
+    R = 64
+    bands, fits = [], []
+    for _ in range(2):
+        band = _band(gb, ctx, sphere5k, R, 2, 2, knn_k=50, deterministic=True)
+        gb.gp_band_init_sphere(band, (0.0, 0.0, 0.0), 0.45, 0.01, seed=5)
+        bands.append(band)
+        fits.append(FitStep(band, Q=40_000, B=15_000, seed=3, lr=1e-3, deterministic=True))
+    K = 7
+    for t in range(K):
+        fits[0].run(t)
+    fits[1].run_pipelined(0, K)
+    torch.cuda.synchronize()
+    for a, b in zip(gb.gp_band_values(bands[0]), gb.gp_band_values(bands[1])):
+        assert torch.equal(a, b)
+    assert torch.equal(fits[0].loss, fits[1].loss)
+    # Two pipelined calls in a row continue where the first stopped.
+    for t in range(K, K + 3):
+        fits[0].run(t)
+    fits[1].run_pipelined(K, 3)
+    torch.cuda.synchronize()
+    assert torch.equal(gb.gp_band_values(bands[0])[0], gb.gp_band_values(bands[1])[0])
+    gb.gp_band_check(bands[1])

@@ -486,3 +486,13 @@ def test_sparse_store_and_band_membership_equal_the_dense_forms():
     assert np.allclose(ga + gbb, gfull[sp.keys], rtol=0, atol=1e-15 * np.abs(gfull).max())
     with pytest.raises(KeyError):
         sp.index(np.array([np.setdiff1d(np.arange(len(D)), req)[0]]))
+
+
+def test_bitmap_vertex_sets_equal_the_set_form():
+    """The dense-bitmap band sets equal band_sets' key-set arithmetic."""
+    pts = synth.sphere_cloud(700, 0.4, seed=3)
+    for R, M1, M2 in ((32, 2, 2), (32, 1, 3), (16, 0, 0), (16, 2, -1), (8, 3, 1)):
+        a = o.band_sets(pts, R, M1, M2)
+        b = o.band_vertex_sets_bitmap(pts, R, M1, M2)
+        assert np.array_equal(a["tv"], b["tv"]) and np.array_equal(a["trainable"], b["trainable"]), (R, M1, M2)
+        assert np.array_equal(a["occupied"], b["occupied"])
