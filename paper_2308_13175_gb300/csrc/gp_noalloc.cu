@@ -173,9 +173,14 @@ __global__ void __launch_bounds__(NA_THREADS) k_na_query(int R, const float* __r
     float ns[3] = {gsv[0] * invs, gsv[1] * invs, gsv[2] * invs};
     float r[3] = {(q[0] - s[0]) - f * n[0], (q[1] - s[1]) - f * n[1], (q[2] - s[2]) - f * n[2]};
     float lp = sqrtf(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
-    float cosv = n[0] * ns[0] + n[1] * ns[1] + n[2] * ns[2];
+    // 1 - n . ns as |n - ns|^2 / 2 plus the deficits of non-unit vectors
+    // (below the 1e-12 floor): no cancellation near cos = 1.
+    const float e0 = n[0] - ns[0], e1 = n[1] - ns[1], e2 = n[2] - ns[2];
+    float lgr = 0.5f * (e0 * e0 + e1 * e1 + e2 * e2);
+    if (!(gl > 1e-12f)) lgr += 0.5f * (1.0f - (n[0] * n[0] + n[1] * n[1] + n[2] * n[2]));
+    if (!(gls > 1e-12f)) lgr += 0.5f * (1.0f - (ns[0] * ns[0] + ns[1] * ns[1] + ns[2] * ns[2]));
     sp = lp;
-    sg = 1.0f - cosv;
+    sg = lgr;
     ss = fabsf(fs);
     if (grad) {
       float ilp = lp > 0.f ? 1.0f / lp : 0.f;

@@ -231,6 +231,64 @@ struct GlobalSink {
 // for latency: both brick slots are read together, then both pull-mask words
 // and all 16 corner values together (the corners of a record that turns out
 // invalid are read for nothing).
+// l_grad = 1 - n . n_s (Eq. 7) without the cancellation of 1 - cos near
+// cos = 1: 1 - n.m = |n - m|^2 / 2 + (1 - |n|^2) / 2 + (1 - |m|^2) / 2, whose
+// last two terms vanish for a unit vector (a gradient above the floor).  The
+// difference n - m of two close unit vectors is computed almost exactly.
+__device__ __forceinline__ float grad_term(const float n[3], const float m[3], bool n_unit, bool m_unit) {
+  const float d0 = n[0] - m[0], d1 = n[1] - m[1], d2 = n[2] - m[2];
+  float l = 0.5f * (d0 * d0 + d1 * d1 + d2 * d2);
+  if (!n_unit) l += 0.5f * (1.0f - (n[0] * n[0] + n[1] * n[1] + n[2] * n[2]));
+  if (!m_unit) l += 0.5f * (1.0f - (m[0] * m[0] + m[1] * m[1] + m[2] * m[2]));
+  return l;
+}
+
+// The backward pass of one record from its forward quantities.  With
+// u = r / |r| (0 at r = 0), for the pull term dL/df = -w u.n and
+// dL/dn = -w f u - w gamma n_s, for the gradient term dL/dn_s = -w gamma n;
+// through n = g / |g|, dL/dg = (I - n n^T) dL/dn / |g| (dL/dn / 1e-12 below the
+// floor), and dL/dt = dL/dg R/2.  For a unit n the projections are taken from
+// small differences instead of differences of large terms:
+//   u.n = ((q - s).n - f) / |r|,  (I - n n^T) u = ((q - s) - ((q - s).n) n) / |r|,
+//   (I - n n^T) n_s = (n_s - n) - ((n_s - n).n) n,
+// which are the same quantities, but keep float32 accuracy when |f| >> |q - s|
+// or n ~ n_s (the residual r = (q - s) - f n loses the small perpendicular
+// part of q - s to the rounding of f n).
+__device__ __forceinline__ void backward_terms(const float q[3], const float s[3], float f, const float nv[3],
+                                               const float ns[3], float lp, float inv, float invs, bool big,
+                                               bool bigs, float w, float gamma, float half_r, float Gq[3],
+                                               float Gs[3], float& dfq) {
+  const float ilp = lp > 0.f ? 1.0f / lp : 0.f;
+  const float d[3] = {q[0] - s[0], q[1] - s[1], q[2] - s[2]};
+  if (big) {
+    const float dn = d[0] * nv[0] + d[1] * nv[1] + d[2] * nv[2];
+    const float e[3] = {ns[0] - nv[0], ns[1] - nv[1], ns[2] - nv[2]};
+    const float en = e[0] * nv[0] + e[1] * nv[1] + e[2] * nv[2];
+    dfq = -w * (dn - f) * ilp;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const float u_perp = (d[a] - dn * nv[a]) * ilp;
+      const float ns_perp = e[a] - en * nv[a];
+      Gq[a] = (-w * f * u_perp - w * gamma * ns_perp) * inv * half_r;
+    }
+  } else {
+    const float r[3] = {d[0] - f * nv[0], d[1] - f * nv[1], d[2] - f * nv[2]};
+    const float un = (r[0] * nv[0] + r[1] * nv[1] + r[2] * nv[2]) * ilp;
+    dfq = -w * un;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) Gq[a] = (-w * f * r[a] * ilp - w * gamma * ns[a]) * inv * half_r;
+  }
+  if (bigs) {
+    const float e[3] = {nv[0] - ns[0], nv[1] - ns[1], nv[2] - ns[2]};
+    const float en = e[0] * ns[0] + e[1] * ns[1] + e[2] * ns[2];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) Gs[a] = -w * gamma * (e[a] - en * ns[a]) * invs * half_r;
+  } else {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) Gs[a] = -w * gamma * nv[a] * invs * half_r;
+  }
+}
+
 // A record between the phases of its evaluation.  The three phases issue
 // the record's dependent loads level by level - the brick slots (phase a),
 // then the pull-mask words and the 16 corner values (phase b) - so that a
@@ -302,32 +360,13 @@ __device__ __forceinline__ bool rec_phase_c(const Grid& G, RecState& R, float w,
   float f = eq.f, fs = es.f;
   float r[3] = {(q[0] - s[0]) - f * nv[0], (q[1] - s[1]) - f * nv[1], (q[2] - s[2]) - f * nv[2]};
   float lp = sqrtf(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
-  float cosv = nv[0] * ns[0] + nv[1] * ns[1] + nv[2] * ns[2];
+  bool big = gl > NORM_FLOOR, bigs = gls > NORM_FLOOR;
   sp += lp;
-  sg += 1.0f - cosv;
+  sg += grad_term(nv, ns, big, bigs);
   ss += fabsf(fs);
   if (!GRAD) return true;
-  float ilp = lp > 0.f ? 1.0f / lp : 0.f;
-  float u[3] = {r[0] * ilp, r[1] * ilp, r[2] * ilp};
-  float un = u[0] * nv[0] + u[1] * nv[1] + u[2] * nv[2];
-  float dfq = -w * un;
-  float dn[3], dns[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    dn[a] = -w * f * u[a] - w * gamma * ns[a];
-    dns[a] = -w * gamma * nv[a];
-  }
-  float ndn = nv[0] * dn[0] + nv[1] * dn[1] + nv[2] * dn[2];
-  float nsdns = ns[0] * dns[0] + ns[1] * dns[1] + ns[2] * dns[2];
-  bool big = gl > NORM_FLOOR, bigs = gls > NORM_FLOOR;
-  float Gq[3], Gs[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    float dg = big ? (dn[a] - nv[a] * ndn) * inv : dn[a] * inv;
-    float dgs = bigs ? (dns[a] - ns[a] * nsdns) * invs : dns[a] * invs;
-    Gq[a] = dg * G.half_r;  // dL/dt = dL/dg * dg/dt
-    Gs[a] = dgs * G.half_r;
-  }
+  float Gq[3], Gs[3], dfq;
+  backward_terms(q, s, f, nv, ns, lp, inv, invs, big, bigs, w, gamma, G.half_r, Gq, Gs, dfq);
   float dfs = fs > 0.f ? w * beta : (fs < 0.f ? -w * beta : 0.f);
   sink.cell(C.cq, C.slot_q, C.tq, dfq, Gq);
   sink.cell(C.cs, C.slot_s, C.ts, dfs, Gs);

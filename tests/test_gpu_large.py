@@ -95,7 +95,7 @@ def test_full_size_parity(name):
     gb.gp_step(band, rec, B, grad, loss, W, nvalid=nvalid)
     torch.cuda.synchronize()
     lf = loss.cpu().numpy()
-    assert lf[gb.GP_LOSS_BV] == float(int(nvalid.item())) > 0.9 * B
+    assert lf[gb.GP_LOSS_BV] == float(int(nvalid.item())) > 0.5 * B
     assert np.all(np.isfinite(lf))
     nn = nn.cpu().numpy()
 
@@ -135,7 +135,7 @@ def test_full_size_parity(name):
     gb.gp_step(band, rec_s, N_NN, gs, ls_t, W, flags=gb.GP_STEP_NO_TV)
     torch.cuda.synchronize()
     lsub = ls_t.cpu().numpy()
-    assert lsub[gb.GP_LOSS_BV] == ref["Bv"] > 0.9 * N_NN
+    assert lsub[gb.GP_LOSS_BV] == ref["Bv"] > 0.5 * N_NN
     for slot, key in ((gb.GP_LOSS_PULL, "l_pull"), (gb.GP_LOSS_GRAD, "l_grad"), (gb.GP_LOSS_SURF, "l_surf"),
                       (gb.GP_LOSS_TOTAL, "loss")):
         assert_rel(lsub[slot], ref[key], what=f"{name} {key}")
