@@ -80,6 +80,9 @@ def alg_bytes(name, n, J, Vs, Vt):
         "k_tv": 8 * Vs,
         "k_query": 24 * n + 8 * Vt,
         "k_adam": 28 * Vt,
+        # the fused L_TV + Adam sweep: values read for the stencil; per trainable
+        # vertex the query part read and reset, m, v read, value, m, v written
+        "k_tv_adam": 4 * Vs + 28 * Vt,
     }.get(name, 0)
 
 
@@ -551,7 +554,8 @@ def run_ours(args, world, rank, local):
         per_kernel[name] = {"launches": cnt, "avg_us": round(1e3 * avg_ms, 2),
                             "share": round(tot / max(sum(v[1] for v in kern.values()), 1e-12), 4),
                             "alg_bytes": int(by), "gbs": round(by / (avg_ms / 1e3) / 1e9, 1) if by else None}
-    fba = fwd_bwd_adam(per_kernel, ("k_count_valid", "k_tv", "k_query", "k_adam"), q_prof / args.steps, Vt, peak)
+    fba = fwd_bwd_adam(per_kernel, ("k_count_valid", "k_tv", "k_query", "k_adam", "k_tv_adam"), q_prof / args.steps,
+                       Vt, peak)
     dom = max(kern.items(), key=lambda kv: kv[1][1])[0]
     dk = per_kernel[dom]
     nn_work = None
@@ -696,8 +700,8 @@ def run_ours(args, world, rank, local):
         flush.fill_(float(k))
         stream.wait_event(ready[b])
         gb.gp_nn(band, dq[b], None, fit.rec, hint=dsrc[b], nvalid_out=fit.nvalid)
-        gb.gp_step(band, fit.rec, B, fit.grad, fit.loss, PAPER_WEIGHTS, nvalid=fit.nvalid, flags=fit.flags)
-        gb.gp_update(band, fit.grad, wl["lr"], step_t + k + 1)
+        gb.gp_step_update(band, fit.rec, B, fit.loss, wl["lr"], step_t + k + 1, PAPER_WEIGHTS, nvalid=fit.nvalid,
+                          flags=fit.flags)
         free[b].record(stream)
         hloss[k].copy_(fit.loss, non_blocking=True)
     e_end.record(stream)
@@ -731,8 +735,8 @@ def run_ours(args, world, rank, local):
             t_ms.append(e0.elapsed_time(e1))
             flush.fill_(float(k))
             e0.record(stream)
-            gb.gp_step(band, rec, B, fit.grad, fit.loss, PAPER_WEIGHTS, nvalid=nv, flags=fit.flags)
-            gb.gp_update(band, fit.grad, wl["lr"], step_t + K + k + 1)
+            gb.gp_step_update(band, rec, B, fit.loss, wl["lr"], step_t + K + k + 1, PAPER_WEIGHTS, nvalid=nv,
+                              flags=fit.flags)
             e1.record(stream)
             torch.cuda.synchronize()
             o_ms.append(e0.elapsed_time(e1))
@@ -765,7 +769,7 @@ def run_ours(args, world, rank, local):
                           "brick": 8},
                "roofline": roofline, "cpu_baseline": cpu,
                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 16 * B, "d2h_bytes_per_step": 32,
-                       "path": "host queries and their source points -> gp_nn (seeded) -> gp_step -> gp_update "
+                       "path": "host queries and their source points -> gp_nn (seeded) -> gp_step_update "
                                "-> loss to host; next step's copy overlapped on a second stream; K steps timed "
                                "as one region, L2 flush included"},
                "gpu_launches": int(launches), "clocks": clk, "kernels": per_kernel, "fwd_bwd_adam": fba,

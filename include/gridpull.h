@@ -172,7 +172,8 @@ gp_status gp_band_export(const gp_band* band, int32_t* ijk_dev, float* d_dev, ui
 
 /* Zero-copy device pointers of the band's values and Adam moments (each
  * V_stored floats, storage order).  Any output may be NULL.  The pointers stay
- * valid until gp_band_destroy. */
+ * valid until gp_band_destroy; the values pointer is the current one of the
+ * band's two value buffers, which gp_step_update swaps. */
 gp_status gp_band_values(gp_band* band, float** d_dev, float** m_dev, float** v_dev);
 
 /* Copy sigma_j (J floats, original point order) to `sigma_dev`. */
@@ -313,6 +314,27 @@ typedef struct gp_adam {
  * trainable set are left untouched (Sec. 3: only variables in the bandwidth are
  * optimised).  Errors: GP_ERR_ARG (step < 1, null pointers). */
 gp_status gp_update(gp_band* band, const float* grad_dev, const gp_adam* hp, int64_t step);
+
+/* One fitting step on the band's own values: the loss and gradient of gp_step
+ * followed by gp_update's Adam at step `step` (>= 1), in two kernels and
+ * without a gradient array: the query pass adds its corner contributions into
+ * the band's internal query gradient (kept all zero between calls), then one
+ * sweep over the bricks computes each vertex's L_TV gradient, adds and resets
+ * the query part and applies Adam to the trainable vertices (Sec. 3: only the
+ * band is optimised).  The new values are written to the band's second value
+ * buffer while the stencil reads the current one; the two are swapped when
+ * the call returns, so the pointer gp_band_values gives changes with every
+ * call (fetch it again) and a band stepped this way must not belong to a
+ * gp_multi.  The values, moments and loss slots equal those of gp_step (same
+ * records, weights and flags) then gp_update with the same hyper-parameters,
+ * bit for bit with GP_STEP_DETERMINISTIC, to float rounding otherwise.
+ * flags: GP_STEP_DETERMINISTIC and/or GP_STEP_NO_TV.  Never allocates; the
+ * swap is a host-side pointer exchange, so a CUDA graph must capture two
+ * consecutive calls.  Errors: GP_ERR_ARG (as gp_step, step < 1, null hp, other
+ * flags), GP_ERR_STATE (deterministic flag without GP_BAND_DETERMINISTIC,
+ * empty band). */
+gp_status gp_step_update(gp_band* band, const float* rec_dev, int64_t B, const int32_t* nvalid_dev,
+                         const gp_loss_w* w, const gp_adam* hp, int64_t step, float* loss_dev, uint32_t flags);
 
 /* ------------------------------------------------------------------ mesh */
 

@@ -90,6 +90,8 @@ SIGNATURES = {
     "gp_nn_work": (ctypes.c_int, [_vp, _vp, _i64, _vp, _vp, ctypes.POINTER(_i64)]),
     "gp_step": (ctypes.c_int, [_vp, _vp, _i64, _vp, _vp, ctypes.POINTER(LossW), _vp, _vp, _u32]),
     "gp_update": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(Adam), _i64]),
+    "gp_step_update": (ctypes.c_int, [_vp, _vp, _i64, _vp, ctypes.POINTER(LossW), ctypes.POINTER(Adam), _i64, _vp,
+                                      _u32]),
     "gp_band_set_query_tiles": (ctypes.c_int, [_vp, _i32, _i32]),
     "gp_band_autotune": (ctypes.c_int, [_vp, _vp, _i64, _vp, ctypes.POINTER(LossW), ctypes.POINTER(_i32),
                                         ctypes.POINTER(_i32)]),
@@ -456,6 +458,21 @@ def gp_band_autotune(band: Band, rec, B: int, weights=(1.0, 1.0, 0.005), nvalid=
     band.ctx.check(band.ctx.lib.gp_band_autotune(band.handle, _ptr(rec), int(B), _ptr(nvalid), ctypes.byref(w),
                                                  ctypes.byref(rpt), ctypes.byref(bps)))
     return {"records_per_thread": rpt.value, "blocks_per_sm": bps.value}
+
+
+def gp_step_update(band: Band, rec, B: int, loss, lr: float, step: int, weights=(1.0, 1.0, 0.005), nvalid=None,
+                   flags: int = 0, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8):
+    """gp_step then gp_update in one call without a gradient array; the band's
+    value buffer alternates (gp_band_values gives the current one)."""
+    import torch
+    _need(rec, torch.float32, 6 * B, "records")
+    _need(loss, torch.float32, 8, "loss")
+    _need(nvalid, torch.int32, 1, "nvalid")
+    w = LossW(*[float(x) for x in weights])
+    hp = Adam(float(lr), float(beta1), float(beta2), float(eps))
+    band.ctx.sync_stream()
+    band.ctx.check(band.ctx.lib.gp_step_update(band.handle, _ptr(rec), int(B), _ptr(nvalid), ctypes.byref(w),
+                                               ctypes.byref(hp), int(step), _ptr(loss), int(flags)))
 
 
 def gp_band_set_query_tiles(band: Band, records_per_thread: int, blocks_per_sm: int):

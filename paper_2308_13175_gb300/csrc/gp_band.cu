@@ -257,6 +257,8 @@ void band_free(gp_band* b) {
   gp_free(b->m);
   gp_free(b->v);
   gp_free(b->acc);
+  gp_free(b->D_alt);
+  gp_free(b->qgrad);
   gp_free(b->pts);
   gp_free(b->pts_sorted);
   gp_free(b->cell_start);
@@ -404,6 +406,8 @@ extern "C" gp_status gp_build_band(gp_ctx* ctx, const float* pts_dev, int64_t J,
   if (!st) st = gp_alloc(ctx, &b->m, V, "adam m");
   if (!st) st = gp_alloc(ctx, &b->v, V, "adam v");
   if (!st && (b->flags & GP_BAND_DETERMINISTIC)) st = gp_alloc(ctx, &b->acc, 2 * V, "fixed-point accumulator");
+  if (!st) st = gp_alloc(ctx, &b->D_alt, V, "second value buffer");
+  if (!st) st = gp_alloc(ctx, &b->qgrad, V, "query gradient");
   if (!st) st = gp_alloc(ctx, &b->partials, (size_t)GP_MAX_PARTIAL_BLOCKS * 8, "partials");
   if (!st) st = gp_alloc(ctx, &b->dev_ints, GP_DI_COUNT, "device ints");
   if (!st) {
@@ -412,6 +416,8 @@ extern "C" gp_status gp_build_band(gp_ctx* ctx, const float* pts_dev, int64_t J,
     if (e == cudaSuccess) e = cudaMemsetAsync(b->m, 0, V * sizeof(float), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->v, 0, V * sizeof(float), s);
     if (e == cudaSuccess && b->acc) e = cudaMemsetAsync(b->acc, 0, 2 * V * sizeof(unsigned long long), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->D_alt, 0, V * sizeof(float), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->qgrad, 0, V * sizeof(float), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->dev_ints, 0, GP_DI_COUNT * sizeof(int32_t), s);
     if (e != cudaSuccess) st = gp_cuda_fail(ctx, e, "gp_build_band: memset");
   }

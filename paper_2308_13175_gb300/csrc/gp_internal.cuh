@@ -75,6 +75,8 @@ struct gp_band {
   float* m = nullptr;              // Adam first moment
   float* v = nullptr;              // Adam second moment
   unsigned long long* acc = nullptr;  // deterministic two-word fixed-point gradient (2 x V_stored)
+  float* D_alt = nullptr;          // second value buffer: gp_step_update writes the new values here, then swaps
+  float* qgrad = nullptr;          // query part of the gradient for gp_step_update, all zero between calls
 
   // Point cloud: original order copy, cell list sorted copy, sigma, permutation.
   float* pts = nullptr;            // J x 3

@@ -289,6 +289,110 @@ __global__ void __launch_bounds__(TV_THREADS, TV_BLOCKS_PER_SM) k_tv(Grid G, con
   (void)err;
 }
 
+// Adam's hyper-parameters for one step, with the bias corrections.
+struct AdamArgs {
+  float lr, b1, b2, eps, bc1, bc2;
+};
+
+// L_TV and Adam in one sweep over the bricks (gp_step_update), after the
+// query pass has added its contributions into qgrad (or, DET, into the
+// fixed-point sums).  For every stored vertex of the brick: the gradient is
+// alpha/|T| dTV/dd + the query part (which is read and reset to zero); a
+// trainable vertex gets Adam's update, written to Dnext with its moments; any
+// other vertex is copied to Dnext unchanged.  Reading the stencil from D and
+// writing Dnext keeps every brick's neighbours at the step's values; the
+// caller swaps the two buffers afterwards.  Each TV_i enters the loss once.
+template <bool DET, bool TV>
+__global__ void __launch_bounds__(TV_THREADS, TV_BLOCKS_PER_SM) k_tv_adam(
+    Grid G, const int32_t* __restrict__ coord, const int32_t* __restrict__ nbrs, int64_t n_bricks, float tv_scale,
+    float* __restrict__ qgrad, unsigned long long* __restrict__ acc, const int32_t* __restrict__ bv,
+    float* __restrict__ Dnext, float* __restrict__ m, float* __restrict__ v, AdamArgs ad,
+    double* __restrict__ partials, int32_t* __restrict__ err, FinalArgs fa) {
+  __shared__ TvShared sh;
+  float tsum = 0.f;
+  float qscale_f = 0.f;
+  if (DET) {
+    const int b = *bv;
+    qscale_f = b > 0 ? 1.0f / (float)b : 0.f;
+  }
+  // This thread's two vertices of every brick (those tv_gather hands it), and
+  // their Adam operands, loaded at the top of the brick's iteration.
+  const int tt = threadIdx.x;
+  const int lv[2] = {(tt & 7) + 16 * ((tt >> 3) & 3) + 64 * (tt >> 5), (tt & 7) + 16 * ((tt >> 3) & 3) + 64 * (tt >> 5) + 8};
+  float pd[2], pm[2], pv[2], pq[2];
+  uint32_t pw[2];
+  auto load = [&](int64_t slot, int k, int l) {
+    const int64_t addr = slot * 512 + l;
+    pd[k] = __ldg(G.D + addr);
+    pw[k] = __ldg(G.masks + slot * 48 + 16 + (l >> 5));
+    if ((pw[k] >> (l & 31)) & 1u) {
+      pm[k] = m[addr];
+      pv[k] = v[addr];
+      if (DET) {
+        const long long hi = (long long)acc[2 * addr], lo = (long long)acc[2 * addr + 1];
+        const float qv =
+            __fmaf_rn(__ll2float_rn(hi), 9.5367431640625e-07f, __ll2float_rn(lo) * 8.673617379884035e-19f);
+        pq[k] = qv;  // scaled by 1/B_v in update(), as k_tv's fold does
+      } else {
+        pq[k] = qgrad[addr];
+      }
+    }
+  };
+  auto update = [&](int64_t slot, int k, int l, float g_tv) {
+    const int64_t addr = slot * 512 + l;
+    if (!((pw[k] >> (l & 31)) & 1u)) {
+      Dnext[addr] = pd[k];
+      return;
+    }
+    float g;
+    if (DET) {
+      acc[2 * addr] = 0ull;
+      acc[2 * addr + 1] = 0ull;
+      g = __fmaf_rn(pq[k], qscale_f, tv_scale * g_tv);
+    } else {
+      qgrad[addr] = 0.f;
+      g = tv_scale * g_tv + pq[k];
+    }
+    const float mm = fmaf(ad.b1, pm[k], (1.0f - ad.b1) * g);
+    const float vv = fmaf(ad.b2, pv[k], (1.0f - ad.b2) * g * g);
+    m[addr] = mm;
+    v[addr] = vv;
+    const float mh = mm / ad.bc1, vh = vv / ad.bc2;
+    Dnext[addr] = pd[k] - ad.lr * mh / (sqrtf(vh) + ad.eps);
+  };
+  if (TV) {
+    tv_sweep(
+        BandTvSrc{G, coord, nbrs}, blockIdx.x, gridDim.x, n_bricks, sh,
+        [&](int64_t slot, int l0, float g0, int l1, float g1, float ts) {
+          tsum += ts;
+          update(slot, 0, l0, g0);
+          update(slot, 1, l1, g1);
+        },
+        [&](int64_t slot) {
+          load(slot, 0, lv[0]);
+          load(slot, 1, lv[1]);
+        });
+  } else {
+    for (int64_t slot = blockIdx.x; slot < n_bricks; slot += gridDim.x) {
+      load(slot, 0, threadIdx.x);
+      load(slot, 1, threadIdx.x + 256);
+      update(slot, 0, threadIdx.x, 0.f);
+      update(slot, 1, threadIdx.x + 256, 0.f);
+    }
+  }
+  __shared__ float red[TV_THREADS / 32];
+  const float wsum = gp_warp_sum(tsum);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = wsum;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sum = 0;
+    for (int k = 0; k < TV_THREADS / 32; ++k) sum += red[k];
+    partials[(int64_t)blockIdx.x * 8 + 3] = sum;
+  }
+  finish_if_last(partials, fa);
+  (void)err;
+}
+
 // One thread per 4 consecutive vertices of an active brick (128 per brick).
 __global__ void __launch_bounds__(256) k_adam(const int32_t* __restrict__ active, int64_t n_active,
                                               const uint32_t* __restrict__ masks, const float* __restrict__ grad,
@@ -537,5 +641,86 @@ extern "C" gp_status gp_band_set_query_tiles(gp_band* b, int32_t rpt, int32_t bp
     return gp_fail(b->ctx, GP_ERR_ARG, "gp_band_set_query_tiles: rpt must be 1 or 2 and bps 2, 3 or 4");
   b->q_rpt = rpt;
   b->q_bps = bps;
+  return GP_OK;
+}
+
+extern "C" gp_status gp_step_update(gp_band* b, const float* rec_dev, int64_t B, const int32_t* nvalid_dev,
+                                    const gp_loss_w* w, const gp_adam* hp, int64_t step, float* loss_dev,
+                                    uint32_t flags) {
+  if (!b) return GP_ERR_ARG;
+  gp_ctx* ctx = b->ctx;
+  if (B < 0 || B >= (int64_t(1) << 31)) return gp_fail(ctx, GP_ERR_ARG, "gp_step_update: B must be in [0, 2^31)");
+  if (!loss_dev || !w || !hp || (B > 0 && !rec_dev)) return gp_fail(ctx, GP_ERR_ARG, "gp_step_update: null pointer");
+  if (step < 1) return gp_fail(ctx, GP_ERR_ARG, "gp_step_update: step must be >= 1");
+  if (flags & ~(GP_STEP_DETERMINISTIC | GP_STEP_NO_TV))
+    return gp_fail(ctx, GP_ERR_ARG, "gp_step_update: flags may only be GP_STEP_DETERMINISTIC and GP_STEP_NO_TV");
+  const bool det = (flags & GP_STEP_DETERMINISTIC) != 0;
+  const bool tv_on = !(flags & GP_STEP_NO_TV);
+  if (((uintptr_t)rec_dev & 7u) != 0) return gp_fail(ctx, GP_ERR_ARG, "gp_step_update: records must be 8-byte aligned");
+  if (det && !b->acc)
+    return gp_fail(ctx, GP_ERR_STATE,
+                   "gp_step_update: deterministic mode needs a band built with GP_BAND_DETERMINISTIC");
+  if (b->n_bricks == 0) return gp_fail(ctx, GP_ERR_STATE, "gp_step_update: empty band");
+  cudaStream_t s = ctx->stream;
+  Grid G;
+  G.table = b->brick_table;
+  G.masks = b->masks;
+  G.D = b->D;
+  G.nb = b->nb;
+  G.R = b->R;
+  G.half_r = 0.5f * (float)b->R;
+  int32_t* err = b->dev_ints + GP_DI_ERROR;
+  const int32_t* bv = nvalid_dev;
+  if (!bv) {
+    int32_t* cnt = b->dev_ints + GP_DI_NVALID;
+    GP_CUDA(ctx, cudaMemsetAsync(cnt, 0, sizeof(int32_t), s));
+    if (B > 0) {
+      GP_KERNEL(ctx, "k_count_valid", k_count_valid<<<q_grid(ctx, B), Q_THREADS, 0, s>>>(G, rec_dev, B, cnt));
+    }
+    bv = cnt;
+  }
+  const unsigned tb = tv_grid(ctx, b->n_bricks);
+  FinalArgs fa;
+  fa.done = b->dev_ints + GP_DI_DONE;
+  fa.q_blocks = 0;
+  fa.tv_blocks = (int)tb;
+  fa.bv = bv;
+  fa.n_tv = b->V_tv;
+  fa.alpha = w->alpha;
+  fa.beta = w->beta;
+  fa.gamma = w->gamma;
+  fa.tv_on = tv_on ? 1 : 0;
+  fa.loss = loss_dev;
+  // The query pass: its contributions into the band's zeroed query gradient
+  // (or the fixed-point sums); its block sums are finished by the sweep.
+  gp_prof_pre(ctx);
+  cudaError_t e = det ? launch_query_tuned<true, false>(b, B, s, G, rec_dev, bv, w->beta, w->gamma, b->qgrad,
+                                                        b->partials, err, fa)
+                      : launch_query_tuned<false, false>(b, B, s, G, rec_dev, bv, w->beta, w->gamma, b->qgrad,
+                                                         b->partials, err, fa);
+  gp_prof_post(ctx, "k_query");
+  if (e != cudaSuccess) return gp_cuda_fail(ctx, e, "k_query");
+  GP_LAUNCH_CHECK(ctx, "k_query");
+  AdamArgs ad;
+  ad.lr = hp->lr;
+  ad.b1 = hp->beta1;
+  ad.b2 = hp->beta2;
+  ad.eps = hp->eps;
+  ad.bc1 = (float)(1.0 - std::pow((double)hp->beta1, (double)step));
+  ad.bc2 = (float)(1.0 - std::pow((double)hp->beta2, (double)step));
+  const float tv_scale = (tv_on && b->V_tv > 0) ? w->alpha / (float)b->V_tv : 0.f;
+  gp_prof_pre(ctx);
+#define GP_TVA(D_, T_)                                                                                             \
+  k_tv_adam<D_, T_><<<tb, TV_THREADS, 0, s>>>(G, b->brick_coord, b->brick_nbr, b->n_bricks, tv_scale, b->qgrad,  \
+                                              b->acc, bv, b->D_alt, b->m, b->v, ad, b->partials, err, fa)
+  if (det) {
+    if (tv_on) GP_TVA(true, true); else GP_TVA(true, false);
+  } else {
+    if (tv_on) GP_TVA(false, true); else GP_TVA(false, false);
+  }
+#undef GP_TVA
+  gp_prof_post(ctx, "k_tv_adam");
+  GP_LAUNCH_CHECK(ctx, "k_tv_adam");
+  std::swap(b->D, b->D_alt);
   return GP_OK;
 }

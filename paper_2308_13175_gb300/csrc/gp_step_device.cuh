@@ -622,9 +622,16 @@ __device__ __forceinline__ void tv_gather(const TvShared& sh, int p, const TvBri
 // by every thread once per item, in order, with the unscaled dTV/dd of the
 // thread's two vertices l0, l1 (tv_gather) and its share of the item's sum of
 // TV_i; it may synchronise the block.
-template <class Src, class Out>
+struct TvNoPre {
+  __device__ __forceinline__ void operator()(int64_t) const {}
+};
+
+// pre(i) (optional) is called by every thread at the top of item i's
+// iteration, while the item's halo copies are still in flight: a place to
+// issue loads whose latency the stencil work then hides.
+template <class Src, class Out, class Pre = TvNoPre>
 __device__ __forceinline__ void tv_sweep(const Src& src, int64_t first, int64_t stride, int64_t n, TvShared& sh,
-                                         Out&& out) {
+                                         Out&& out, Pre&& pre = Pre()) {
   const int l = threadIdx.x;
   if (first >= n) return;
   const TvPlan pl = tv_plan();
@@ -641,6 +648,7 @@ __device__ __forceinline__ void tv_sweep(const Src& src, int64_t first, int64_t 
   }
   int p = 0;
   for (int64_t i = first; i < n; i += stride) {
+    pre(i);
     __syncthreads();  // the previous item is done with buffer p ^ 1 and inv; bk / slot[p ^ 1] written
     const int64_t next = i + stride, after = next + stride;
     if (next < n) tv_issue(sh, p ^ 1, pl);

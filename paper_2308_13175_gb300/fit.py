@@ -23,13 +23,18 @@ PAPER_WEIGHTS = (1.0, 1.0, 0.005)
 
 class FitStep:
     def __init__(self, band: gb.Band, Q: int, B: int, seed: int = 0, weights=PAPER_WEIGHTS, lr: float = 1e-3,
-                 lr_decay: float = 1.0, lr_every: int = 0, deterministic: bool = False):
+                 lr_decay: float = 1.0, lr_every: int = 0, deterministic: bool = False, fused=None):
         self.band = band
         self.Q, self.B = int(Q), int(min(B, Q))
         self.seed = int(seed)
         self.weights = tuple(float(w) for w in weights)
         self.lr, self.lr_decay, self.lr_every = float(lr), float(lr_decay), int(lr_every)
         self.flags = gb.GP_STEP_DETERMINISTIC if deterministic else 0
+        # fused: gp_step_update (no gradient array); else gp_step then gp_update.
+        # Default: fused for the deterministic sums (its sweep folds them in at
+        # no extra pass; measured 1.6x faster there), separate otherwise (the
+        # two forms measured within 5% of each other).
+        self.fused = bool(deterministic) if fused is None else bool(fused)
         self.batches_per_epoch = math.ceil(self.Q / self.B)
         dev = torch.device("cuda", band.ctx.device)
         self.device = dev
@@ -75,6 +80,10 @@ class FitStep:
 
     def _descend(self, t: int, buf: dict, count: int):
         """Eq. 8 forward and backward on buf's records, then Adam."""
+        if self.fused:
+            gb.gp_step_update(self.band, buf["rec"], count, self.loss, self.lr_at(t), t + 1, self.weights,
+                              nvalid=buf["nvalid"], flags=self.flags)
+            return
         gb.gp_step(self.band, buf["rec"], count, self.grad, self.loss, self.weights, nvalid=buf["nvalid"],
                    flags=self.flags)
         gb.gp_update(self.band, self.grad, self.lr_at(t), t + 1)

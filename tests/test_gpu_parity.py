@@ -638,7 +638,7 @@ def test_pipelined_steps_equal_sequential_steps(gb, ctx, sphere5k):
         band = _band(gb, ctx, sphere5k, R, 2, 2, knn_k=50, deterministic=True)
         gb.gp_band_init_sphere(band, (0.0, 0.0, 0.0), 0.45, 0.01, seed=5)
         bands.append(band)
-        fits.append(FitStep(band, Q=40_000, B=15_000, seed=3, lr=1e-3, deterministic=True))
+        fits.append(FitStep(band, Q=40_000, B=15_000, seed=3, lr=1e-3, deterministic=True, fused=True))
     K = 7
     for t in range(K):
         fits[0].run(t)
@@ -653,4 +653,49 @@ def test_pipelined_steps_equal_sequential_steps(gb, ctx, sphere5k):
     fits[1].run_pipelined(K, 3)
     torch.cuda.synchronize()
     assert torch.equal(gb.gp_band_values(bands[0])[0], gb.gp_band_values(bands[1])[0])
+    gb.gp_band_check(bands[1])
+
+
+@pytest.mark.parametrize("det", [False, True])
+def test_step_update_equals_step_then_update(gb, ctx, object100k, det):
+    """gp_step_update (query pass, then one sweep computing L_TV, adding the
+    query part and applying Adam into the second value buffer) against
+    gp_step then gp_update on an identical band: values, moments and loss
+    slots over three steps - bit for bit with the deterministic sums."""
+    import torch
+    R = 256
+    bands = [_band(gb, ctx, object100k, R, 2, 2, knn_k=0, deterministic=det) for _ in range(2)]
+    c = 0.5 * (object100k.min(0) + object100k.max(0))
+    sets, q, s = _step_inputs(object100k, R, 2, 2, 80_000, 2.0 / R, seed=31, use_nn=False)
+    for band in bands:
+        _set_field(gb, band, sets, R, 0.3, 2e-3, seed=32, center=c)
+    rec = torch.from_numpy(np.ascontiguousarray(np.concatenate([q, s], axis=1), np.float32)).cuda()
+    flags = gb.GP_STEP_DETERMINISTIC if det else 0
+    grad = torch.empty(bands[0].V_stored, dtype=torch.float32, device="cuda")
+    la = torch.zeros(8, dtype=torch.float32, device="cuda")
+    lb = torch.zeros(8, dtype=torch.float32, device="cuda")
+    w = (1.0, 1.0, 0.005)
+    d0 = gb.gp_band_values(bands[0])[0].clone()
+    for t in range(1, 4):
+        gb.gp_step(bands[0], rec, len(q), grad, la, w, flags=flags)
+        gb.gp_update(bands[0], grad, 1e-3, t)
+        gb.gp_step_update(bands[1], rec, len(q), lb, 1e-3, t, w, flags=flags)
+        torch.cuda.synchronize()
+        va, vb = gb.gp_band_values(bands[0]), gb.gp_band_values(bands[1])
+        if det:
+            assert torch.equal(la, lb)
+            for x, y in zip(va, vb):
+                assert torch.equal(x, y)
+        else:
+            for k in range(5):
+                assert_rel(lb[k].item(), la[k].item(), what=f"slot {k} step {t}")
+            # Float sums in different orders: moments norm-wise to 1e-5; the
+            # value changes norm-wise to 1e-3 (Adam's m / sqrt(v) amplifies the
+            # rounding of gradients that nearly cancel).
+            for x, y, name in zip(va[1:], vb[1:], ("m", "v")):
+                assert float(torch.linalg.norm(x - y)) <= 1e-5 * float(torch.linalg.norm(x)), (name, t)
+            da, db = va[0] - d0, vb[0] - d0
+            assert float(torch.linalg.norm(da - db)) <= 1e-3 * float(torch.linalg.norm(da)), t
+    # The query gradient is left all zero; the second buffer's frozen values
+    # equal the current ones.
     gb.gp_band_check(bands[1])
