@@ -596,7 +596,7 @@ def run_ours(args, world, rank, local):
     # trainable-mask words once (the +1 apron re-reads are overhead), plus the
     # 36-byte triangles the emit pass writes.
     mesh = None
-    if rank == 0 and not args.deterministic:
+    if rank == 0 and not args.deterministic and not args.no_mesh:
         # A field worth meshing: every stored vertex gets its exact distance
         # to the cloud (gp_nn on the vertex positions) less half a cell, whose
         # zero set is a thin closed sheet around the points - the shape a
@@ -937,6 +937,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-torch", action="store_true", help="skip the plain PyTorch autograd comparison")
     ap.add_argument("--nn-grid", type=int, default=0, help="cells per axis of the point cell list (0 = automatic)")
+    ap.add_argument("--no-mesh", action="store_true", help="skip the surface-extraction and metrics leg")
     ap.add_argument("--no-pipeline", action="store_true",
                     help="time the sequential steps (L2 flushed between them) as the headline")
     ap.add_argument("--deterministic", action="store_true",
