@@ -31,13 +31,18 @@ def _nn(path: str):
     """Brute-force NN(q) of one chunk of queries over the whole cloud."""
     q = np.load(path)
     t = time.perf_counter()
-    o.nearest_point(q, np.asarray(_POINTS), chunk=8)
+    o.nearest_point(q, np.asarray(_POINTS), chunk=_chunk(len(_POINTS)))
     return time.perf_counter() - t
+
+
+def _chunk(J: int) -> int:
+    """Queries per brute-force block: about 4e7 distances (a few hundred MB)."""
+    return int(max(8, min(512, 4e7 // max(J, 1))))
 
 
 def _nn_idx(path: str):
     """Brute-force NN(q) indices of one chunk of queries."""
-    return o.nearest_point(np.load(path), np.asarray(_POINTS), chunk=8)
+    return o.nearest_point(np.load(path), np.asarray(_POINTS), chunk=_chunk(len(_POINTS)))
 
 
 def _sigma(args):
