@@ -806,7 +806,7 @@ def run_collection(args, world, rank, local):
         Q = wl["q_per_point"] * len(pts)
         Qs.append(Q)
         Bs.append(-(-Q // wl["batches_per_epoch"]))
-    multi = gb.gp_multi_create(ctx, bands, Qs, Bs, seed=rank, spatial=True)
+    multi = gb.gp_multi_create(ctx, bands, Qs, Bs, seed=rank, spatial=True, deterministic=args.deterministic)
     n = len(bands)
     loss = torch.zeros(8 * n, dtype=torch.float32, device="cuda")
     tune = gb.gp_multi_autotune(multi, PAPER_WEIGHTS)
@@ -913,7 +913,9 @@ def run_collection(args, world, rank, local):
                           "V_stored": Vs, "V_trainable": Vt, "autotuned": {k: tune[k] for k in (
                               "records_per_tile", "blocks_per_sm_nn", "blocks_per_sm_tv", "blocks_per_sm_query")},
                           "l2": "flushed between timed steps (256 MB write outside the step events)",
-                          "timed": "CUDA graph replays of one captured gp_multi_step"},
+                          "timed": "CUDA graph replays of one captured gp_multi_step",
+                          "gradient_sum": "deterministic two-word fixed point" if args.deterministic
+                          else "float atomics"},
                "roofline": roofline, "cpu_baseline": None,
                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 32 * n},
                "gpu_launches": int(per_step_launches * args.steps), "clocks": clk, "kernels": per_kernel,

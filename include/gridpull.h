@@ -441,10 +441,17 @@ typedef struct gp_multi_info {
   int64_t step;                 /* t, the next step to run                     */
 } gp_multi_info;
 
+#define GP_MULTI_DETERMINISTIC 2u /* gp_multi_create: bitwise repeatable steps -
+                                     the query sums in two-word integer fixed
+                                     point (folded in by the L_TV sweep, which
+                                     then runs after the query pass) and the
+                                     loss sums in integers of 2^-24           */
+
 /* Bands: n distinct bands of ctx, built with knn_k > 0 and without
  * GP_BAND_DETERMINISTIC; they must outlive the multi.  Q[k], B[k]: pool size
  * and batch size of cloud k, 1 <= B[k] <= Q[k] < 2^31, sum of B[k] < 2^31.
- * flags: 0 or GP_SAMPLE_SPATIAL.  Allocates the multi's buffers (the
+ * flags: GP_SAMPLE_SPATIAL and/or GP_MULTI_DETERMINISTIC (which allocates 16
+ * more bytes per stored vertex).  Allocates the multi's buffers (the
  * dominant ones: 36 bytes per record slot, 4 bytes per stored vertex, 8 bytes
  * per point) and synchronises.  t starts at 0.  Errors: GP_ERR_ARG,
  * GP_ERR_OOM, GP_ERR_CUDA. */

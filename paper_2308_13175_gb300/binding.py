@@ -21,6 +21,7 @@ GP_STEP_DETERMINISTIC = 1
 GP_STEP_NO_TV = 2
 GP_STEP_LOSS_ONLY = 4
 GP_SAMPLE_SPATIAL = 1
+GP_MULTI_DETERMINISTIC = 2
 GP_LOSS_TOTAL, GP_LOSS_PULL, GP_LOSS_GRAD, GP_LOSS_SURF, GP_LOSS_TV, GP_LOSS_BV, GP_LOSS_T = range(7)
 
 STATUS_NAMES = {0: "GP_OK", 1: "GP_ERR_ARG", 2: "GP_ERR_OOM", 3: "GP_ERR_CUDA", 4: "GP_ERR_TIMEOUT",
@@ -530,15 +531,16 @@ class Multi:
             pass
 
 
-def gp_multi_create(ctx: Context, bands, Q, B, seed: int = 0, spatial: bool = True) -> Multi:
+def gp_multi_create(ctx: Context, bands, Q, B, seed: int = 0, spatial: bool = True,
+                    deterministic: bool = False) -> Multi:
     n = len(bands)
     arr = (_vp * n)(*[b.handle for b in bands])
     qa = (_i64 * n)(*[int(x) for x in Q])
     ba = (_i64 * n)(*[int(x) for x in B])
     out = _vp()
     ctx.sync_stream()
-    ctx.check(ctx.lib.gp_multi_create(ctx.handle, arr, n, qa, ba, int(seed), GP_SAMPLE_SPATIAL if spatial else 0,
-                                      ctypes.byref(out)))
+    flags = (GP_SAMPLE_SPATIAL if spatial else 0) | (GP_MULTI_DETERMINISTIC if deterministic else 0)
+    ctx.check(ctx.lib.gp_multi_create(ctx.handle, arr, n, qa, ba, int(seed), flags, ctypes.byref(out)))
     return Multi(ctx, out, bands, Q, B)
 
 

@@ -41,6 +41,7 @@ struct MShape {
   float* m;
   float* v;
   float* grad;  // this cloud's slice of the gradient buffer
+  unsigned long long* acc;  // its slice of the fixed-point query sums (deterministic multis), else null
   const float* pts;
   const float* sigma;
   const float* normals;
@@ -297,6 +298,20 @@ __device__ __forceinline__ float block_sum(float v, float* red) {
   return s;
 }
 
+// Loss sums of the deterministic mode: a block's float sum as an integer in
+// units of 2^-24 (integer additions do not depend on their order).
+__device__ __forceinline__ long long loss_fixed(float x) { return __double2ll_rn((double)x * 16777216.0); }
+
+// g + (hi 2^-20 + lo 2^-60) * scale from a two-word fixed-point sum, which is
+// cleared (the fold of gp_step's deterministic mode).
+__device__ __forceinline__ float fold_fixed(unsigned long long* a, float scale, float g) {
+  const long long hi = (long long)a[0], lo = (long long)a[1];
+  a[0] = 0ull;
+  a[1] = 0ull;
+  const float qv = __fmaf_rn(__ll2float_rn(hi), 9.5367431640625e-07f, __ll2float_rn(lo) * 8.673617379884035e-19f);
+  return __fmaf_rn(qv, scale, g);
+}
+
 struct MultiTvSrc {
   const MShape* shapes;
   const MTile* tiles;
@@ -313,16 +328,27 @@ struct MultiTvSrc {
 // the block's tiles); the gradient is overwritten at every slot of every
 // brick; the TV sums go to each cloud's slot 3, one atomic per run of tiles of
 // the same cloud.
+// DET: the query pass ran first into the fixed-point sums, which are folded
+// in here (scaled by 1/B_v of the cloud) and cleared; the TV sums go to the
+// integer loss sums.
+template <bool DET>
 __global__ void __launch_bounds__(TV_SWEEP_THREADS, TV_BLOCKS_PER_SM) k_m_tv(const MShape* __restrict__ shapes,
                                                            const MTile* __restrict__ tiles, int64_t ntiles,
-                                                           float alpha, double* __restrict__ sums) {
+                                                           float alpha, double* __restrict__ sums,
+                                                           long long* __restrict__ isums,
+                                                           const int32_t* __restrict__ nvalid) {
   __shared__ TvShared sh;
   __shared__ float red[32];
   int cur = -1;
   float acc = 0.f;
   auto flush = [&]() {
     const float bs = block_sum(acc, red);
-    if (threadIdx.x == 0 && bs != 0.f) atomicAdd(sums + 4 * cur + 3, (double)bs);
+    if (threadIdx.x == 0 && bs != 0.f) {
+      if (DET)
+        atomicAdd((unsigned long long*)(isums + 4 * cur + 3), (unsigned long long)loss_fixed(bs));
+      else
+        atomicAdd(sums + 4 * cur + 3, (double)bs);
+    }
     acc = 0.f;
   };
   tv_sweep(MultiTvSrc{shapes, tiles}, blockIdx.x, gridDim.x, ntiles, sh,
@@ -336,8 +362,16 @@ __global__ void __launch_bounds__(TV_SWEEP_THREADS, TV_BLOCKS_PER_SM) k_m_tv(con
              acc += ts;
              const float tv_scale = S.V_tv > 0 ? alpha / (float)S.V_tv : 0.f;
              float* gp = S.grad + (int64_t)tl.first * 512;
-             gp[l0] = tv_scale * g0;
-             gp[l1] = tv_scale * g1;
+             if (DET) {
+               const int bv = nvalid[tl.shape];
+               const float qscale = bv > 0 ? 1.0f / (float)bv : 0.f;
+               unsigned long long* ap = S.acc + 2 * (int64_t)tl.first * 512;
+               gp[l0] = fold_fixed(ap + 2 * l0, qscale, tv_scale * g0);
+               gp[l1] = fold_fixed(ap + 2 * l1, qscale, tv_scale * g1);
+             } else {
+               gp[l0] = tv_scale * g0;
+               gp[l1] = tv_scale * g1;
+             }
            });
   if (cur >= 0) flush();
 }
@@ -345,10 +379,12 @@ __global__ void __launch_bounds__(TV_SWEEP_THREADS, TV_BLOCKS_PER_SM) k_m_tv(con
 // Fused forward + hand-written backward of every valid record (the gp_step
 // record code), loss sums per cloud.  At most 256 threads, so that the record
 // code keeps its registers (at 512 it would spill).
+template <bool DET>
 __global__ void __launch_bounds__(256) k_m_query(const MShape* __restrict__ shapes, const MTile* __restrict__ tiles,
                                                  int64_t ntiles, int tq, const float* __restrict__ rec,
                                                  const int32_t* __restrict__ nvalid, float beta, float gamma,
-                                                 double* __restrict__ sums, int32_t* __restrict__ err) {
+                                                 double* __restrict__ sums, long long* __restrict__ isums,
+                                                 int32_t* __restrict__ err) {
   __shared__ float red[32];
   // Loss sums stay in registers over a block's run of tiles of one cloud and
   // are reduced over the block when the cloud changes and at the end.
@@ -359,9 +395,16 @@ __global__ void __launch_bounds__(256) k_m_query(const MShape* __restrict__ shap
     const float b = block_sum(sg, red);
     const float c = block_sum(ss, red);
     if (threadIdx.x == 0) {
-      if (a != 0.f) atomicAdd(sums + 4 * cur + 0, (double)a);
-      if (b != 0.f) atomicAdd(sums + 4 * cur + 1, (double)b);
-      if (c != 0.f) atomicAdd(sums + 4 * cur + 2, (double)c);
+      if (DET) {
+        unsigned long long* is = (unsigned long long*)(isums + 4 * cur);
+        if (a != 0.f) atomicAdd(is + 0, (unsigned long long)loss_fixed(a));
+        if (b != 0.f) atomicAdd(is + 1, (unsigned long long)loss_fixed(b));
+        if (c != 0.f) atomicAdd(is + 2, (unsigned long long)loss_fixed(c));
+      } else {
+        if (a != 0.f) atomicAdd(sums + 4 * cur + 0, (double)a);
+        if (b != 0.f) atomicAdd(sums + 4 * cur + 1, (double)b);
+        if (c != 0.f) atomicAdd(sums + 4 * cur + 2, (double)c);
+      }
     }
     sp = sg = ss = 0.f;
   };
@@ -373,12 +416,12 @@ __global__ void __launch_bounds__(256) k_m_query(const MShape* __restrict__ shap
       cur = tl.shape;
     }
     const int bv = nvalid[tl.shape];
-    const float w = bv > 0 ? 1.0f / (float)bv : 0.f;
+    const float w = DET ? 1.0f : (bv > 0 ? 1.0f / (float)bv : 0.f);  // fixed-point sums: 1/B_v at the fold
     const int64_t end = min((int64_t)tl.first + tq, S.B);
     for (int64_t i = (int64_t)tl.first + threadIdx.x; i < end; i += blockDim.x) {
       float qq[3], s3[3];
       load_rec(rec, S.rec_off + i, qq, s3);
-      query_record<false, true>(S.G, qq, s3, w, beta, gamma, S.grad, nullptr, err, sp, sg, ss);
+      query_record<DET, true>(S.G, qq, s3, w, beta, gamma, S.grad, S.acc, err, sp, sg, ss);
     }
   }
   if (cur >= 0) flush();
@@ -406,13 +449,19 @@ __global__ void __launch_bounds__(256) k_m_adam(const MShape* __restrict__ shape
 // Loss slots of every cloud from its sums; clears the sums and counts for the
 // next step, records the epoch of the stored orders and advances t.
 __global__ void k_m_finish(const MShape* __restrict__ shapes, int n, int32_t* __restrict__ nvalid,
-                           double* __restrict__ sums, int64_t* __restrict__ t_dev,
+                           double* __restrict__ sums, long long* __restrict__ isums, int64_t* __restrict__ t_dev,
                            int64_t* __restrict__ perm_epoch, float alpha, float beta, float gamma,
                            float* __restrict__ loss) {
   const int64_t t = *t_dev;
   for (int k = threadIdx.x; k < n; k += blockDim.x) {
     perm_epoch[k] = t / shapes[k].nb_epoch;
     const int bv = nvalid[k];
+    if (isums) {  // deterministic: the integer sums in units of 2^-24
+      for (int c = 0; c < 4; ++c) {
+        sums[4 * k + c] = (double)isums[4 * k + c] * (1.0 / 16777216.0);
+        isums[4 * k + c] = 0;
+      }
+    }
     const double* sk = sums + 4 * k;
     const double lp = bv > 0 ? sk[0] / bv : 0.0, lg = bv > 0 ? sk[1] / bv : 0.0, ls = bv > 0 ? sk[2] / bv : 0.0;
     const int64_t V_tv = shapes[k].V_tv;
@@ -454,6 +503,8 @@ struct gp_multi {
   int32_t *src = nullptr, *perm = nullptr, *inv = nullptr, *eslot = nullptr, *counts = nullptr, *nvalid = nullptr,
           *err = nullptr;
   double* sums = nullptr;
+  unsigned long long* acc = nullptr;  // deterministic: two-word fixed-point query sums over all clouds
+  long long* isums = nullptr;         // deterministic: integer loss sums (4 per cloud)
   int64_t* t = nullptr;
   int64_t* perm_epoch = nullptr;  // per cloud: epoch of the stored Pi_e (-1: none)
 };
@@ -465,7 +516,7 @@ void multi_free(gp_multi* m) {
   for (void* p : {(void*)m->shapes, (void*)m->rec_tiles, (void*)m->pt_tiles, (void*)m->brick_tiles,
                   (void*)m->active_tiles, (void*)m->q, (void*)m->rec, (void*)m->grad, (void*)m->src,
                   (void*)m->perm, (void*)m->inv, (void*)m->eslot, (void*)m->counts, (void*)m->nvalid, (void*)m->err,
-                  (void*)m->sums, (void*)m->t, (void*)m->perm_epoch})
+                  (void*)m->sums, (void*)m->acc, (void*)m->isums, (void*)m->t, (void*)m->perm_epoch})
     gp_free(p);
   delete m;
 }
@@ -507,19 +558,32 @@ gp_status launch_nn(gp_multi* m) {
 
 gp_status launch_tv(gp_multi* m, const gp_loss_w* w) {
   gp_ctx* ctx = m->ctx;
-  GP_KERNEL(ctx, "k_m_tv",
-            k_m_tv<<<persistent_grid(m, m->bpsm[ST_TV], m->n_brick_tiles), TV_SWEEP_THREADS, 0, ctx->stream>>>(
-                m->shapes, m->brick_tiles, m->n_brick_tiles, w->alpha, m->sums));
+  const unsigned grid = persistent_grid(m, m->bpsm[ST_TV], m->n_brick_tiles);
+  if (m->acc)
+    GP_KERNEL(ctx, "k_m_tv",
+              k_m_tv<true><<<grid, TV_SWEEP_THREADS, 0, ctx->stream>>>(m->shapes, m->brick_tiles, m->n_brick_tiles,
+                                                                       w->alpha, m->sums, m->isums, m->nvalid));
+  else
+    GP_KERNEL(ctx, "k_m_tv",
+              k_m_tv<false><<<grid, TV_SWEEP_THREADS, 0, ctx->stream>>>(m->shapes, m->brick_tiles, m->n_brick_tiles,
+                                                                        w->alpha, m->sums, m->isums, m->nvalid));
   return GP_OK;
 }
 
 gp_status launch_query(gp_multi* m, const gp_loss_w* w) {
   gp_ctx* ctx = m->ctx;
-  GP_KERNEL(ctx, "k_m_query",
-            k_m_query<<<persistent_grid(m, m->bpsm[ST_QUERY], m->n_rec_tiles), std::min(m->tq, 256), 0,
-                        ctx->stream>>>(
-                m->shapes, m->rec_tiles, m->n_rec_tiles, m->tq, m->rec, m->nvalid, w->beta, w->gamma, m->sums,
-                m->err));
+  const unsigned grid = persistent_grid(m, m->bpsm[ST_QUERY], m->n_rec_tiles);
+  const int threads = std::min(m->tq, 256);
+  if (m->acc)
+    GP_KERNEL(ctx, "k_m_query",
+              k_m_query<true><<<grid, threads, 0, ctx->stream>>>(m->shapes, m->rec_tiles, m->n_rec_tiles, m->tq,
+                                                                 m->rec, m->nvalid, w->beta, w->gamma, m->sums,
+                                                                 m->isums, m->err));
+  else
+    GP_KERNEL(ctx, "k_m_query",
+              k_m_query<false><<<grid, threads, 0, ctx->stream>>>(m->shapes, m->rec_tiles, m->n_rec_tiles, m->tq,
+                                                                  m->rec, m->nvalid, w->beta, w->gamma, m->sums,
+                                                                  m->isums, m->err));
   return GP_OK;
 }
 
@@ -558,8 +622,8 @@ gp_status launch_adam_finish(gp_multi* m, const gp_loss_w* w, const gp_adam* hp,
                   m->shapes, m->active_tiles, m->n_active_tiles, m->t, hp->lr, decay, every, hp->beta1, hp->beta2,
                   hp->eps));
   GP_KERNEL(ctx, "k_m_finish",
-            k_m_finish<<<1, 256, 0, s>>>(m->shapes, m->n, m->nvalid, m->sums, m->t, m->perm_epoch, w->alpha,
-                                         w->beta, w->gamma, loss_dev));
+            k_m_finish<<<1, 256, 0, s>>>(m->shapes, m->n, m->nvalid, m->sums, m->isums, m->t, m->perm_epoch,
+                                         w->alpha, w->beta, w->gamma, loss_dev));
   return GP_OK;
 }
 
@@ -567,6 +631,8 @@ gp_status clear_step_state(gp_multi* m) {
   cudaStream_t s = m->ctx->stream;
   GP_CUDA(m->ctx, cudaMemsetAsync(m->nvalid, 0, m->n * sizeof(int32_t), s));
   GP_CUDA(m->ctx, cudaMemsetAsync(m->sums, 0, 4 * m->n * sizeof(double), s));
+  if (m->isums) GP_CUDA(m->ctx, cudaMemsetAsync(m->isums, 0, 4 * m->n * sizeof(long long), s));
+  if (m->acc) GP_CUDA(m->ctx, cudaMemsetAsync(m->acc, 0, 2 * m->V_total * sizeof(unsigned long long), s));
   return GP_OK;
 }
 
@@ -578,7 +644,8 @@ extern "C" gp_status gp_multi_create(gp_ctx* ctx, gp_band* const* bands, int32_t
   if (!out) return gp_fail(ctx, GP_ERR_ARG, "gp_multi_create: null output");
   *out = nullptr;
   if (!bands || !Q || !B || n < 1) return gp_fail(ctx, GP_ERR_ARG, "gp_multi_create: null or empty input");
-  if (flags & ~(uint32_t)GP_SAMPLE_SPATIAL) return gp_fail(ctx, GP_ERR_ARG, "gp_multi_create: unknown flags");
+  if (flags & ~(uint32_t)(GP_SAMPLE_SPATIAL | GP_MULTI_DETERMINISTIC))
+    return gp_fail(ctx, GP_ERR_ARG, "gp_multi_create: unknown flags");
   gp_multi* m = new (std::nothrow) gp_multi();
   if (!m) return gp_fail(ctx, GP_ERR_OOM, "gp_multi_create: host allocation");
   m->ctx = ctx;
@@ -622,6 +689,8 @@ extern "C" gp_status gp_multi_create(gp_ctx* ctx, gp_band* const* bands, int32_t
   }
   gp_status st = GP_OK;
   if (!st) st = gp_alloc(ctx, &m->grad, m->V_total, "multi gradient");
+  if (!st && (flags & GP_MULTI_DETERMINISTIC)) st = gp_alloc(ctx, &m->acc, 2 * m->V_total, "multi fixed-point sums");
+  if (!st && (flags & GP_MULTI_DETERMINISTIC)) st = gp_alloc(ctx, &m->isums, 4 * (size_t)n, "multi integer sums");
   if (!st) st = gp_alloc(ctx, &m->perm, m->J_total, "multi permutation");
   if (!st) st = gp_alloc(ctx, &m->inv, m->J_total, "multi inverse permutation");
   if (!st) st = gp_alloc(ctx, &m->eslot, m->J_total, "multi emission slots");
@@ -655,6 +724,7 @@ extern "C" gp_status gp_multi_create(gp_ctx* ctx, gp_band* const* bands, int32_t
     S.m = b->m;
     S.v = b->v;
     S.grad = m->grad + m->grad_off[(size_t)k];
+    S.acc = m->acc ? m->acc + 2 * m->grad_off[(size_t)k] : nullptr;
     S.pts = b->pts;
     S.sigma = b->sigma;
     S.normals = b->normals;
@@ -710,8 +780,13 @@ extern "C" gp_status gp_multi_step(gp_multi* m, const gp_loss_w* w, const gp_ada
   if (lr_every < 0) return gp_fail(m->ctx, GP_ERR_ARG, "gp_multi_step: lr_every must be >= 0");
   gp_status st = launch_sampling(m);
   if (!st) st = launch_nn(m);
-  if (!st) st = launch_tv(m, w);
-  if (!st) st = launch_query(m, w);
+  if (m->acc) {  // deterministic: the query sums first, folded in by the sweep
+    if (!st) st = launch_query(m, w);
+    if (!st) st = launch_tv(m, w);
+  } else {
+    if (!st) st = launch_tv(m, w);
+    if (!st) st = launch_query(m, w);
+  }
   if (!st) st = launch_adam_finish(m, w, hp, lr_decay, lr_every, loss_dev);
   return st;
 }

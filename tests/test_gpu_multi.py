@@ -269,3 +269,35 @@ def test_multi_rejects_bad_input(gb, ctx, clouds):
     with pytest.raises(gb.GridPullError):
         gb.gp_multi_buffers(multi, 1)
     multi.close()
+
+
+def test_deterministic_multi_repeats_bitwise_and_matches_atomic(gb, ctx, clouds):
+    """GP_MULTI_DETERMINISTIC: two multis over identical bands give the same
+    values, moments and loss slots bit for bit after four steps (across an
+    epoch boundary, spatial order, autotuned first), and agree with the
+    float-atomic multi to float rounding."""
+    import torch
+    runs = []
+    for det in (True, True, False):
+        bands = _make_bands(gb, ctx, clouds)
+        m = gb.gp_multi_create(ctx, bands, [c[4] for c in clouds], [c[5] for c in clouds], seed=11, spatial=True,
+                               deterministic=det)
+        gb.gp_multi_autotune(m, (1.0, 1.0, 0.005))
+        loss = torch.zeros(8 * len(bands), dtype=torch.float32, device="cuda")
+        for _ in range(4):
+            gb.gp_multi_step(m, loss, (1.0, 1.0, 0.005), lr=1e-3)
+        torch.cuda.synchronize()
+        assert gb.gp_multi_get_info(m)["error_bits"] == 0
+        runs.append(([tuple(x.clone() for x in gb.gp_band_values(b)) for b in bands], loss.clone()))
+        m.close()
+    (va, la), (vb, lb), (vc, lc) = runs
+    assert torch.equal(la, lb)
+    for a, b in zip(va, vb):
+        for x, y in zip(a, b):
+            assert torch.equal(x, y)
+    for k in range(len(clouds)):
+        for slot in (gb.GP_LOSS_TOTAL, gb.GP_LOSS_PULL, gb.GP_LOSS_GRAD, gb.GP_LOSS_SURF, gb.GP_LOSS_TV):
+            assert_rel(lc[8 * k + slot].item(), la[8 * k + slot].item(), tol=1e-4, what=f"cloud {k} slot {slot}")
+        # values: Adam moves each by at most about lr per step; float sums in
+        # other orders can flip a near-zero gradient's step, nothing more.
+        assert float((vc[k][0] - va[k][0]).abs().max()) <= 2 * 4 * 1e-3
