@@ -351,28 +351,65 @@ __global__ void __launch_bounds__(TV_SWEEP_THREADS, TV_BLOCKS_PER_SM) k_m_tv(con
     }
     acc = 0.f;
   };
-  tv_sweep(MultiTvSrc{shapes, tiles}, blockIdx.x, gridDim.x, ntiles, sh,
-           [&](int64_t ti, int l0, float g0, int l1, float g1, float ts) {
-             const MTile tl = tiles[ti];
-             const MShape& S = shapes[tl.shape];
-             if (tl.shape != cur) {
-               if (cur >= 0) flush();
-               cur = tl.shape;
-             }
-             acc += ts;
-             const float tv_scale = S.V_tv > 0 ? alpha / (float)S.V_tv : 0.f;
-             float* gp = S.grad + (int64_t)tl.first * 512;
-             if (DET) {
-               const int bv = nvalid[tl.shape];
-               const float qscale = bv > 0 ? 1.0f / (float)bv : 0.f;
-               unsigned long long* ap = S.acc + 2 * (int64_t)tl.first * 512;
-               gp[l0] = fold_fixed(ap + 2 * l0, qscale, tv_scale * g0);
-               gp[l1] = fold_fixed(ap + 2 * l1, qscale, tv_scale * g1);
-             } else {
-               gp[l0] = tv_scale * g0;
-               gp[l1] = tv_scale * g1;
-             }
-           });
+  // DET: this thread's two vertices of each brick (those tv_gather hands
+  // it) have their fixed-point sums loaded at the top of the brick's
+  // iteration, under its halo copies; only trainable vertices can hold any.
+  const int tt = threadIdx.x;
+  const int lv0 = (tt & 7) + 16 * ((tt >> 3) & 3) + 64 * (tt >> 5);
+  long long phi[2] = {0, 0}, plo[2] = {0, 0};
+  bool ptr[2] = {false, false};
+  auto out = [&](int64_t ti, int l0, float g0, int l1, float g1, float ts) {
+        const MTile tl = tiles[ti];
+        const MShape& S = shapes[tl.shape];
+        if (tl.shape != cur) {
+          if (cur >= 0) flush();
+          cur = tl.shape;
+        }
+        acc += ts;
+        const float tv_scale = S.V_tv > 0 ? alpha / (float)S.V_tv : 0.f;
+        float* gp = S.grad + (int64_t)tl.first * 512;
+        if (DET) {
+          const int bv = nvalid[tl.shape];
+          const float qscale = bv > 0 ? 1.0f / (float)bv : 0.f;
+          unsigned long long* ap = S.acc + 2 * (int64_t)tl.first * 512;
+          const int ls[2] = {l0, l1};
+          const float gs[2] = {g0, g1};
+#pragma unroll
+          for (int k = 0; k < 2; ++k) {
+            float g = tv_scale * gs[k];
+            if (ptr[k]) {
+              ap[2 * ls[k]] = 0ull;
+              ap[2 * ls[k] + 1] = 0ull;
+              const float qv = __fmaf_rn(__ll2float_rn(phi[k]), 9.5367431640625e-07f,
+                                         __ll2float_rn(plo[k]) * 8.673617379884035e-19f);
+              g = __fmaf_rn(qv, qscale, g);
+            }
+            gp[ls[k]] = g;
+          }
+        } else {
+          gp[l0] = tv_scale * g0;
+          gp[l1] = tv_scale * g1;
+        }
+      };
+  auto pre = [&](int64_t ti) {
+        const MTile tl = tiles[ti];
+        const MShape& S = shapes[tl.shape];
+        const unsigned long long* ap = S.acc + 2 * (int64_t)tl.first * 512;
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          const int l = lv0 + 8 * k;
+          const uint32_t word = __ldg(S.G.masks + (int64_t)tl.first * 48 + 16 + (l >> 5));
+          ptr[k] = (word >> (l & 31)) & 1u;
+          if (ptr[k]) {
+            phi[k] = (long long)ap[2 * l];
+            plo[k] = (long long)ap[2 * l + 1];
+          }
+        }
+      };
+  if constexpr (DET)
+    tv_sweep(MultiTvSrc{shapes, tiles}, blockIdx.x, gridDim.x, ntiles, sh, out, pre);
+  else
+    tv_sweep(MultiTvSrc{shapes, tiles}, blockIdx.x, gridDim.x, ntiles, sh, out);
   if (cur >= 0) flush();
 }
 
