@@ -655,59 +655,101 @@ def run_ours(args, world, rank, local):
             del pts_dev
         del tri
 
-    # End to end through the public API: every step copies its queries and
-    # their source points from pinned host memory, runs NN + step + update and
-    # copies its loss back to pinned host memory.  The copy of step k + 1 runs
-    # on a second stream into the other of two device buffers while step k
-    # computes; the K steps (copies, steps, read-backs and the L2 flush before
-    # each step) are timed as one region on the device.
+    # End to end through the public API on the headline's kind of batch: the
+    # queries and source points of NH steps are drawn by the device sampler
+    # (the spatially ordered batches the headline steps on) and kept in pinned
+    # host memory before timing.  In the timed region every step copies its
+    # batch from the host, runs gp_nn (seeded) and the descent (FitStep's
+    # form) and copies its loss back to pinned host memory.  Where the
+    # headline is pipelined (working set larger than L2) the copy of batch
+    # k + 2 and the search of batch k + 1 run on two more streams while step k
+    # descends, as FitStep.run_pipelined overlaps its draws; otherwise the
+    # steps run in turn with an L2 flush before each, the next copy
+    # overlapped.  The K steps are timed as one region.
     B = wl["B"]
     K = args.steps
     NH = min(K, 8)  # distinct host batches, reused in turn
-    rng = np.random.default_rng(rank + 7)
-    jj = rng.integers(0, len(pts), size=(NH, B))
-    sig = gb.gp_band_sigma(band).cpu().numpy()
+    t_e2e = t_next
+    t_next += K
     hq = torch.empty((NH, B, 3), dtype=torch.float32).pin_memory()
-    hq.copy_(torch.from_numpy((pts[jj] + sig[jj][..., None] * rng.normal(size=(NH, B, 3))).astype(np.float32)))
-    hsrc = torch.from_numpy(jj.astype(np.int32)).pin_memory()  # each query's source point: the search's seed
+    hsrc = torch.empty((NH, B), dtype=torch.int32).pin_memory()
+    counts_h = []
+    for k in range(NH):
+        epoch, first, count = fit.batch_of(t_e2e + k)
+        gb.gp_sample(band, fit.seed, epoch, fit.Q, first, count, fit.q, fit.src, spatial=True)
+        hq[k, :count].copy_(fit.q[:count])
+        hsrc[k, :count].copy_(fit.src[:count])
+        counts_h.append(count)
+    torch.cuda.synchronize()
     hloss = torch.empty((K, 8), dtype=torch.float32).pin_memory()
     dq = [torch.empty((B, 3), dtype=torch.float32, device="cuda") for _ in range(2)]
     dsrc = [torch.empty(B, dtype=torch.int32, device="cuda") for _ in range(2)]
-    copy_stream = torch.cuda.Stream()
-    ready = [torch.cuda.Event() for _ in range(2)]
-    free = [torch.cuda.Event() for _ in range(2)]
+    copy_stream, search_stream = torch.cuda.Stream(), torch.cuda.Stream()
+    _, hi_prio = torch.cuda.Stream.priority_range()
+    step_stream = torch.cuda.Stream(priority=hi_prio) if pipelined_headline else stream
+    if not pipelined_headline:
+        search_stream = stream
+    side_streams = []
+    for st_ in (copy_stream, search_stream, step_stream):
+        if st_.cuda_stream != stream.cuda_stream and all(st_.cuda_stream != o.cuda_stream for o in side_streams):
+            side_streams.append(st_)
+    copied = [torch.cuda.Event() for _ in range(2)]
+    searched = [torch.cuda.Event() for _ in range(2)]
+    stepped = [torch.cuda.Event() for _ in range(2)]
 
-    def issue_copy(k):
+    def e2e_copy(k):
         b = k % 2
         with torch.cuda.stream(copy_stream):
-            copy_stream.wait_event(free[b])  # step k - 2 is done with this buffer
+            if k >= 2:
+                copy_stream.wait_event(searched[b])  # the search of step k - 2 has read dq[b]
             dq[b].copy_(hq[k % NH], non_blocking=True)
             dsrc[b].copy_(hsrc[k % NH], non_blocking=True)
-            ready[b].record(copy_stream)
+            copied[b].record(copy_stream)
+
+    def e2e_search(k):
+        b, n = k % 2, counts_h[k % NH]
+        with torch.cuda.stream(search_stream):
+            search_stream.wait_event(copied[b])
+            if k >= 2:
+                search_stream.wait_event(stepped[b])  # step k - 2 has read buffer b's records
+            gb.gp_nn(band, dq[b][:n], None, fit.bufs[b]["rec"], hint=dsrc[b][:n], nvalid_out=fit.bufs[b]["nvalid"])
+            searched[b].record(search_stream)
 
     barrier(world)
     torch.cuda.synchronize()
     e_start = torch.cuda.Event(enable_timing=True)
     e_end = torch.cuda.Event(enable_timing=True)
-    step_t = t_next + 2
     e_start.record(stream)
-    copy_stream.wait_stream(stream)
-    issue_copy(0)
+    for st_ in side_streams:
+        st_.wait_stream(stream)
+    e2e_q = 0
+    e2e_copy(0)
+    if K > 1:
+        e2e_copy(1)
+    if pipelined_headline:
+        e2e_search(0)
     for k in range(K):
-        b = k % 2
-        if k + 1 < K:
-            issue_copy(k + 1)
-        flush.fill_(float(k))
-        stream.wait_event(ready[b])
-        gb.gp_nn(band, dq[b], None, fit.rec, hint=dsrc[b], nvalid_out=fit.nvalid)
-        gb.gp_step_update(band, fit.rec, B, fit.loss, wl["lr"], step_t + k + 1, PAPER_WEIGHTS, nvalid=fit.nvalid,
-                          flags=fit.flags)
-        free[b].record(stream)
-        hloss[k].copy_(fit.loss, non_blocking=True)
+        b, n = k % 2, counts_h[k % NH]
+        if pipelined_headline:
+            if k + 1 < K:
+                e2e_search(k + 1)
+        else:
+            flush.fill_(float(k))
+            e2e_search(k)
+        if k + 2 < K:
+            e2e_copy(k + 2)
+        with torch.cuda.stream(step_stream):
+            step_stream.wait_event(searched[b])
+            fit._descend(t_e2e + k, fit.bufs[b], n)
+            hloss[k].copy_(fit.loss, non_blocking=True)
+            stepped[b].record(step_stream)
+        e2e_q += n
+    for st_ in side_streams:
+        stream.wait_stream(st_)
     e_end.record(stream)
     e_end.synchronize()
     e2e_ms = reduce_max(e_start.elapsed_time(e_end), world)
-    e2e_value = reduce_sum(float(K * B), world) / (e2e_ms / 1e3)
+    e2e_value = reduce_sum(float(e2e_q), world) / (e2e_ms / 1e3)
     loss_final = float(hloss[K - 1][gb.GP_LOSS_TOTAL])
 
     # Plain PyTorch autograd on the same GPU and the same records: Eq. 8 in torch
@@ -769,9 +811,14 @@ def run_ours(args, world, rank, local):
                           "brick": 8},
                "roofline": roofline, "cpu_baseline": cpu,
                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 16 * B, "d2h_bytes_per_step": 32,
-                       "path": "host queries and their source points -> gp_nn (seeded) -> gp_step_update "
-                               "-> loss to host; next step's copy overlapped on a second stream; K steps timed "
-                               "as one region, L2 flush included"},
+                       "path": ("host batches (the device sampler's spatially ordered queries and their "
+                                "source points, drawn before timing) -> H2D copy -> gp_nn (seeded) -> " +
+                                ("gp_step_update" if fit.fused else "gp_step + gp_update") +
+                                " -> loss to host; " +
+                                ("copy of step k + 2 and search of step k + 1 on two more streams while step k "
+                                 "descends" if pipelined_headline else
+                                 "steps in turn, L2 flush before each, next copy on a second stream") +
+                                "; K steps timed as one region")},
                "gpu_launches": int(launches), "clocks": clk, "kernels": per_kernel, "fwd_bwd_adam": fba,
                "nn_work": nn_work, "other_form": other,
                "mesh": mesh,
