@@ -212,11 +212,12 @@ __device__ __forceinline__ void nn_seed(NNState& st, const float q[3], const int
 }
 
 // Seeded search (thr finite from the start): walk the slabs (fixed z) and, in
-// each, the rows (fixed y) closest first, alternating sides, each clipped to
-// the cells within the current radius; a side stops at its first slab or row
-// whose lower bound exceeds thr, since bounds only grow outwards and thr only
-// shrinks.  Every point with squared distance <= the final thr lies in a row
-// that was visited, within the x-range read.
+// each, the rows (fixed y) closest first, two at a time (one each side), each
+// clipped to the cells within the radius as it stood when the pair was
+// tested; a side stops at its first slab or row whose lower bound exceeds
+// thr, since bounds only grow outwards and thr only shrinks.  Every point
+// with squared distance <= the final thr lies in a row that was visited,
+// within the x-range read.
 template <typename F>
 __device__ __forceinline__ void nn_ball_walk(const float q[3], const int c[3], const NNGrid& g, float margin,
                                              const float& thr, F&& visit) {
@@ -239,6 +240,12 @@ __device__ __forceinline__ void nn_ball_walk(const float q[3], const int c[3], c
       }
       bool y_done[2] = {false, false};
       for (int ky = 0; !(y_done[0] && y_done[1]); ++ky) {
+        // Both rows of this distance (c_y + ky, c_y - ky) are tested and
+        // their cell starts loaded before either is scanned, so that the two
+        // rows' loads are in flight together.  The second row's test and
+        // x-range then use the radius from before the first row's scan: a
+        // superset of what the shrunken radius needs.
+        int a[2] = {0, 0}, b[2] = {0, 0};
 #pragma unroll
         for (int sy = 0; sy < 2; ++sy) {
           if (y_done[sy] || (ky == 0 && sy == 1)) continue;
@@ -256,8 +263,12 @@ __device__ __forceinline__ void nn_ball_walk(const float q[3], const int c[3], c
           const float rad = sqrtf(thr - lyz2) * 1.000001f + margin;
           const int xa = nn_cell(q[0] - rad, g), xb = nn_cell(q[0] + rad, g);
           const int64_t row = ((int64_t)cz * G + cy) * G;
-          visit(__ldg(g.start + row + xa), __ldg(g.start + row + xb + 1));
+          a[sy] = __ldg(g.start + row + xa);
+          b[sy] = __ldg(g.start + row + xb + 1);
         }
+#pragma unroll
+        for (int sy = 0; sy < 2; ++sy)
+          if (b[sy] > a[sy]) visit(a[sy], b[sy]);
       }
     }
   }
