@@ -157,7 +157,7 @@ gp_status gp_build_permutation(gp_band* band, uint64_t seed, uint32_t epoch);
 
 // Tile of sorted points handled by one block of the spatial batch order.
 constexpr int GP_ORDER_THREADS = 512;
-constexpr int GP_ORDER_PER_THREAD = 1;
+constexpr int GP_ORDER_PER_THREAD = 4;
 constexpr int GP_ORDER_TILE = GP_ORDER_THREADS * GP_ORDER_PER_THREAD;
 
 // ------------------------------------------------------ device: geometry

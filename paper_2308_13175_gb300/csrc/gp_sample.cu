@@ -14,6 +14,8 @@
 // Neighbouring outputs then lie close together, which is what the nearest-point
 // search and the gather / scatter of the step profit from; the loss does not
 // depend on the order.
+#include <algorithm>
+
 #include "gp_internal.cuh"
 
 namespace {
@@ -66,36 +68,51 @@ __global__ void k_sample(const float* __restrict__ pts, const float* __restrict_
   put_query(i, gp_draw_query(pts, sigma, j, k, epoch, k0, k1), j, k, q, src, pos);
 }
 
-// Pass 1: queries owned by each tile of sorted points (GP_ORDER_TILE points,
-// one per thread), TPB tiles per block; only the tile totals are needed, so
-// each is a warp-sum reduction with one barrier for all of them.  Four tiles
-// per block pay on large clouds (10 M points: 53 -> 37 us); on small ones the
-// grid would be too small, so they take one.
+// The GP_ORDER_PER_THREAD consecutive emission slots of this thread in tile
+// `tile` (an aligned 16-byte load where all are in range), 0 past J.
+__device__ __forceinline__ void load_slots(const int32_t* __restrict__ eslot, int64_t J, int64_t t0,
+                                           int32_t p[GP_ORDER_PER_THREAD]) {
+  static_assert(GP_ORDER_PER_THREAD == 4, "one int4 of slots per thread");
+  if (t0 + 3 < J) {
+    const int4 v = __ldg(reinterpret_cast<const int4*>(eslot + t0));
+    p[0] = v.x;
+    p[1] = v.y;
+    p[2] = v.z;
+    p[3] = v.w;
+  } else {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) p[u] = t0 + u < J ? __ldg(eslot + t0 + u) : 0;
+  }
+}
+
+// Pass 1: queries owned by each tile of GP_ORDER_TILE sorted points (four
+// consecutive points per thread); only the tile totals are needed.
 constexpr int COUNT_WARPS = GP_ORDER_THREADS / 32;
 
-template <int COUNT_TILES>
 __global__ void __launch_bounds__(GP_ORDER_THREADS) k_order_count(const int32_t* __restrict__ eslot, int64_t J,
                                                                   int64_t first, int64_t last,
                                                                   int32_t* __restrict__ tiles, int64_t ntiles) {
-  static_assert(GP_ORDER_PER_THREAD == 1, "one point per thread and tile");
-  __shared__ int red[COUNT_TILES][COUNT_WARPS];
-  const int64_t tile0 = (int64_t)blockIdx.x * COUNT_TILES;
+  __shared__ int red[COUNT_WARPS];
+  const int64_t t0 = (int64_t)blockIdx.x * GP_ORDER_TILE + (int64_t)threadIdx.x * GP_ORDER_PER_THREAD;
+  int32_t p[GP_ORDER_PER_THREAD];
+  load_slots(eslot, J, t0, p);
+  int c = 0;
 #pragma unroll
-  for (int k = 0; k < COUNT_TILES; ++k) {
-    const int64_t t = (tile0 + k) * GP_ORDER_TILE + threadIdx.x;
-    int c = 0;
-    if (t < J) {
+  for (int u = 0; u < GP_ORDER_PER_THREAD; ++u) {
+    if (t0 + u < J) {
       int64_t r0;
-      owned_range(eslot[t], J, first, last, r0, c);
+      int n;
+      owned_range(p[u], J, first, last, r0, n);
+      c += n;
     }
-    c = gp_warp_sum_i(c);
-    if ((threadIdx.x & 31) == 0) red[k][threadIdx.x >> 5] = c;
   }
+  c = gp_warp_sum_i(c);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = c;
   __syncthreads();
-  if (threadIdx.x < COUNT_TILES && tile0 + threadIdx.x < ntiles) {
+  if (threadIdx.x == 0 && blockIdx.x < ntiles) {
     int total = 0;
-    for (int w = 0; w < COUNT_WARPS; ++w) total += red[threadIdx.x][w];
-    tiles[tile0 + threadIdx.x] = total;
+    for (int w = 0; w < COUNT_WARPS; ++w) total += red[w];
+    tiles[blockIdx.x] = total;
   }
 }
 
@@ -105,45 +122,66 @@ __global__ void __launch_bounds__(GP_ORDER_THREADS) k_order_tiles(int32_t* __res
   gp_block_scan_inplace(tiles, ntiles);
 }
 
-// Pass 3: every sorted point writes its queries at its offset.
+// Pass 3: the tile's queries in order (by point, then replica) written from
+// its offset.  The points' query counts are scanned into shared memory first;
+// the queries are then drawn one per thread over the tile's compacted list
+// (each finds its point by a binary search of the offsets), so that a warp's
+// lanes all draw even when few of the tile's points own a query.  `splits`
+// blocks share a tile (each scans it, then draws every splits-th round of
+// its list), so that clouds of few tiles with many queries per point still
+// fill the GPU.
 __global__ void __launch_bounds__(GP_ORDER_THREADS) k_order_emit(
     const int32_t* __restrict__ order, const int32_t* __restrict__ eslot, const float4* __restrict__ epts,
-    int64_t J, int64_t first, int64_t last, const int32_t* __restrict__ tiles,
+    int64_t J, int64_t first, int64_t last, const int32_t* __restrict__ tiles, int splits,
     uint32_t epoch, uint32_t k0, uint32_t k1, float* __restrict__ q, int32_t* __restrict__ src,
     int32_t* __restrict__ pos, int32_t* __restrict__ err) {
-  int64_t base = (int64_t)blockIdx.x * GP_ORDER_TILE + (int64_t)threadIdx.x * GP_ORDER_PER_THREAD;
+  __shared__ int s_pre[GP_ORDER_TILE];  // first query of each point within the tile
+  __shared__ int s_r0[GP_ORDER_TILE];   // its first replica
+  __shared__ int s_p[GP_ORDER_TILE];    // its pool slot
+  const int tile = blockIdx.x / splits, split = blockIdx.x % splits;
+  const int64_t tile_base = (int64_t)tile * GP_ORDER_TILE;
+  const int l0 = threadIdx.x * GP_ORDER_PER_THREAD;
   const int64_t n_out = last - first;
-  int jj[GP_ORDER_PER_THREAD], nn[GP_ORDER_PER_THREAD];
-  int64_t rr[GP_ORDER_PER_THREAD], pp[GP_ORDER_PER_THREAD];
+  int32_t p[GP_ORDER_PER_THREAD];
+  load_slots(eslot, J, tile_base + l0, p);
+  int nn[GP_ORDER_PER_THREAD], rr[GP_ORDER_PER_THREAD];
   int c = 0;
 #pragma unroll
   for (int u = 0; u < GP_ORDER_PER_THREAD; ++u) {
-    int64_t t = base + u;
     nn[u] = 0;
-    jj[u] = 0;
-    pp[u] = 0;
     rr[u] = 0;
-    if (t < J) {
-      pp[u] = eslot[t];
-      owned_range(pp[u], J, first, last, rr[u], nn[u]);
-      if (nn[u]) jj[u] = order[t];
-      c += nn[u];
+    if (tile_base + l0 + u < J) {
+      int64_t r0;
+      owned_range(p[u], J, first, last, r0, nn[u]);
+      rr[u] = (int)r0;
     }
+    c += nn[u];
   }
   int excl;
-  block_exclusive_scan(c, &excl);
-  int64_t out = (int64_t)tiles[blockIdx.x] + excl;
+  const int total = block_exclusive_scan(c, &excl);
 #pragma unroll
   for (int u = 0; u < GP_ORDER_PER_THREAD; ++u) {
-    for (int r = 0; r < nn[u]; ++r) {
-      int64_t k = pp[u] + (rr[u] + r) * J;
-      int64_t i = out++;
-      if (i < 0 || i >= n_out) {  // only if Pi_e were not a bijection
-        atomicOr(err, GP_EF_RANGE);
-        continue;
-      }
-      put_query(i, gp_draw_query4(epts[base + u], k, epoch, k0, k1), jj[u], k, q, src, pos);
+    s_pre[l0 + u] = excl;
+    s_r0[l0 + u] = rr[u];
+    s_p[l0 + u] = p[u];
+    excl += nn[u];
+  }
+  __syncthreads();
+  const int64_t out0 = tiles[tile];
+  for (int i = split * GP_ORDER_THREADS + threadIdx.x; i < total; i += splits * GP_ORDER_THREADS) {
+    // The last point t with s_pre[t] <= i (s_pre[0] = 0): the one owning query i.
+    int t = 0;
+#pragma unroll
+    for (int step = GP_ORDER_TILE / 2; step > 0; step >>= 1)
+      if (s_pre[t + step] <= i) t += step;
+    const int64_t k = (int64_t)s_p[t] + (int64_t)(s_r0[t] + (i - s_pre[t])) * J;
+    const int64_t o = out0 + i;
+    if (o < 0 || o >= n_out) {  // only if Pi_e were not a bijection
+      atomicOr(err, GP_EF_RANGE);
+      continue;
     }
+    const int64_t g = tile_base + t;
+    put_query(o, gp_draw_query4(__ldg(epts + g), k, epoch, k0, k1), __ldg(order + g), k, q, src, pos);
   }
 }
 
@@ -188,15 +226,18 @@ extern "C" gp_status gp_sample(gp_band* b, uint64_t seed, uint32_t epoch, int64_
   const int64_t J = b->J, last = first + count;
   const int64_t ntiles = (J + GP_ORDER_TILE - 1) / GP_ORDER_TILE;
   GP_KERNEL(ctx, "k_order_count",
-            (ntiles >= 8 * (int64_t)ctx->num_sms
-                 ? k_order_count<4><<<(unsigned)((ntiles + 3) / 4), GP_ORDER_THREADS, 0, ctx->stream>>>(
-                       b->emit_slot, J, first, last, b->order_tiles, ntiles)
-                 : k_order_count<1><<<(unsigned)ntiles, GP_ORDER_THREADS, 0, ctx->stream>>>(
-                       b->emit_slot, J, first, last, b->order_tiles, ntiles)));
+            k_order_count<<<(unsigned)ntiles, GP_ORDER_THREADS, 0, ctx->stream>>>(b->emit_slot, J, first, last,
+                                                                                 b->order_tiles, ntiles));
   GP_KERNEL(ctx, "k_order_tiles", k_order_tiles<<<1, GP_ORDER_THREADS, 0, ctx->stream>>>(b->order_tiles, ntiles));
+  // Blocks per tile: enough for about four per SM, at most one per round of
+  // GP_ORDER_THREADS queries of an average tile.
+  const int64_t per_tile = (count + ntiles - 1) / ntiles;
+  int64_t splits = (4 * (int64_t)ctx->num_sms + ntiles - 1) / ntiles;
+  splits = std::min<int64_t>(splits, (per_tile + GP_ORDER_THREADS - 1) / GP_ORDER_THREADS);
+  splits = std::max<int64_t>(1, std::min<int64_t>(splits, 64));
   GP_KERNEL(ctx, "k_order_emit",
-            k_order_emit<<<(unsigned)ntiles, GP_ORDER_THREADS, 0, ctx->stream>>>(
-                b->emit_order, b->emit_slot, b->emit_pts, J, first, last, b->order_tiles, epoch, k0, k1, q_dev,
-                src_dev, pos_dev, b->dev_ints + GP_DI_ERROR));
+            k_order_emit<<<(unsigned)(ntiles * splits), GP_ORDER_THREADS, 0, ctx->stream>>>(
+                b->emit_order, b->emit_slot, b->emit_pts, J, first, last, b->order_tiles, (int)splits, epoch, k0,
+                k1, q_dev, src_dev, pos_dev, b->dev_ints + GP_DI_ERROR));
   return GP_OK;
 }

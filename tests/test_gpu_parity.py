@@ -291,9 +291,12 @@ def test_sampler_spatial_order_matches_oracle(gb, ctx, sphere5k, J, Q, first, co
     z = (want - pts[j]) / sig[j][:, None]
     bound = 2e-6 * (np.abs(pts[j]) + sig[j][:, None] * (1 + np.abs(z))) + 1e-7
     assert np.all(np.abs(q - want) <= bound)
-    # Outputs of one point are adjacent, and neighbours are close in space.
+    # Outputs of one point are adjacent, in increasing pool position, and
+    # neighbours are close in space.
     starts = np.flatnonzero(np.diff(src)) + 1
     assert len(np.unique(src)) == len(starts) + 1
+    same = np.diff(src) == 0
+    assert np.all(np.diff(pos)[same] > 0)
     if J > 100:
         step = np.linalg.norm(np.diff(pts[src], axis=0), axis=1).mean()
         rand = np.linalg.norm(pts[src] - pts[np.random.default_rng(0).permutation(src)], axis=1).mean()
