@@ -262,9 +262,12 @@ __global__ void GP_NN_BOUNDS k_nn(NNGrid g, const float* __restrict__ qin, int64
 // order.  Which thread searches a query does not change its result.
 // Measured on GB300: 18% faster than k_nn on the 4,194,304-query superquadric
 // batch and 10% on the 2,097,152-query scene batch, 6-10% slower on the
-// 262,144-query single-object batch, hence NN_SORTED_MIN_QUERIES.
-constexpr int NN_THREADS = 256;
-constexpr int NN_SPAN = 256;  // queries sorted together (a multiple of 32 dividing NN_THREADS)
+// 262,144-query single-object batch, hence NN_SORTED_MIN_QUERIES.  Blocks of
+// 128 (sorted together) beat 256 by 4% on the scene: a block's slot is held
+// until its slowest warp ends, and smaller blocks leave shorter tails; 64
+// or a 64-query sort span lose more than that.
+constexpr int NN_THREADS = 128;
+constexpr int NN_SPAN = 128;  // queries sorted together (a multiple of 32 dividing NN_THREADS)
 constexpr int NN_SEGS = NN_THREADS / NN_SPAN;
 constexpr int NN_SPAN_WARPS = NN_SPAN / 32;
 constexpr int NN_BUCKETS = 16;
