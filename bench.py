@@ -761,8 +761,12 @@ def run_ours(args, world, rank, local):
         ts = from_band(band, device="cuda", dtype=torch.float32)
         Dt = gb.gp_band_values(band)[0].clone().requires_grad_(True)
         opt = torch.optim.Adam([Dt], lr=wl["lr"])
-        rec = fit.rec.clone()
-        nv = fit.nvalid.clone()
+        while fit.batch_of(t_next)[2] != B:  # a full batch of the epoch
+            t_next += 1
+        fit._draw(t_next, fit.bufs[0])
+        t_next += 1
+        rec = fit.bufs[0]["rec"].clone()
+        nv = fit.bufs[0]["nvalid"].clone()
         for _ in range(3):
             ts.step(Dt, opt, rec, PAPER_WEIGHTS)
         Kt = max(3, min(args.steps, 10))
@@ -777,7 +781,7 @@ def run_ours(args, world, rank, local):
             t_ms.append(e0.elapsed_time(e1))
             flush.fill_(float(k))
             e0.record(stream)
-            gb.gp_step_update(band, rec, B, fit.loss, wl["lr"], step_t + K + k + 1, PAPER_WEIGHTS, nvalid=nv,
+            gb.gp_step_update(band, rec, B, fit.loss, wl["lr"], t_next + k + 1, PAPER_WEIGHTS, nvalid=nv,
                               flags=fit.flags)
             e1.record(stream)
             torch.cuda.synchronize()
