@@ -932,9 +932,39 @@ def run_collection(args, world, rank, local):
                             "alg_bytes": int(by), "gbs": round(by / (avg_ms / 1e3) / 1e9, 1) if by else None}
     fba = fwd_bwd_adam(per_kernel, ("k_m_tv", "k_m_query", "k_m_adam", "k_m_finish"), q_prof / Kp, Vt, peak)
     dom = max(kern.items(), key=lambda kv: kv[1][1])[0]
-    achieved = per_kernel[dom]["gbs"] or 0.0
-    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": None, "peak_kind": peak_kind}
+    # The search's candidate distances: k_m_nn walks each record's ball as
+    # gp_nn does (same seeds, same walk), so gp_nn_work on every cloud's
+    # records of the last step counts them.
+    cand, nrec = 0, 0
+    for k, band in enumerate(bands):
+        rec_k, src_k, _ = gb.gp_multi_buffers(multi, k)
+        sel = src_k >= 0
+        qk = rec_k[sel][:, :3].contiguous()
+        if len(qk) == 0:
+            continue
+        nn_tmp = torch.empty(len(qk), dtype=torch.int32, device="cuda")
+        cand += gb.gp_nn_work(band, qk, nn_tmp, hint=src_k[sel].contiguous())
+        nrec += len(qk)
+    nn_work = None
+    if nrec > 0 and "k_m_nn" in per_kernel:
+        per_q = cand / nrec
+        nk = per_kernel["k_m_nn"]
+        tfl = per_q * (q_prof / Kp) * NN_FLOPS_PER_CANDIDATE / (nk["avg_us"] * 1e-6) / 1e12
+        fp32_peak, fp32_kind = fp32_peak_tflops(torch.cuda.get_device_properties(local).multi_processor_count)
+        nn_work = {"kernel": "k_m_nn", "candidates_per_query": round(per_q, 2),
+                   "candidates_per_s": per_q * (q_prof / Kp) / (nk["avg_us"] * 1e-6), "fp32_tflops": round(tfl, 3),
+                   "fp32_peak_tflops": round(fp32_peak, 2), "frac": round(tfl / fp32_peak, 4),
+                   "peak_kind": fp32_kind}
+    if dom == "k_m_nn" and nn_work is not None:
+        roofline = {"bound": "alu", "kernel": dom, "achieved": nn_work["fp32_tflops"],
+                    "peak": nn_work["fp32_peak_tflops"], "unit": "TFLOP/s", "frac": nn_work["frac"], "traffic": None,
+                    "peak_kind": nn_work["peak_kind"],
+                    "work": f"{NN_FLOPS_PER_CANDIDATE} FP32 flops per candidate distance, "
+                            f"{nn_work['candidates_per_query']} candidates per query (gp_nn_work)"}
+    else:
+        achieved = per_kernel[dom]["gbs"] or 0.0
+        roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "frac": round(achieved / peak, 4), "traffic": None, "peak_kind": peak_kind}
 
     # End to end through the public call: gp_multi_step from Python (no graph)
     # and the n x 8 loss slots read back to the host every step.
@@ -970,7 +1000,7 @@ def run_collection(args, world, rank, local):
                "roofline": roofline, "cpu_baseline": None,
                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 32 * n},
                "gpu_launches": int(per_step_launches * args.steps), "clocks": clk, "kernels": per_kernel,
-               "fwd_bwd_adam": fba,
+               "fwd_bwd_adam": fba, "nn_work": nn_work,
                "error_bits": info["error_bits"],
                "loss_last_mean": float(hloss.view(n, 8)[:, gb.GP_LOSS_TOTAL].mean())}
         print(json.dumps(out), flush=True)
