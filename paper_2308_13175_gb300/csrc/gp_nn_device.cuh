@@ -43,6 +43,11 @@ __device__ __forceinline__ float nn_gap(const float q[3], const int c[3], int r,
   return gap;
 }
 
+// sqrt(x) for the x-range of a row, as x rsqrt(x): within a relative 3e-7
+// of the correctly rounded root, which the range's factor 1.000001 and its
+// additive margin (>= 2e-5) cover.  0 for x <= 0.
+__device__ __forceinline__ float nn_row_sqrt(float x) { return x > 0.f ? x * rsqrtf(x) : 0.f; }
+
 __device__ __forceinline__ float nn_margin(const float q[3]) {
   float m = fmaxf(fabsf(q[0]), fmaxf(fabsf(q[1]), fabsf(q[2])));
   return 1e-5f * (2.0f + m);
@@ -102,6 +107,7 @@ struct NNState {
 };
 
 __device__ __forceinline__ void nn_update(NNState& st, float d, int j) {
+  if (d > st.b2) return;   // neither the best nor the runner-up (b1 <= b2)
   if (j == st.j1) return;  // the seeded point, met again in the scan
   if (d < st.b1 || (d == st.b1 && j < st.j1)) {
     st.b2 = st.b1;
@@ -149,7 +155,7 @@ __device__ __forceinline__ void nn_row_ring(const float q[3], const int c[3], in
       int xa = 0, xb = G - 1;
       float rem = thr - lyz2;
       if (rem < 16.0f) {
-        float rad = sqrtf(rem) * 1.000001f + margin;
+        float rad = nn_row_sqrt(rem) * 1.000001f + margin;
         xa = nn_cell(q[0] - rad, g);
         xb = nn_cell(q[0] + rad, g);
       }
@@ -260,7 +266,7 @@ __device__ __forceinline__ void nn_ball_walk(const float q[3], const int c[3], c
             y_done[sy] = true;
             continue;
           }
-          const float rad = sqrtf(thr - lyz2) * 1.000001f + margin;
+          const float rad = nn_row_sqrt(thr - lyz2) * 1.000001f + margin;
           const int xa = nn_cell(q[0] - rad, g), xb = nn_cell(q[0] + rad, g);
           const int64_t row = ((int64_t)cz * G + cy) * G;
           a[sy] = __ldg(g.start + row + xa);
