@@ -471,15 +471,15 @@ __global__ void __launch_bounds__(256) k_m_adam(const MShape* __restrict__ shape
                                                 int64_t ntiles, const int64_t* __restrict__ t_dev, float lr,
                                                 float decay, int64_t every, float b1, float b2, float eps) {
   const int64_t t = *t_dev;
-  const float bc1 = (float)(1.0 - pow((double)b1, (double)(t + 1)));
-  const float bc2 = (float)(1.0 - pow((double)b2, (double)(t + 1)));
+  const float ibc1 = (float)(1.0 / (1.0 - pow((double)b1, (double)(t + 1))));
+  const float ibc2 = (float)(1.0 / (1.0 - pow((double)b2, (double)(t + 1))));
   const float lr_t = every > 0 ? (float)((double)lr * pow((double)decay, (double)(t / every))) : lr;
   const int64_t n = ntiles * 128;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const MTile tl = tiles[i >> 7];
     const MShape& S = shapes[tl.shape];
     adam_quad(__ldg(S.active + tl.first), (int)(i & 127), S.G.masks, S.grad, S.D, S.m, S.v, lr_t, b1, b2, eps,
-              bc1, bc2);
+              ibc1, ibc2);
   }
 }
 

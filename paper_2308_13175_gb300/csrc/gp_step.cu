@@ -291,7 +291,7 @@ __global__ void __launch_bounds__(TV_THREADS, TV_BLOCKS_PER_SM) k_tv(Grid G, con
 
 // Adam's hyper-parameters for one step, with the bias corrections.
 struct AdamArgs {
-  float lr, b1, b2, eps, bc1, bc2;
+  float lr, b1, b2, eps, ibc1, ibc2;  // ibc = 1 / (1 - beta^t)
 };
 
 // L_TV and Adam in one sweep over the bricks (gp_step_update), after the
@@ -353,12 +353,11 @@ __global__ void __launch_bounds__(TV_THREADS, TV_BLOCKS_PER_SM) k_tv_adam(
       qgrad[addr] = 0.f;
       g = tv_scale * g_tv + pq[k];
     }
-    const float mm = fmaf(ad.b1, pm[k], (1.0f - ad.b1) * g);
-    const float vv = fmaf(ad.b2, pv[k], (1.0f - ad.b2) * g * g);
+    float mm = pm[k], vv = pv[k];
+    const float dn = adam_elem(g, mm, vv, pd[k], ad.lr, ad.b1, ad.b2, ad.eps, ad.ibc1, ad.ibc2);
     m[addr] = mm;
     v[addr] = vv;
-    const float mh = mm / ad.bc1, vh = vv / ad.bc2;
-    Dnext[addr] = pd[k] - ad.lr * mh / (sqrtf(vh) + ad.eps);
+    Dnext[addr] = dn;
   };
   if (TV) {
     tv_sweep(
@@ -397,10 +396,10 @@ __global__ void __launch_bounds__(TV_THREADS, TV_BLOCKS_PER_SM) k_tv_adam(
 __global__ void __launch_bounds__(256) k_adam(const int32_t* __restrict__ active, int64_t n_active,
                                               const uint32_t* __restrict__ masks, const float* __restrict__ grad,
                                               float* __restrict__ D, float* __restrict__ m, float* __restrict__ v,
-                                              float lr, float b1, float b2, float eps, float bc1, float bc2) {
+                                              float lr, float b1, float b2, float eps, float ibc1, float ibc2) {
   const int64_t n = n_active * 128;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    adam_quad(__ldg(active + (i >> 7)), (int)(i & 127), masks, grad, D, m, v, lr, b1, b2, eps, bc1, bc2);
+    adam_quad(__ldg(active + (i >> 7)), (int)(i & 127), masks, grad, D, m, v, lr, b1, b2, eps, ibc1, ibc2);
 }
 
 // One resident wave of k_query: each thread takes several records and the
@@ -535,7 +534,7 @@ extern "C" gp_status gp_update(gp_band* b, const float* grad_dev, const gp_adam*
   int64_t cap = (int64_t)ctx->num_sms * 8;
   GP_KERNEL(ctx, "k_adam", k_adam<<<gp_blocks(b->n_active * 128, 256, cap), 256, 0, ctx->stream>>>(b->active, b->n_active, b->masks, grad_dev, b->D,
                                                                   b->m, b->v, hp->lr, hp->beta1, hp->beta2, hp->eps,
-                                                                  (float)bc1, (float)bc2));
+                                                                  (float)(1.0 / bc1), (float)(1.0 / bc2)));
   return GP_OK;
 }
 
@@ -706,8 +705,8 @@ extern "C" gp_status gp_step_update(gp_band* b, const float* rec_dev, int64_t B,
   ad.b1 = hp->beta1;
   ad.b2 = hp->beta2;
   ad.eps = hp->eps;
-  ad.bc1 = (float)(1.0 - std::pow((double)hp->beta1, (double)step));
-  ad.bc2 = (float)(1.0 - std::pow((double)hp->beta2, (double)step));
+  ad.ibc1 = (float)(1.0 / (1.0 - std::pow((double)hp->beta1, (double)step)));
+  ad.ibc2 = (float)(1.0 / (1.0 - std::pow((double)hp->beta2, (double)step)));
   const float tv_scale = (tv_on && b->V_tv > 0) ? w->alpha / (float)b->V_tv : 0.f;
   gp_prof_pre(ctx);
 #define GP_TVA(D_, T_)                                                                                             \

@@ -681,13 +681,30 @@ __device__ __forceinline__ void tv_sweep(const Src& src, int64_t first, int64_t 
   cp_async_wait0();
 }
 
-// Adam (Kingma and Ba) on the trainable vertices among 4q .. 4q + 3 of brick
-// `slot` (q in [0, 128)): one 16-byte load and store per array.  Vertices of
-// the quad that are not trainable are written back unchanged.
+// One Adam step (Kingma and Ba; Sec. 4 "Details") of one vertex, the bias
+// corrections given as their reciprocals ibc = 1 / (1 - beta^t):
+//   m <- b1 m + (1 - b1) g,  v <- b2 v + (1 - b2) g^2,
+//   d <- d - lr (m ibc1) / (sqrt(v ibc2) + eps).
+// The root is x rsqrt(x) and the division __fdividef: a few ulp each, far
+// inside the step's tolerance, and neither has a slow path.
+__device__ __forceinline__ float adam_elem(float g, float& m, float& v, float d, float lr, float b1, float b2,
+                                           float eps, float ibc1, float ibc2) {
+  const float mm = fmaf(b1, m, (1.0f - b1) * g);
+  const float vv = fmaf(b2, v, (1.0f - b2) * g * g);
+  m = mm;
+  v = vv;
+  const float mh = mm * ibc1, vh = vv * ibc2;
+  const float root = (vh > 0.f && vh < INFINITY) ? vh * rsqrtf(vh) : vh;
+  return d - __fdividef(lr * mh, root + eps);
+}
+
+// Adam on the trainable vertices among 4q .. 4q + 3 of brick `slot` (q in
+// [0, 128)): one 16-byte load and store per array.  Vertices of the quad that
+// are not trainable are written back unchanged.
 __device__ __forceinline__ void adam_quad(int slot, int q, const uint32_t* __restrict__ masks,
                                           const float* __restrict__ grad, float* __restrict__ D,
                                           float* __restrict__ m, float* __restrict__ v, float lr, float b1, float b2,
-                                          float eps, float bc1, float bc2) {
+                                          float eps, float ibc1, float ibc2) {
   const uint32_t bits = (__ldg(masks + (int64_t)slot * 48 + 16 + (q >> 3)) >> ((4 * q) & 31)) & 15u;
   if (!bits) return;
   const int64_t a = (int64_t)slot * 512 + 4 * q;
@@ -695,20 +712,14 @@ __device__ __forceinline__ void adam_quad(int slot, int q, const uint32_t* __res
   float4 m4 = *reinterpret_cast<const float4*>(m + a);
   float4 v4 = *reinterpret_cast<const float4*>(v + a);
   float4 d4 = *reinterpret_cast<const float4*>(D + a);
-  float* gp = reinterpret_cast<float*>(const_cast<float4*>(&g4));
+  const float* gp = reinterpret_cast<const float*>(&g4);
   float* mp = reinterpret_cast<float*>(&m4);
   float* vp = reinterpret_cast<float*>(&v4);
   float* dp = reinterpret_cast<float*>(&d4);
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     if (!((bits >> k) & 1u)) continue;
-    const float g = gp[k];
-    const float mm = fmaf(b1, mp[k], (1.0f - b1) * g);
-    const float vv = fmaf(b2, vp[k], (1.0f - b2) * g * g);
-    mp[k] = mm;
-    vp[k] = vv;
-    const float mh = mm / bc1, vh = vv / bc2;
-    dp[k] -= lr * mh / (sqrtf(vh) + eps);
+    dp[k] = adam_elem(gp[k], mp[k], vp[k], dp[k], lr, b1, b2, eps, ibc1, ibc2);
   }
   *reinterpret_cast<float4*>(m + a) = m4;
   *reinterpret_cast<float4*>(v + a) = v4;
