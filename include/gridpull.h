@@ -272,12 +272,34 @@ typedef struct gp_loss_w {
  * counts it); otherwise gp_step counts them first.  If d_dev is not NULL the values are
  * read from it (V_stored floats) instead of the band's own.  Errors:
  * GP_ERR_ARG (B < 0, null rec/loss, B >= 2^31, rec_dev not 8-byte aligned,
- * grad_dev not 16-byte aligned: its corner pairs are added as vector reductions),
+ * grad_dev not 16-byte aligned: its corner pairs are added as vector reductions;
+ * d_dev not 16-byte aligned: corners are read as vectors and bricks copied in bulk),
  * GP_ERR_STATE (deterministic
  * flag on a band built without GP_BAND_DETERMINISTIC). */
 gp_status gp_step(gp_band* band, const float* rec_dev, int64_t B, const int32_t* nvalid_dev,
                   const float* d_dev, const gp_loss_w* w, float* grad_dev, float* loss_dev,
                   uint32_t flags);
+
+/* Forms of the atomic-mode query pass (gp_step, gp_step_update; the
+ * deterministic sums always take the direct form).  All give the same
+ * results up to the order of the float additions.
+ *   GP_QUERY_DIRECT: every record's 16 corner contributions go to the
+ *     gradient as global vector reductions (8 or 16 bytes per cell edge).
+ *   GP_QUERY_WINDOW: tiles of 512 consecutive records; each tile's window is
+ *     the 3 x 3 x 3 bricks around the brick of its middle record's NN(q).
+ *     Cells inside the window add their corner gradients into a shared-memory
+ *     copy of the window, written to the gradient once per tile (one 16-byte
+ *     reduction per non-zero group of four slots); the other cells take the
+ *     direct path.  Pays off on batches in spatial order (gp_sample with
+ *     GP_SAMPLE_SPATIAL), whose consecutive records share corners.
+ *   GP_QUERY_WINDOW_STAGED: as GP_QUERY_WINDOW, and the window bricks' values
+ *     and pull-band masks are staged in shared memory by bulk copies
+ *     (cp.async.bulk), so that in-window cells read no global memory.
+ * The gradient the corners of a cell receive is the derivative of Eq. 3-7
+ * at its record, as in the direct form. */
+#define GP_QUERY_DIRECT 0
+#define GP_QUERY_WINDOW 1
+#define GP_QUERY_WINDOW_STAGED 2
 
 /* Chooses the launch shape of gp_step's fused forward + backward kernel: the
  * records each thread keeps in flight (*rpt_out = 1 or 2; with 2, both
@@ -286,7 +308,9 @@ gp_status gp_step(gp_band* band, const float* rec_dev, int64_t B, const int32_t*
  * cap of 128, 80 or 64 registers per thread), by timing each candidate with
  * CUDA events on the B records rec_dev (a representative batch, e.g. from
  * gp_nn; nvalid_dev as for gp_step, NULL = counted here).  The choice is kept
- * in the band and used by later gp_step calls.  Reads the band's values,
+ * in the band and used by later gp_step calls; the windowed forms
+ * (GP_QUERY_WINDOW, GP_QUERY_WINDOW_STAGED) are timed too, and the form of the
+ * fastest candidate is kept (gp_band_query_shape reads it).  Reads the band's values,
  * writes nothing of the band but the choice; allocates and frees a scratch
  * gradient; synchronises.  rpt_out, bps_out may be NULL.  Errors: GP_ERR_ARG
  * (B outside (0, 2^31), null records or weights, misaligned records),
@@ -297,6 +321,15 @@ gp_status gp_band_autotune(gp_band* band, const float* rec_dev, int64_t B, const
 /* Sets that launch shape directly: rpt records per thread (1 or 2) and bps
  * blocks per SM (2, 3 or 4).  Errors: GP_ERR_ARG. */
 gp_status gp_band_set_query_tiles(gp_band* band, int32_t rpt, int32_t bps);
+
+/* Sets the form of the atomic-mode query pass (GP_QUERY_*).  gp_band_autotune
+ * also times the two windowed forms (after the direct shapes) and keeps the
+ * fastest of all.  Errors: GP_ERR_ARG. */
+gp_status gp_band_set_query_form(gp_band* band, int32_t form);
+
+/* The band's current query-pass choice: records per thread, blocks per SM
+ * (direct form) and the form (GP_QUERY_*).  Any pointer may be NULL. */
+gp_status gp_band_query_shape(const gp_band* band, int32_t* rpt_out, int32_t* bps_out, int32_t* form_out);
 
 /* ----------------------------------------------------------------- update */
 

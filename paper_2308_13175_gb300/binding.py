@@ -21,6 +21,9 @@ GP_STEP_DETERMINISTIC = 1
 GP_STEP_NO_TV = 2
 GP_STEP_LOSS_ONLY = 4
 GP_SAMPLE_SPATIAL = 1
+GP_QUERY_DIRECT = 0
+GP_QUERY_WINDOW = 1
+GP_QUERY_WINDOW_STAGED = 2
 GP_MULTI_DETERMINISTIC = 2
 GP_LOSS_TOTAL, GP_LOSS_PULL, GP_LOSS_GRAD, GP_LOSS_SURF, GP_LOSS_TV, GP_LOSS_BV, GP_LOSS_T = range(7)
 
@@ -94,6 +97,8 @@ SIGNATURES = {
     "gp_step_update": (ctypes.c_int, [_vp, _vp, _i64, _vp, ctypes.POINTER(LossW), ctypes.POINTER(Adam), _i64, _vp,
                                       _u32]),
     "gp_band_set_query_tiles": (ctypes.c_int, [_vp, _i32, _i32]),
+    "gp_band_set_query_form": (ctypes.c_int, [_vp, _i32]),
+    "gp_band_query_shape": (ctypes.c_int, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
     "gp_band_autotune": (ctypes.c_int, [_vp, _vp, _i64, _vp, ctypes.POINTER(LossW), ctypes.POINTER(_i32),
                                         ctypes.POINTER(_i32)]),
     "gp_multi_create": (ctypes.c_int, [_vp, ctypes.POINTER(_vp), _i32, ctypes.POINTER(_i64), ctypes.POINTER(_i64),
@@ -448,8 +453,9 @@ def gp_step(band: Band, rec, B: int, grad, loss, weights=(1.0, 1.0, 0.005), nval
 
 
 def gp_band_autotune(band: Band, rec, B: int, weights=(1.0, 1.0, 0.005), nvalid=None) -> dict:
-    """Times the fused step kernel's launch shapes on these records and keeps
-    the fastest in the band; returns {"records_per_thread", "blocks_per_sm"}."""
+    """Times the fused step kernel's launch shapes and forms on these records
+    and keeps the fastest in the band; returns {"records_per_thread",
+    "blocks_per_sm", "form"} (form: GP_QUERY_*)."""
     import torch
     _need(rec, torch.float32, 6 * B, "records")
     _need(nvalid, torch.int32, 1, "nvalid")
@@ -458,7 +464,7 @@ def gp_band_autotune(band: Band, rec, B: int, weights=(1.0, 1.0, 0.005), nvalid=
     band.ctx.sync_stream()
     band.ctx.check(band.ctx.lib.gp_band_autotune(band.handle, _ptr(rec), int(B), _ptr(nvalid), ctypes.byref(w),
                                                  ctypes.byref(rpt), ctypes.byref(bps)))
-    return {"records_per_thread": rpt.value, "blocks_per_sm": bps.value}
+    return gp_band_query_shape(band)
 
 
 def gp_step_update(band: Band, rec, B: int, loss, lr: float, step: int, weights=(1.0, 1.0, 0.005), nvalid=None,
@@ -478,6 +484,17 @@ def gp_step_update(band: Band, rec, B: int, loss, lr: float, step: int, weights=
 
 def gp_band_set_query_tiles(band: Band, records_per_thread: int, blocks_per_sm: int):
     band.ctx.check(band.ctx.lib.gp_band_set_query_tiles(band.handle, int(records_per_thread), int(blocks_per_sm)))
+
+
+def gp_band_set_query_form(band: Band, form: int):
+    band.ctx.check(band.ctx.lib.gp_band_set_query_form(band.handle, int(form)))
+
+
+def gp_band_query_shape(band: Band) -> dict:
+    rpt, bps, form = _i32(0), _i32(0), _i32(0)
+    band.ctx.check(band.ctx.lib.gp_band_query_shape(band.handle, ctypes.byref(rpt), ctypes.byref(bps),
+                                                    ctypes.byref(form)))
+    return {"records_per_thread": rpt.value, "blocks_per_sm": bps.value, "form": form.value}
 
 
 def gp_update(band: Band, grad, lr: float, step: int, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8):

@@ -98,6 +98,9 @@ struct gp_band {
   // resident blocks per SM it is compiled for), set by gp_band_autotune.
   int q_rpt = 1;
   int q_bps = 3;
+  // Form of the (atomic-mode) query pass: GP_QUERY_DIRECT, GP_QUERY_WINDOW
+  // or GP_QUERY_WINDOW_STAGED, also chosen by gp_band_autotune.
+  int q_form = GP_QUERY_DIRECT;
 
   // Scratch for reductions and counters.
   double* partials = nullptr;      // GP_MAX_PARTIAL_BLOCKS x 8

@@ -21,6 +21,7 @@
 
 #include "gp_internal.cuh"
 #include "gp_step_device.cuh"
+#include "gp_query_win.cuh"
 
 namespace {
 
@@ -197,6 +198,102 @@ cudaError_t launch_query_ilp(gp_ctx* ctx, int64_t B, cudaStream_t s, Grid G, con
   return cudaGetLastError();
 }
 
+// The windowed form (gp_query_win.cuh): tiles of WQ_TILE records, a
+// persistent grid of 2 blocks per SM, each tile's window set up
+// by warp 0 during the previous tile and, when staged, its bricks copied
+// while the previous tile's window is written out.  Atomic mode only.
+template <bool STAGE, bool LAST>
+__global__ void __launch_bounds__(WQ_THREADS, 2)
+    k_query_win(Grid G, const int32_t* __restrict__ nbrs, const float* __restrict__ rec, int64_t B,
+                const int32_t* __restrict__ bv, float beta, float gamma, float* __restrict__ grad,
+                double* __restrict__ partials, int32_t* __restrict__ err, FinalArgs fa) {
+  extern __shared__ __align__(128) unsigned char wq_smem[];
+  float* acc = reinterpret_cast<float*>(wq_smem);
+  float* val = acc + WIN_V;
+  uint32_t* pull = reinterpret_cast<uint32_t*>(val + WIN_V);
+  __shared__ int sh_slot[2][WIN_BRICKS];
+  __shared__ int sh_lo[2][3];
+  __shared__ uint32_t sh_present[2];
+  __shared__ int sh_abort;
+  __shared__ __align__(8) unsigned long long sh_bar;
+
+  for (int i = threadIdx.x; i < WIN_V / 4; i += WQ_THREADS)
+    reinterpret_cast<float4*>(acc)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  const int64_t ntiles = (B + WQ_TILE - 1) / WQ_TILE;
+  int64_t tile = blockIdx.x;
+  if (threadIdx.x < 32) win_setup(G, nbrs, rec, B, tile, ntiles, sh_slot[0], sh_lo[0], &sh_present[0]);
+  if (threadIdx.x == 0) {
+    sh_abort = 0;
+    if (STAGE) mbar_init(&sh_bar, 1);
+  }
+  __syncthreads();
+  if (STAGE && threadIdx.x == 0 && tile < ntiles && sh_present[0])
+    win_issue(G, sh_slot[0], sh_present[0], val, pull, &sh_bar);
+  uint32_t parity = 0;  // of the barrier phase the next staged tile completes
+  const int bvv = *bv;
+  const float w = bvv > 0 ? 1.0f / (float)bvv : 0.f;
+  float sp = 0.f, sg = 0.f, ss = 0.f;
+  for (int it = 0; tile < ntiles; ++it, tile += gridDim.x) {
+    const int p = it & 1;
+    Win W;
+    W.lo[0] = sh_lo[p][0];
+    W.lo[1] = sh_lo[p][1];
+    W.lo[2] = sh_lo[p][2];
+    W.present = sh_present[p];
+    const int64_t next = tile + gridDim.x;
+    if (threadIdx.x < 32) win_setup(G, nbrs, rec, B, next, ntiles, sh_slot[p ^ 1], sh_lo[p ^ 1], &sh_present[p ^ 1]);
+    RecState R[WQ_RPT];
+#pragma unroll
+    for (int r = 0; r < WQ_RPT; ++r) {
+      const int64_t i = tile * WQ_TILE + r * WQ_THREADS + threadIdx.x;
+      float q[3] = {0.f, 0.f, 0.f}, s[3] = {0.f, 0.f, 0.f};
+      if (i < B) load_rec(rec, i, q, s);
+      win_phase_a<STAGE>(G, W, sh_slot[p], q, s, i < B, R[r]);
+    }
+    if (STAGE && W.present) {
+      if (!mbar_wait(&sh_bar, parity)) {
+        atomicOr(err, GP_EF_TIMEOUT);
+        sh_abort = 1;
+      }
+      parity ^= 1u;
+    }
+#pragma unroll
+    for (int r = 0; r < WQ_RPT; ++r) win_phase_b<STAGE>(G, W, sh_slot[p], val, pull, R[r]);
+    WindowSink sink{G, grad, acc, W, err};
+#pragma unroll
+    for (int r = 0; r < WQ_RPT; ++r) rec_phase_c<true>(G, R[r], w, beta, gamma, sink, err, sp, sg, ss);
+    __syncthreads();
+    const bool abort = sh_abort != 0;
+    if (STAGE && threadIdx.x == 0 && !abort && next < ntiles && sh_present[p ^ 1])
+      win_issue(G, sh_slot[p ^ 1], sh_present[p ^ 1], val, pull, &sh_bar);
+    win_flush(acc, sh_slot[p], grad);
+    __syncthreads();
+    if (abort) {
+      // The copies of the phase that ran out may still be in flight: wait
+      // for them (bounded) before the block leaves.
+      if (STAGE && threadIdx.x == 0) mbar_wait(&sh_bar, parity ^ 1u);
+      break;
+    }
+  }
+  block_store3(partials, sp, sg, ss);
+  if (LAST) finish_if_last(partials, fa);
+}
+
+template <bool STAGE, bool LAST>
+cudaError_t launch_query_win(gp_ctx* ctx, const int32_t* nbrs, int64_t B, cudaStream_t s, Grid G, const float* rec,
+                             const int32_t* bv, float beta, float gamma, float* grad, double* partials, int32_t* err,
+                             FinalArgs& fa) {
+  const size_t smem = STAGE ? WQ_SMEM_STAGED : WQ_SMEM_ACC;
+  cudaError_t e = cudaFuncSetAttribute(k_query_win<STAGE, LAST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  const int per_sm = 2;
+  const unsigned grid = gp_blocks(B, WQ_TILE, std::min<int64_t>((int64_t)ctx->num_sms * per_sm, GP_MAX_PARTIAL_BLOCKS));
+  fa.q_blocks = (int)grid;
+  k_query_win<STAGE, LAST><<<grid, WQ_THREADS, smem, s>>>(G, nbrs, rec, B, bv, beta, gamma, grad, partials, err, fa);
+  return cudaGetLastError();
+}
+
 // The tuned launch shape: RPT in {1, 2} records per thread, MINB in {2, 3, 4}.
 template <bool DET, bool LAST>
 cudaError_t launch_query_tuned(const gp_band* b, int64_t B, cudaStream_t s, Grid G, const float* rec,
@@ -204,6 +301,10 @@ cudaError_t launch_query_tuned(const gp_band* b, int64_t B, cudaStream_t s, Grid
                                int32_t* err, FinalArgs& fa) {
   gp_ctx* ctx = b->ctx;
   unsigned long long* acc = b->acc;
+  if (!DET && b->q_form == GP_QUERY_WINDOW_STAGED)
+    return launch_query_win<true, LAST>(ctx, b->brick_nbr, B, s, G, rec, bv, beta, gamma, grad, partials, err, fa);
+  if (!DET && b->q_form == GP_QUERY_WINDOW)
+    return launch_query_win<false, LAST>(ctx, b->brick_nbr, B, s, G, rec, bv, beta, gamma, grad, partials, err, fa);
   if (b->q_rpt == 2) {
     if (b->q_bps == 2)
       return launch_query_ilp<DET, LAST, 2, 2>(ctx, B, s, G, rec, bv, beta, gamma, grad, acc, partials, err, fa);
@@ -432,6 +533,7 @@ extern "C" gp_status gp_step(gp_band* b, const float* rec_dev, int64_t B, const 
   if (((uintptr_t)rec_dev & 7u) != 0) return gp_fail(ctx, GP_ERR_ARG, "gp_step: records must be 8-byte aligned");
   if (((uintptr_t)grad_dev & 15u) != 0)
     return gp_fail(ctx, GP_ERR_ARG, "gp_step: the gradient must be 16-byte aligned");
+  if (((uintptr_t)d_dev & 15u) != 0) return gp_fail(ctx, GP_ERR_ARG, "gp_step: the values must be 16-byte aligned");
   if (det && grad_on && !b->acc)
     return gp_fail(ctx, GP_ERR_STATE, "gp_step: deterministic mode needs a band built with GP_BAND_DETERMINISTIC");
   cudaStream_t s = ctx->stream;
@@ -585,7 +687,8 @@ extern "C" gp_status gp_band_autotune(gp_band* b, const float* rec_dev, int64_t 
   int best_rpt = b->q_rpt, best_bps = b->q_bps;
   float best = INFINITY;
   const int rpts[2] = {1, 2}, bpss[3] = {2, 3, 4};
-  const int save_rpt = b->q_rpt, save_bps = b->q_bps;
+  const int save_rpt = b->q_rpt, save_bps = b->q_bps, save_form = b->q_form;
+  b->q_form = GP_QUERY_DIRECT;
   for (int ri = 0; ri < 2 && e == cudaSuccess; ++ri) {
     for (int bi = 0; bi < 3 && e == cudaSuccess; ++bi) {
       b->q_rpt = rpts[ri];
@@ -619,6 +722,38 @@ extern "C" gp_status gp_band_autotune(gp_band* b, const float* rec_dev, int64_t 
       }
     }
   }
+  // The windowed forms, timed the same way.
+  int best_form = GP_QUERY_DIRECT;
+  const int forms[2] = {GP_QUERY_WINDOW, GP_QUERY_WINDOW_STAGED};
+  for (int fi = 0; fi < 2 && e == cudaSuccess; ++fi) {
+    b->q_form = forms[fi];
+    FinalArgs fa;
+    fa.done = b->dev_ints + GP_DI_DONE;
+    fa.q_blocks = 0;
+    fa.tv_blocks = 0;
+    fa.bv = bv;
+    fa.n_tv = b->V_tv;
+    fa.alpha = w->alpha;
+    fa.beta = w->beta;
+    fa.gamma = w->gamma;
+    fa.tv_on = 0;
+    fa.loss = loss;
+    auto launch = [&]() -> cudaError_t {
+      return launch_query_tuned<false, true>(b, B, s, G, rec_dev, bv, w->beta, w->gamma, grad, b->partials, err, fa);
+    };
+    e = launch();
+    if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = launch();
+    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e == cudaSuccess && ms < best) {
+      best = ms;
+      best_form = forms[fi];
+    }
+  }
+  b->q_form = save_form;
   b->q_rpt = save_rpt;
   b->q_bps = save_bps;
   if (e0) cudaEventDestroy(e0);
@@ -629,6 +764,7 @@ extern "C" gp_status gp_band_autotune(gp_band* b, const float* rec_dev, int64_t 
   if (e != cudaSuccess) return gp_cuda_fail(ctx, e, "gp_band_autotune");
   b->q_rpt = best_rpt;
   b->q_bps = best_bps;
+  b->q_form = best_form;
   if (rpt_out) *rpt_out = best_rpt;
   if (bps_out) *bps_out = best_bps;
   return GP_OK;
@@ -640,6 +776,22 @@ extern "C" gp_status gp_band_set_query_tiles(gp_band* b, int32_t rpt, int32_t bp
     return gp_fail(b->ctx, GP_ERR_ARG, "gp_band_set_query_tiles: rpt must be 1 or 2 and bps 2, 3 or 4");
   b->q_rpt = rpt;
   b->q_bps = bps;
+  return GP_OK;
+}
+
+extern "C" gp_status gp_band_set_query_form(gp_band* b, int32_t form) {
+  if (!b) return GP_ERR_ARG;
+  if (form != GP_QUERY_DIRECT && form != GP_QUERY_WINDOW && form != GP_QUERY_WINDOW_STAGED)
+    return gp_fail(b->ctx, GP_ERR_ARG, "gp_band_set_query_form: form must be a GP_QUERY_* value");
+  b->q_form = form;
+  return GP_OK;
+}
+
+extern "C" gp_status gp_band_query_shape(const gp_band* b, int32_t* rpt_out, int32_t* bps_out, int32_t* form_out) {
+  if (!b) return GP_ERR_ARG;
+  if (rpt_out) *rpt_out = b->q_rpt;
+  if (bps_out) *bps_out = b->q_bps;
+  if (form_out) *form_out = b->q_form;
   return GP_OK;
 }
 

@@ -487,6 +487,76 @@ def _spatial_order(q, R):
     return np.argsort(cq[:, 0] + R * (cq[:, 1] + R * cq[:, 2]), kind="stable")
 
 
+def _morton_order(s, R):
+    """Records sorted by the Morton code of the cell of s, as the sampler's
+    spatial batches list their source points."""
+    c = np.clip(np.floor((s.astype(np.float64) + 1) * R / 2).astype(np.int64), 0, R - 1)
+    code = np.zeros(len(s), np.int64)
+    for b in range(11):
+        for a in range(3):
+            code |= ((c[:, a] >> b) & 1) << (3 * b + a)
+    return np.argsort(code, kind="stable")
+
+
+@pytest.mark.parametrize("form", ["window", "window_staged"])
+def test_step_windowed_forms_match_oracle(gb, ctx, object100k, sphere5k, form):
+    """The windowed query pass (a tile's in-window corner gradients summed in
+    shared memory and written once; with staging, the window bricks copied in
+    bulk) against the oracle: records in Morton order of their source cell
+    (most cells in the window) in a batch of several tiles per block with a
+    ragged last tile, the same records in random order (few in the window),
+    batches shorter than a tile, tiles whose anchor record is outside the
+    band or not finite, records in one cell, and a dense grid whose windows
+    meet the grid boundary."""
+    import torch
+    f = gb.GP_QUERY_WINDOW if form == "window" else gb.GP_QUERY_WINDOW_STAGED
+    R = 256
+    band = _band(gb, ctx, object100k, R, 2, 2, knn_k=0)
+    c = 0.5 * (object100k.min(0) + object100k.max(0))
+    sets, q, s = _step_inputs(object100k, R, 2, 2, 400_123, 2.0 / R, seed=41, use_nn=False)
+    D, _ = _set_field(gb, band, sets, R, 0.3, 2e-3, seed=42, center=c)
+    gb.gp_band_set_query_form(band, f)
+    assert gb.gp_band_query_shape(band)["form"] == f
+    order = _morton_order(s, R)
+    qo, so = q[order], s[order]
+    ref = _check_step(gb, band, R, sets, qo, so, (1.0, 1.0, 0.005), D)
+    assert ref["Bv"] > 350_000
+    _check_step(gb, band, R, sets, q[:150_000], s[:150_000], (2.0, 0.5, 0.3), D)
+    for n in (1, 100, 513):
+        _check_step(gb, band, R, sets, qo[:n], so[:n], (1.0, 1.0, 0.005), D)
+    # Anchors outside the band (a far corner of the domain) and not finite:
+    # those tiles take the direct path for every cell.
+    qa, sa = qo[:2048].copy(), so[:2048].copy()
+    sa[256] = (0.99, 0.99, 0.99)
+    sa[512 + 256] = (np.nan, 0.0, 0.0)
+    _check_step(gb, band, R, sets, qa, sa, (1.0, 1.0, 0.005), D)
+    # Every record in one cell: all contributions meet on the same 8 slots.
+    Rs = 64
+    bs = _band(gb, ctx, sphere5k, Rs, 2, 2, knn_k=0)
+    gb.gp_band_set_query_form(bs, f)
+    sets_s = o.band_sets(sphere5k, Rs, 2, 2)
+    Ds, _ = _set_field(gb, bs, sets_s, Rs, 0.5, 0.05, seed=43)
+    h = 2.0 / Rs
+    cell = np.floor((sphere5k[0].astype(np.float64) + 1) / h)
+    rng = np.random.default_rng(44)
+    q1 = (-1 + h * (cell + rng.uniform(0.05, 0.95, size=(3000, 3)))).astype(np.float32)
+    ref = _check_step(gb, bs, Rs, sets_s, q1, np.repeat(sphere5k[:1], len(q1), axis=0), (1.0, 1.0, 0.005), Ds)
+    assert ref["Bv"] > 2500
+    # Dense grid: the windows of bricks on the grid boundary.
+    bd = _band(gb, ctx, sphere5k, Rs, -1, -1, knn_k=0)
+    gb.gp_band_set_query_form(bd, f)
+    sets_d, qd, sd = _step_inputs(sphere5k, Rs, -1, -1, 30_000, 4.0 / Rs, seed=45, use_nn=True)
+    Dd, _ = _set_field(gb, bd, sets_d, Rs, 0.5, 0.1, seed=46)
+    od = _morton_order(sd, Rs)
+    _check_step(gb, bd, Rs, sets_d, qd[od], sd[od], (1.0, 1.0, 0.005), Dd)
+    # A changed form and a bad one.
+    with pytest.raises(gb.GridPullError):
+        gb.gp_band_set_query_form(band, 3)
+    gb.gp_band_check(band)
+    gb.gp_band_check(bs)
+    gb.gp_band_check(bd)
+
+
 @pytest.mark.parametrize("rpt,bps", [(1, 2), (1, 3), (1, 4), (2, 2), (2, 3), (2, 4)])
 def test_step_tile_shapes_match_oracle(gb, ctx, object100k, rpt, bps):
     """The fused step kernel at every launch shape the autotuner can pick, on
@@ -551,6 +621,8 @@ def test_autotune_picks_a_shape_and_leaves_the_band(gb, ctx, object100k):
     before = gb.gp_band_values(band)[0].clone()
     tune = gb.gp_band_autotune(band, rec, len(q))
     assert tune["records_per_thread"] in (1, 2) and tune["blocks_per_sm"] in (2, 3, 4)
+    assert tune["form"] in (gb.GP_QUERY_DIRECT, gb.GP_QUERY_WINDOW, gb.GP_QUERY_WINDOW_STAGED)
+    assert gb.gp_band_query_shape(band) == tune
     assert torch.equal(before, gb.gp_band_values(band)[0])
     _check_step(gb, band, R, sets, q[order], s[order], (1.0, 1.0, 0.005), D)
     with pytest.raises(gb.GridPullError):
@@ -568,6 +640,10 @@ def test_step_rejects_misaligned_buffers(gb, ctx, sphere5k):
         gb.gp_step(band, rec, 10, grad[1:], loss)                  # gradient off by 4 bytes
     with pytest.raises(gb.GridPullError):
         gb.gp_step(band, rec.view(-1)[1:], 10, grad[:band.V_stored], loss)  # records off by 4 bytes
+    vals = torch.zeros(band.V_stored + 4, dtype=torch.float32, device="cuda")
+    gb.gp_step(band, rec, 10, grad[4:], loss, d=vals[4:])             # 16-byte aligned values
+    with pytest.raises(gb.GridPullError):
+        gb.gp_step(band, rec, 10, grad[4:], loss, d=vals[1:band.V_stored + 1])  # values off by 4 bytes
 
 
 def test_step_deterministic_needs_band_flag(gb, ctx, sphere5k):
@@ -659,8 +735,8 @@ def test_pipelined_steps_equal_sequential_steps(gb, ctx, sphere5k):
     gb.gp_band_check(bands[1])
 
 
-@pytest.mark.parametrize("det", [False, True])
-def test_step_update_equals_step_then_update(gb, ctx, object100k, det):
+@pytest.mark.parametrize("det,form", [(False, 0), (True, 0), (False, 2)])
+def test_step_update_equals_step_then_update(gb, ctx, object100k, det, form):
     """gp_step_update (query pass, then one sweep computing L_TV, adding the
     query part and applying Adam into the second value buffer) against
     gp_step then gp_update on an identical band: values, moments and loss
@@ -672,6 +748,10 @@ def test_step_update_equals_step_then_update(gb, ctx, object100k, det):
     sets, q, s = _step_inputs(object100k, R, 2, 2, 80_000, 2.0 / R, seed=31, use_nn=False)
     for band in bands:
         _set_field(gb, band, sets, R, 0.3, 2e-3, seed=32, center=c)
+        gb.gp_band_set_query_form(band, form)
+    if form:
+        order = _morton_order(s, R)
+        q, s = q[order], s[order]
     rec = torch.from_numpy(np.ascontiguousarray(np.concatenate([q, s], axis=1), np.float32)).cuda()
     flags = gb.GP_STEP_DETERMINISTIC if det else 0
     grad = torch.empty(bands[0].V_stored, dtype=torch.float32, device="cuda")
