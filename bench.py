@@ -442,6 +442,37 @@ def run_reference(args, world, rank):
 
 
 # ------------------------------------------------------------- our arm
+def query_form_times(gb, ctx, band, fit, tuned, workload, reps):
+    """The query kernel's time (CUDA events of the library's tracing, µs per
+    launch) in every form and launch shape gp_band_autotune chooses among, on
+    step 0's batch; the band's choice is restored afterwards."""
+    import torch
+    from paper_2308_13175_gb300.fit import PAPER_WEIGHTS
+    epoch, first, count = fit.batch_of(0)
+    cands = [(f, r, b) for f in (gb.GP_QUERY_DIRECT, gb.GP_QUERY_WINDOW) for r in (1, 2) for b in (2, 3, 4)]
+    cands += [(gb.GP_QUERY_WINDOW_STAGED, r, 2) for r in (1, 2)]
+    names = {gb.GP_QUERY_DIRECT: "direct", gb.GP_QUERY_WINDOW: "window", gb.GP_QUERY_WINDOW_STAGED: "window_staged"}
+    out = []
+    for f, r, b in cands:
+        gb.gp_band_set_query_form(band, f)
+        gb.gp_band_set_query_tiles(band, r, b)
+        for _ in range(2):
+            gb.gp_step(band, fit.rec, count, fit.grad, fit.loss, PAPER_WEIGHTS, nvalid=fit.nvalid)
+        torch.cuda.synchronize()
+        gb.gp_profile(ctx, True)
+        for _ in range(reps):
+            gb.gp_step(band, fit.rec, count, fit.grad, fit.loss, PAPER_WEIGHTS, nvalid=fit.nvalid)
+        prof = gb.gp_profile_read(ctx)
+        gb.gp_profile(ctx, False)
+        n, ms = prof["k_query"]
+        out.append({"form": names[f], "records_per_thread": r, "blocks_per_sm": b,
+                    "us_per_launch": round(1000.0 * ms / n, 2)})
+    gb.gp_band_set_query_form(band, tuned["form"])
+    gb.gp_band_set_query_tiles(band, tuned["records_per_thread"], tuned["blocks_per_sm"])
+    gb.gp_band_check(band)
+    return {"workload": workload, "records": count, "autotuned": tuned, "query_forms": out}
+
+
 def run_ours(args, world, rank, local):
     import torch
     from paper_2308_13175_gb300 import binding as gb
@@ -486,6 +517,10 @@ def run_ours(args, world, rank, local):
         return ms, queries
 
     tuned = fit.autotune(0)
+    if args.query_forms:
+        print(json.dumps(query_form_times(gb, ctx, band, fit, tuned, args.workload, max(args.steps, 1))))
+        return
+
     def pipelined_steps(first_t, K):
         """K steps as one region, each next batch's draw overlapped with the
         current step (FitStep.run_pipelined); no flush between steps."""
@@ -1025,6 +1060,9 @@ def main():
                     help="time the sequential steps (L2 flushed between them) as the headline")
     ap.add_argument("--deterministic", action="store_true",
                     help="bit-reproducible gradient sums (fixed point) instead of float atomics")
+    ap.add_argument("--query-forms", action="store_true",
+                    help="print the query kernel's time in every form and launch shape the autotuner chooses among "
+                         "(--steps launches each) instead of the bench line")
     ap.add_argument("--m1", type=int, default=None, help="override the pull bandwidth M1 (-1 = all grids)")
     ap.add_argument("--m2", type=int, default=None, help="override the TV bandwidth M2 (-1 = all grids)")
     args = ap.parse_args()

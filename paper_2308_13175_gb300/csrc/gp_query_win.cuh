@@ -1,7 +1,7 @@
 // The windowed form of the fused forward + backward pass (Eq. 3-8 per
 // record, as in gp_step_device.cuh), for batches in spatial order.
 //
-// A block takes tiles of WQ_TILE consecutive records.  Records in spatial
+// A block takes tiles of 256 x RPT consecutive records.  Records in spatial
 // order (the sampler's GP_SAMPLE_SPATIAL batches: by source point, the points
 // in Morton order of their cells) lie close together, and so do the corners
 // their gradients go to.  Each tile gets a window: the 3 x 3 x 3 bricks
@@ -26,8 +26,6 @@
 #include "gp_step_device.cuh"
 
 constexpr int WQ_THREADS = 256;
-constexpr int WQ_RPT = 2;                      // records per thread and tile
-constexpr int WQ_TILE = WQ_THREADS * WQ_RPT;   // 512 records per tile
 constexpr int WIN_BRICKS = 27;                 // 3 x 3 x 3 bricks
 constexpr int WIN_V = WIN_BRICKS * 512;        // 13,824 slots
 // Dynamic shared memory: the gradient window, then (STAGE) the staged values
@@ -197,14 +195,14 @@ __device__ __forceinline__ void win_phase_b(const Grid& G, const Win& W, const i
 // brick the band does not store) or a tile past the end gives an empty
 // window, and every cell of the tile then takes the direct path.
 __device__ __forceinline__ void win_setup(const Grid& G, const int32_t* __restrict__ nbrs,
-                                          const float* __restrict__ rec, int64_t B, int64_t tile, int64_t ntiles,
-                                          int* slot, int* lo, uint32_t* present) {
+                                          const float* __restrict__ rec, int64_t B, int tile_n, int64_t tile,
+                                          int64_t ntiles, int* slot, int* lo, uint32_t* present) {
   const int lane = threadIdx.x & 31;
   int sl = -1;
   int c[3] = {0, 0, 0};
   if (tile < ntiles) {
-    const int64_t t0 = tile * WQ_TILE;
-    const int64_t n = B - t0 < WQ_TILE ? B - t0 : WQ_TILE;
+    const int64_t t0 = tile * tile_n;
+    const int64_t n = B - t0 < tile_n ? B - t0 : tile_n;
     float q[3], s[3];
     load_rec(rec, t0 + n / 2, q, s);
     bool ok = true;

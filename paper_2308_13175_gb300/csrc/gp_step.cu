@@ -198,15 +198,17 @@ cudaError_t launch_query_ilp(gp_ctx* ctx, int64_t B, cudaStream_t s, Grid G, con
   return cudaGetLastError();
 }
 
-// The windowed form (gp_query_win.cuh): tiles of WQ_TILE records, a
-// persistent grid of 2 blocks per SM, each tile's window set up
-// by warp 0 during the previous tile and, when staged, its bricks copied
-// while the previous tile's window is written out.  Atomic mode only.
-template <bool STAGE, bool LAST>
-__global__ void __launch_bounds__(WQ_THREADS, 2)
+// The windowed form (gp_query_win.cuh): tiles of 256 RPT records, a
+// persistent grid of MINB blocks per SM (MINB also caps the registers), each
+// tile's window set up by warp 0 during the previous tile and, when staged,
+// its bricks copied while the previous tile's window is written out.  Atomic
+// mode only.
+template <bool STAGE, bool LAST, int RPT, int MINB>
+__global__ void __launch_bounds__(WQ_THREADS, MINB)
     k_query_win(Grid G, const int32_t* __restrict__ nbrs, const float* __restrict__ rec, int64_t B,
                 const int32_t* __restrict__ bv, float beta, float gamma, float* __restrict__ grad,
                 double* __restrict__ partials, int32_t* __restrict__ err, FinalArgs fa) {
+  constexpr int TILE = WQ_THREADS * RPT;
   extern __shared__ __align__(128) unsigned char wq_smem[];
   float* acc = reinterpret_cast<float*>(wq_smem);
   float* val = acc + WIN_V;
@@ -219,9 +221,9 @@ __global__ void __launch_bounds__(WQ_THREADS, 2)
 
   for (int i = threadIdx.x; i < WIN_V / 4; i += WQ_THREADS)
     reinterpret_cast<float4*>(acc)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-  const int64_t ntiles = (B + WQ_TILE - 1) / WQ_TILE;
+  const int64_t ntiles = (B + TILE - 1) / TILE;
   int64_t tile = blockIdx.x;
-  if (threadIdx.x < 32) win_setup(G, nbrs, rec, B, tile, ntiles, sh_slot[0], sh_lo[0], &sh_present[0]);
+  if (threadIdx.x < 32) win_setup(G, nbrs, rec, B, TILE, tile, ntiles, sh_slot[0], sh_lo[0], &sh_present[0]);
   if (threadIdx.x == 0) {
     sh_abort = 0;
     if (STAGE) mbar_init(&sh_bar, 1);
@@ -241,11 +243,12 @@ __global__ void __launch_bounds__(WQ_THREADS, 2)
     W.lo[2] = sh_lo[p][2];
     W.present = sh_present[p];
     const int64_t next = tile + gridDim.x;
-    if (threadIdx.x < 32) win_setup(G, nbrs, rec, B, next, ntiles, sh_slot[p ^ 1], sh_lo[p ^ 1], &sh_present[p ^ 1]);
-    RecState R[WQ_RPT];
+    if (threadIdx.x < 32)
+      win_setup(G, nbrs, rec, B, TILE, next, ntiles, sh_slot[p ^ 1], sh_lo[p ^ 1], &sh_present[p ^ 1]);
+    RecState R[RPT];
 #pragma unroll
-    for (int r = 0; r < WQ_RPT; ++r) {
-      const int64_t i = tile * WQ_TILE + r * WQ_THREADS + threadIdx.x;
+    for (int r = 0; r < RPT; ++r) {
+      const int64_t i = tile * TILE + r * WQ_THREADS + threadIdx.x;
       float q[3] = {0.f, 0.f, 0.f}, s[3] = {0.f, 0.f, 0.f};
       if (i < B) load_rec(rec, i, q, s);
       win_phase_a<STAGE>(G, W, sh_slot[p], q, s, i < B, R[r]);
@@ -258,10 +261,10 @@ __global__ void __launch_bounds__(WQ_THREADS, 2)
       parity ^= 1u;
     }
 #pragma unroll
-    for (int r = 0; r < WQ_RPT; ++r) win_phase_b<STAGE>(G, W, sh_slot[p], val, pull, R[r]);
+    for (int r = 0; r < RPT; ++r) win_phase_b<STAGE>(G, W, sh_slot[p], val, pull, R[r]);
     WindowSink sink{G, grad, acc, W, err};
 #pragma unroll
-    for (int r = 0; r < WQ_RPT; ++r) rec_phase_c<true>(G, R[r], w, beta, gamma, sink, err, sp, sg, ss);
+    for (int r = 0; r < RPT; ++r) rec_phase_c<true>(G, R[r], w, beta, gamma, sink, err, sp, sg, ss);
     __syncthreads();
     const bool abort = sh_abort != 0;
     if (STAGE && threadIdx.x == 0 && !abort && next < ntiles && sh_present[p ^ 1])
@@ -279,19 +282,43 @@ __global__ void __launch_bounds__(WQ_THREADS, 2)
   if (LAST) finish_if_last(partials, fa);
 }
 
-template <bool STAGE, bool LAST>
+template <bool STAGE, bool LAST, int RPT, int MINB>
 cudaError_t launch_query_win(gp_ctx* ctx, const int32_t* nbrs, int64_t B, cudaStream_t s, Grid G, const float* rec,
                              const int32_t* bv, float beta, float gamma, float* grad, double* partials, int32_t* err,
                              FinalArgs& fa) {
   const size_t smem = STAGE ? WQ_SMEM_STAGED : WQ_SMEM_ACC;
-  cudaError_t e = cudaFuncSetAttribute(k_query_win<STAGE, LAST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(k_query_win<STAGE, LAST, RPT, MINB>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const int per_sm = 2;
-  const unsigned grid = gp_blocks(B, WQ_TILE, std::min<int64_t>((int64_t)ctx->num_sms * per_sm, GP_MAX_PARTIAL_BLOCKS));
+  const unsigned grid = gp_blocks(B, WQ_THREADS * RPT,
+                                  std::min<int64_t>((int64_t)ctx->num_sms * MINB, GP_MAX_PARTIAL_BLOCKS));
   fa.q_blocks = (int)grid;
-  k_query_win<STAGE, LAST><<<grid, WQ_THREADS, smem, s>>>(G, nbrs, rec, B, bv, beta, gamma, grad, partials, err, fa);
+  k_query_win<STAGE, LAST, RPT, MINB><<<grid, WQ_THREADS, smem, s>>>(G, nbrs, rec, B, bv, beta, gamma, grad,
+                                                                      partials, err, fa);
   return cudaGetLastError();
+}
+
+// The windowed forms at the band's launch shape: (RPT, MINB) as for the
+// direct form; the staged form holds 110 KB of shared memory per block, so
+// it runs 2 blocks per SM whatever MINB is.
+template <bool LAST>
+cudaError_t launch_query_window_tuned(const gp_band* b, int64_t B, cudaStream_t s, Grid G, const float* rec,
+                                      const int32_t* bv, float beta, float gamma, float* grad, double* partials,
+                                      int32_t* err, FinalArgs& fa) {
+  gp_ctx* ctx = b->ctx;
+  const int32_t* nb = b->brick_nbr;
+#define GP_QW(ST_, R_, M_) \
+  launch_query_win<ST_, LAST, R_, M_>(ctx, nb, B, s, G, rec, bv, beta, gamma, grad, partials, err, fa)
+  if (b->q_form == GP_QUERY_WINDOW_STAGED) return b->q_rpt == 2 ? GP_QW(true, 2, 2) : GP_QW(true, 1, 2);
+  if (b->q_rpt == 2) {
+    if (b->q_bps == 3) return GP_QW(false, 2, 3);
+    if (b->q_bps == 4) return GP_QW(false, 2, 4);
+    return GP_QW(false, 2, 2);
+  }
+  if (b->q_bps == 3) return GP_QW(false, 1, 3);
+  if (b->q_bps == 4) return GP_QW(false, 1, 4);
+  return GP_QW(false, 1, 2);
+#undef GP_QW
 }
 
 // The tuned launch shape: RPT in {1, 2} records per thread, MINB in {2, 3, 4}.
@@ -301,10 +328,8 @@ cudaError_t launch_query_tuned(const gp_band* b, int64_t B, cudaStream_t s, Grid
                                int32_t* err, FinalArgs& fa) {
   gp_ctx* ctx = b->ctx;
   unsigned long long* acc = b->acc;
-  if (!DET && b->q_form == GP_QUERY_WINDOW_STAGED)
-    return launch_query_win<true, LAST>(ctx, b->brick_nbr, B, s, G, rec, bv, beta, gamma, grad, partials, err, fa);
-  if (!DET && b->q_form == GP_QUERY_WINDOW)
-    return launch_query_win<false, LAST>(ctx, b->brick_nbr, B, s, G, rec, bv, beta, gamma, grad, partials, err, fa);
+  if (!DET && b->q_form != GP_QUERY_DIRECT)
+    return launch_query_window_tuned<LAST>(b, B, s, G, rec, bv, beta, gamma, grad, partials, err, fa);
   if (b->q_rpt == 2) {
     if (b->q_bps == 2)
       return launch_query_ilp<DET, LAST, 2, 2>(ctx, B, s, G, rec, bv, beta, gamma, grad, acc, partials, err, fa);
@@ -722,11 +747,16 @@ extern "C" gp_status gp_band_autotune(gp_band* b, const float* rec_dev, int64_t 
       }
     }
   }
-  // The windowed forms, timed the same way.
+  // The windowed forms at the same shapes (the staged one at 2 blocks per
+  // SM only), timed the same way.
   int best_form = GP_QUERY_DIRECT;
-  const int forms[2] = {GP_QUERY_WINDOW, GP_QUERY_WINDOW_STAGED};
-  for (int fi = 0; fi < 2 && e == cudaSuccess; ++fi) {
-    b->q_form = forms[fi];
+  const int wcand[8][3] = {{GP_QUERY_WINDOW, 1, 2}, {GP_QUERY_WINDOW, 1, 3}, {GP_QUERY_WINDOW, 1, 4},
+                           {GP_QUERY_WINDOW, 2, 2}, {GP_QUERY_WINDOW, 2, 3}, {GP_QUERY_WINDOW, 2, 4},
+                           {GP_QUERY_WINDOW_STAGED, 1, 2}, {GP_QUERY_WINDOW_STAGED, 2, 2}};
+  for (int fi = 0; fi < 8 && e == cudaSuccess; ++fi) {
+    b->q_form = wcand[fi][0];
+    b->q_rpt = wcand[fi][1];
+    b->q_bps = wcand[fi][2];
     FinalArgs fa;
     fa.done = b->dev_ints + GP_DI_DONE;
     fa.q_blocks = 0;
@@ -750,7 +780,9 @@ extern "C" gp_status gp_band_autotune(gp_band* b, const float* rec_dev, int64_t 
     if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
     if (e == cudaSuccess && ms < best) {
       best = ms;
-      best_form = forms[fi];
+      best_form = wcand[fi][0];
+      best_rpt = wcand[fi][1];
+      best_bps = wcand[fi][2];
     }
   }
   b->q_form = save_form;

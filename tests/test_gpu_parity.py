@@ -498,8 +498,9 @@ def _morton_order(s, R):
     return np.argsort(code, kind="stable")
 
 
-@pytest.mark.parametrize("form", ["window", "window_staged"])
-def test_step_windowed_forms_match_oracle(gb, ctx, object100k, sphere5k, form):
+@pytest.mark.parametrize("form,rpt,bps", [("window", 1, 4), ("window", 2, 2), ("window_staged", 1, 2),
+                                          ("window_staged", 2, 2)])
+def test_step_windowed_forms_match_oracle(gb, ctx, object100k, sphere5k, form, rpt, bps):
     """The windowed query pass (a tile's in-window corner gradients summed in
     shared memory and written once; with staging, the window bricks copied in
     bulk) against the oracle: records in Morton order of their source cell
@@ -516,7 +517,8 @@ def test_step_windowed_forms_match_oracle(gb, ctx, object100k, sphere5k, form):
     sets, q, s = _step_inputs(object100k, R, 2, 2, 400_123, 2.0 / R, seed=41, use_nn=False)
     D, _ = _set_field(gb, band, sets, R, 0.3, 2e-3, seed=42, center=c)
     gb.gp_band_set_query_form(band, f)
-    assert gb.gp_band_query_shape(band)["form"] == f
+    gb.gp_band_set_query_tiles(band, rpt, bps)
+    assert gb.gp_band_query_shape(band) == {"records_per_thread": rpt, "blocks_per_sm": bps, "form": f}
     order = _morton_order(s, R)
     qo, so = q[order], s[order]
     ref = _check_step(gb, band, R, sets, qo, so, (1.0, 1.0, 0.005), D)
@@ -534,6 +536,7 @@ def test_step_windowed_forms_match_oracle(gb, ctx, object100k, sphere5k, form):
     Rs = 64
     bs = _band(gb, ctx, sphere5k, Rs, 2, 2, knn_k=0)
     gb.gp_band_set_query_form(bs, f)
+    gb.gp_band_set_query_tiles(bs, rpt, bps)
     sets_s = o.band_sets(sphere5k, Rs, 2, 2)
     Ds, _ = _set_field(gb, bs, sets_s, Rs, 0.5, 0.05, seed=43)
     h = 2.0 / Rs
@@ -545,6 +548,7 @@ def test_step_windowed_forms_match_oracle(gb, ctx, object100k, sphere5k, form):
     # Dense grid: the windows of bricks on the grid boundary.
     bd = _band(gb, ctx, sphere5k, Rs, -1, -1, knn_k=0)
     gb.gp_band_set_query_form(bd, f)
+    gb.gp_band_set_query_tiles(bd, rpt, bps)
     sets_d, qd, sd = _step_inputs(sphere5k, Rs, -1, -1, 30_000, 4.0 / Rs, seed=45, use_nn=True)
     Dd, _ = _set_field(gb, bd, sets_d, Rs, 0.5, 0.1, seed=46)
     od = _morton_order(sd, Rs)
