@@ -126,7 +126,10 @@ def fwd_bwd_adam(per_kernel: dict, names, queries_per_step: float, V_trainable: 
 # the dominant kernel from one ncu capture of the current kernel code
 # (summaries in profiles/), by workload; a kernel changed since its capture
 # must be dropped from here.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # profiles/k_nn_sorted_scene_1024.md: mean of three full-size launches.
+    ("scene", "k_nn_sorted"): 1_138_243_072,
+}
 
 
 def peaks():
