@@ -328,9 +328,9 @@ struct MultiTvSrc {
 // the block's tiles); the gradient is overwritten at every slot of every
 // brick; the TV sums go to each cloud's slot 3, one atomic per run of tiles of
 // the same cloud.
-// DET: the query pass ran first into the fixed-point sums, which are folded
-// in here (scaled by 1/B_v of the cloud) and cleared; the TV sums go to the
-// integer loss sums.
+// DET: the query pass ran first into the fixed-point sums (its contributions
+// already scaled by 1/B_v of the cloud), which are folded in here and
+// cleared; the TV sums go to the integer loss sums.
 template <bool DET>
 __global__ void __launch_bounds__(TV_SWEEP_THREADS, TV_BLOCKS_PER_SM) k_m_tv(const MShape* __restrict__ shapes,
                                                            const MTile* __restrict__ tiles, int64_t ntiles,
@@ -369,8 +369,6 @@ __global__ void __launch_bounds__(TV_SWEEP_THREADS, TV_BLOCKS_PER_SM) k_m_tv(con
         const float tv_scale = S.V_tv > 0 ? alpha / (float)S.V_tv : 0.f;
         float* gp = S.grad + (int64_t)tl.first * 512;
         if (DET) {
-          const int bv = nvalid[tl.shape];
-          const float qscale = bv > 0 ? 1.0f / (float)bv : 0.f;
           unsigned long long* ap = S.acc + 2 * (int64_t)tl.first * 512;
           const int ls[2] = {l0, l1};
           const float gs[2] = {g0, g1};
@@ -382,7 +380,7 @@ __global__ void __launch_bounds__(TV_SWEEP_THREADS, TV_BLOCKS_PER_SM) k_m_tv(con
               ap[2 * ls[k] + 1] = 0ull;
               const float qv = __fmaf_rn(__ll2float_rn(phi[k]), 9.5367431640625e-07f,
                                          __ll2float_rn(plo[k]) * 8.673617379884035e-19f);
-              g = __fmaf_rn(qv, qscale, g);
+              g = __fadd_rn(qv, g);
             }
             gp[ls[k]] = g;
           }
@@ -453,7 +451,7 @@ __global__ void __launch_bounds__(256) k_m_query(const MShape* __restrict__ shap
       cur = tl.shape;
     }
     const int bv = nvalid[tl.shape];
-    const float w = DET ? 1.0f : (bv > 0 ? 1.0f / (float)bv : 0.f);  // fixed-point sums: 1/B_v at the fold
+    const float w = bv > 0 ? 1.0f / (float)bv : 0.f;  // also for the fixed-point sums (taken pre-scaled)
     const int64_t end = min((int64_t)tl.first + tq, S.B);
     for (int64_t i = (int64_t)tl.first + threadIdx.x; i < end; i += blockDim.x) {
       float qq[3], s3[3];

@@ -138,7 +138,6 @@ __global__ void __launch_bounds__(Q_THREADS, Q_BLOCKS_PER_SM) k_query(Grid G, co
   const int64_t n = B;
   int bvv = *bv;
   float w = bvv > 0 ? 1.0f / (float)bvv : 0.f;
-  if (DET) w = 1.0f;  // fixed-point sums are scaled by 1/B_v at the end
   float sp = 0.f, sg = 0.f, ss = 0.f;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     float q[3], s[3];
@@ -164,7 +163,7 @@ __global__ void __launch_bounds__(Q_THREADS, MINB) k_query_ilp(Grid G, const flo
                                                                double* __restrict__ partials,
                                                                int32_t* __restrict__ err, FinalArgs fa) {
   const int bvv = *bv;
-  const float w = DET ? 1.0f : (bvv > 0 ? 1.0f / (float)bvv : 0.f);
+  const float w = bvv > 0 ? 1.0f / (float)bvv : 0.f;  // also for the fixed-point sums (taken pre-scaled)
   float sp = 0.f, sg = 0.f, ss = 0.f;
   GlobalSink<DET> sink{G, grad, acc, err};
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -369,11 +368,6 @@ __global__ void __launch_bounds__(TV_THREADS, TV_BLOCKS_PER_SM) k_tv(Grid G, con
                                                    int32_t* __restrict__ err, FinalArgs fa) {
   __shared__ TvShared sh;
   float tsum = 0.f;
-  float qscale_f = 0.f;
-  if (DET) {
-    int b = *bv;
-    qscale_f = b > 0 ? 1.0f / (float)b : 0.f;
-  }
   const int l = threadIdx.x;
   auto emit = [&](int64_t addr, float gv) {
     if (!GRAD) return;
@@ -383,8 +377,9 @@ __global__ void __launch_bounds__(TV_THREADS, TV_BLOCKS_PER_SM) k_tv(Grid G, con
       acc[2 * addr + 1] = 0ull;
       // hi 2^-20 + lo 2^-60 in float32 (the scales are exact powers of two):
       // the same operations on the same integers, so still bit-reproducible.
+      // The query pass added its contributions already scaled by 1/B_v.
       const float qv = __fmaf_rn(__ll2float_rn(hi), 9.5367431640625e-07f, __ll2float_rn(lo) * 8.673617379884035e-19f);
-      gv = __fmaf_rn(qv, qscale_f, gv);
+      gv = __fadd_rn(qv, gv);
     }
     grad[addr] = gv;
   };
@@ -436,11 +431,6 @@ __global__ void __launch_bounds__(TV_THREADS, TV_BLOCKS_PER_SM) k_tv_adam(
     double* __restrict__ partials, int32_t* __restrict__ err, FinalArgs fa) {
   __shared__ TvShared sh;
   float tsum = 0.f;
-  float qscale_f = 0.f;
-  if (DET) {
-    const int b = *bv;
-    qscale_f = b > 0 ? 1.0f / (float)b : 0.f;
-  }
   // This thread's two vertices of every brick (those tv_gather hands it), and
   // their Adam operands, loaded at the top of the brick's iteration.
   const int tt = threadIdx.x;
@@ -458,7 +448,7 @@ __global__ void __launch_bounds__(TV_THREADS, TV_BLOCKS_PER_SM) k_tv_adam(
         const long long hi = (long long)acc[2 * addr], lo = (long long)acc[2 * addr + 1];
         const float qv =
             __fmaf_rn(__ll2float_rn(hi), 9.5367431640625e-07f, __ll2float_rn(lo) * 8.673617379884035e-19f);
-        pq[k] = qv;  // scaled by 1/B_v in update(), as k_tv's fold does
+        pq[k] = qv;  // already scaled by 1/B_v by the query pass
       } else {
         pq[k] = qgrad[addr];
       }
@@ -474,7 +464,7 @@ __global__ void __launch_bounds__(TV_THREADS, TV_BLOCKS_PER_SM) k_tv_adam(
     if (DET) {
       acc[2 * addr] = 0ull;
       acc[2 * addr + 1] = 0ull;
-      g = __fmaf_rn(pq[k], qscale_f, tv_scale * g_tv);
+      g = __fadd_rn(pq[k], tv_scale * g_tv);
     } else {
       qgrad[addr] = 0.f;
       g = tv_scale * g_tv + pq[k];

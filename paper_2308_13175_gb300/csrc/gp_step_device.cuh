@@ -4,6 +4,8 @@
 // The formulas are stated in the header comment of gp_step.cu.
 #pragma once
 
+#include <string.h>
+
 #include "gp_internal.cuh"
 
 constexpr float NORM_FLOOR = 1e-12f;
@@ -103,8 +105,15 @@ __device__ __forceinline__ void red_add_v4(float* addr, float a, float b, float 
 // hi 2^40 + lo = v 2^60 rounded toward zero below 2^-60, by integer
 // arithmetic on v's bits.  Integer sums do not depend on the order of the
 // additions.  Returns false for a non-finite v or |v| >= 2^42 (FIX_LIMIT).
-__device__ __forceinline__ bool fix_split(float v, long long& hi, long long& lo) {
+// Integer arithmetic only, so the host build (a CPU test of its boundaries)
+// computes the same integers as the device.
+__host__ __device__ __forceinline__ bool fix_split(float v, long long& hi, long long& lo) {
+#ifdef __CUDA_ARCH__
   const uint32_t u = __float_as_uint(v);
+#else
+  uint32_t u;
+  memcpy(&u, &v, sizeof(u));
+#endif
   const int ex = (int)((u >> 23) & 0xffu);
   if (ex == 0xff) return false;
   long long m = (long long)(u & 0x7fffffu);
@@ -118,8 +127,10 @@ __device__ __forceinline__ bool fix_split(float v, long long& hi, long long& lo)
   hi = 0;
   lo = 0;
   if (m == 0) return true;
-  const int sh = e + 60;  // v 2^60 = m 2^sh
-  if (sh >= 82) return false;  // |v| >= 2^42
+  const int sh = e + 60;  // v 2^60 = m 2^sh, m < 2^24
+  // |v| >= 2^42 exactly when e >= 19 (m >= 2^23 for a normal v), i.e. sh >= 79;
+  // below that hi = m 2^(sh - 40) < 2^62 fits its 64-bit word.
+  if (sh >= 79) return false;
   if (sh >= 40) {
     hi = m << (sh - 40);
   } else if (sh >= 0) {
@@ -225,7 +236,8 @@ struct GlobalSink {
 
 // One step record: classify it, evaluate Eq. 3 at q and at s, add its loss
 // terms to sp / sg / ss and (GRAD) scatter its gradient to the 8 + 8 corners,
-// scaled by w (1/B_v; 1 for the fixed-point sums, scaled at the end).
+// scaled by w = 1/B_v (the fixed-point sums too: a contribution below 2^-20
+// then has no high word, and most corners take one 64-bit atomic, not two).
 //
 // The validity test is the one of classify(), with its memory reads arranged
 // for latency: both brick slots are read together, then both pull-mask words

@@ -598,16 +598,18 @@ def test_step_records_in_one_cell(gb, ctx, sphere5k):
 
 def test_step_deterministic_overflow_raises_numeric(gb, ctx, sphere5k):
     """A constant field has grad f = 0, so the normal is taken against the
-    1e-12 floor and a record's corner contributions reach ~1e13, beyond the
+    1e-12 floor and a record's corner contributions reach ~1e13 (one valid
+    record: B_v = 1, so the 1/B_v scaling leaves them so), beyond the
     fixed-point sums' limit of 2^42: the step raises GP_ERR_NUMERIC (read by
     gp_band_check) instead of wrapping around."""
     import torch
     R = 64
     band = _band(gb, ctx, sphere5k, R, -1, -1, knn_k=0, deterministic=True)
     gb.gp_band_set_values(band, torch.ones(band.V_stored, dtype=torch.float32, device="cuda"))
-    q = (sphere5k[:64] * 1.01).astype(np.float32)
+    q = (sphere5k[:1] * 1.01).astype(np.float32)
     gb.gp_band_check(band)  # clean before the step
-    _run_step(gb, band, q, sphere5k[:64], (1.0, 1.0, 0.005), gb.GP_STEP_DETERMINISTIC)
+    _, loss = _run_step(gb, band, q, sphere5k[:1], (1.0, 1.0, 0.005), gb.GP_STEP_DETERMINISTIC)
+    assert loss[gb.GP_LOSS_BV] == 1
     with pytest.raises(gb.GridPullError, match="GP_ERR_NUMERIC|numeric"):
         gb.gp_band_check(band)
     gb.gp_band_check(band)  # the flag was cleared by the read
