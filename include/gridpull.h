@@ -319,7 +319,9 @@ gp_status gp_band_autotune(gp_band* band, const float* rec_dev, int64_t B, const
                            const gp_loss_w* w, int32_t* rpt_out, int32_t* bps_out);
 
 /* Sets that launch shape directly: rpt records per thread (1 or 2) and bps
- * blocks per SM (2, 3 or 4).  Errors: GP_ERR_ARG. */
+ * blocks per SM (2, 3 or 4).  The windowed forms take the same shape (tiles
+ * of 256 rpt records); the staged one runs 2 blocks per SM whatever bps is.
+ * Errors: GP_ERR_ARG. */
 gp_status gp_band_set_query_tiles(gp_band* band, int32_t rpt, int32_t bps);
 
 /* Sets the form of the atomic-mode query pass (GP_QUERY_*).  gp_band_autotune
