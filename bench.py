@@ -78,6 +78,10 @@ def alg_bytes(name, n, J, Vs, Vt):
         "k_nn_sorted": 36 * n + 16 * J,
         "k_count_valid": 24 * n,
         "k_tv": 8 * Vs,
+        # the two-pass L_TV of gp_step: D read and 1/TV written; D and 1/TV
+        # read and the gradient written
+        "k_tv_inv": 8 * Vs,
+        "k_tv_grad": 12 * Vs,
         "k_query": 24 * n + 8 * Vt,
         "k_adam": 28 * Vt,
         # the fused L_TV + Adam sweep: values read for the stencil; per trainable
@@ -592,7 +596,8 @@ def run_ours(args, world, rank, local):
         per_kernel[name] = {"launches": cnt, "avg_us": round(1e3 * avg_ms, 2),
                             "share": round(tot / max(sum(v[1] for v in kern.values()), 1e-12), 4),
                             "alg_bytes": int(by), "gbs": round(by / (avg_ms / 1e3) / 1e9, 1) if by else None}
-    fba = fwd_bwd_adam(per_kernel, ("k_count_valid", "k_tv", "k_query", "k_adam", "k_tv_adam"), q_prof / args.steps,
+    fba = fwd_bwd_adam(per_kernel, ("k_count_valid", "k_tv", "k_tv_inv", "k_tv_grad", "k_query", "k_adam", "k_tv_adam"),
+                       q_prof / args.steps,
                        Vt, peak)
     dom = max(kern.items(), key=lambda kv: kv[1][1])[0]
     dk = per_kernel[dom]

@@ -259,6 +259,7 @@ void band_free(gp_band* b) {
   gp_free(b->acc);
   gp_free(b->D_alt);
   gp_free(b->qgrad);
+  gp_free(b->tv_inv);
   gp_free(b->pts);
   gp_free(b->pts_sorted);
   gp_free(b->cell_start);
@@ -408,6 +409,7 @@ extern "C" gp_status gp_build_band(gp_ctx* ctx, const float* pts_dev, int64_t J,
   if (!st && (b->flags & GP_BAND_DETERMINISTIC)) st = gp_alloc(ctx, &b->acc, 2 * V, "fixed-point accumulator");
   if (!st) st = gp_alloc(ctx, &b->D_alt, V, "second value buffer");
   if (!st) st = gp_alloc(ctx, &b->qgrad, V, "query gradient");
+  if (!st) st = gp_alloc(ctx, &b->tv_inv, V, "1/TV of the two-pass L_TV");
   if (!st) st = gp_alloc(ctx, &b->partials, (size_t)GP_MAX_PARTIAL_BLOCKS * 8, "partials");
   if (!st) st = gp_alloc(ctx, &b->dev_ints, GP_DI_COUNT, "device ints");
   if (!st) {

@@ -77,6 +77,7 @@ struct gp_band {
   unsigned long long* acc = nullptr;  // deterministic two-word fixed-point gradient (2 x V_stored)
   float* D_alt = nullptr;          // second value buffer: gp_step_update writes the new values here, then swaps
   float* qgrad = nullptr;          // query part of the gradient for gp_step_update, all zero between calls
+  float* tv_inv = nullptr;         // 1/TV_i per slot (0 outside T), written by gp_step's first L_TV pass
 
   // Point cloud: original order copy, cell list sorted copy, sigma, permutation.
   float* pts = nullptr;            // J x 3

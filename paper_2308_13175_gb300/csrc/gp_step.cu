@@ -22,6 +22,7 @@
 #include "gp_internal.cuh"
 #include "gp_step_device.cuh"
 #include "gp_query_win.cuh"
+#include "gp_tv2.cuh"
 
 namespace {
 
@@ -410,6 +411,112 @@ __global__ void __launch_bounds__(TV_THREADS, TV_BLOCKS_PER_SM) k_tv(Grid G, con
   (void)err;
 }
 
+// The two-pass L_TV of gp_step (gp_tv2.cuh).  Pass 1: 1/TV_i of every T
+// vertex into inv (0 at every other slot), the block's sum of TV_i into
+// partials[block*8 + 3].  The 6 squared differences are summed in the order
+// of the single-sweep form (-x, +x, -y, +y, -z, +z), so inv is the same.
+constexpr int TV2_BLOCKS_PER_SM = 16;
+__global__ void __launch_bounds__(TV2_THREADS, TV2_BLOCKS_PER_SM)
+    k_tv_inv(Grid G, const int32_t* __restrict__ coord, const int32_t* __restrict__ nbrs, int64_t n_bricks,
+             float* __restrict__ inv, double* __restrict__ partials) {
+  __shared__ Tv2Stage s;
+  __shared__ uint32_t Tw[16];
+  const int t = threadIdx.x, x = t & 7, y = t >> 3;
+  float tsum = 0.f;
+  for (int64_t b = blockIdx.x; b < n_bricks; b += gridDim.x) {
+    Tv2Regs r;
+    tv2_load(G.D, nbrs + 27 * b, b, r);
+    const uint32_t tw = t < 16 ? __ldg(G.masks + b * 48 + t) : 0u;
+    const int ox = __ldg(coord + 3 * b) * 8, oy = __ldg(coord + 3 * b + 1) * 8, oz = __ldg(coord + 3 * b + 2) * 8;
+    __syncthreads();  // the previous brick is done with s and Tw
+    tv2_store(s, r);
+    if (t < 16) Tw[t] = tw;
+    __syncthreads();
+#pragma unroll 2
+    for (int z = 0; z < 8; ++z) {
+      const int l = (z * 8 + y) * 8 + x;
+      float iv = 0.f;
+      if ((Tw[z * 2 + (y >> 2)] >> ((y & 3) * 8 + x)) & 1u) {
+        float n[6];
+        bool ok[6];
+        tv2_nbrs(s, x, y, z, n);
+        tv2_ingrid(ox + x, oy + y, oz + z, G.R, ok);
+        const float d = s.c[l];
+        float s2 = 0.f;
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+          const float e = d - n[j];
+          if (ok[j]) s2 = fmaf(e, e, s2);
+        }
+        iv = s2 > 0.f ? rsqrtf(s2) : 0.f;
+        tsum += s2 * iv;
+      }
+      inv[b * 512 + l] = iv;
+    }
+  }
+  __shared__ float red[TV2_THREADS / 32];
+  const float w = gp_warp_sum(tsum);
+  if ((t & 31) == 0) red[t >> 5] = w;
+  __syncthreads();
+  if (t == 0) {
+    double sum = 0;
+    for (int k = 0; k < TV2_THREADS / 32; ++k) sum += red[k];
+    partials[(int64_t)blockIdx.x * 8 + 3] = sum;
+  }
+}
+
+// Pass 2: the gradient of every stored slot, alpha/|T| dTV/dd (0 outside the
+// grid), plus, DET, the fixed-point query sums (folded and cleared), in the
+// single-sweep form's order of terms.  LAST: this kernel writes the loss slots.
+template <bool DET, bool LAST>
+__global__ void __launch_bounds__(TV2_THREADS, TV2_BLOCKS_PER_SM)
+    k_tv_grad(Grid G, const int32_t* __restrict__ coord, const int32_t* __restrict__ nbrs, int64_t n_bricks,
+              const float* __restrict__ inv, float tv_scale, float* __restrict__ grad,
+              unsigned long long* __restrict__ acc, double* __restrict__ partials, FinalArgs fa) {
+  __shared__ Tv2Stage sd, si;
+  const int t = threadIdx.x, x = t & 7, y = t >> 3;
+  for (int64_t b = blockIdx.x; b < n_bricks; b += gridDim.x) {
+    Tv2Regs rd, ri;
+    tv2_load(G.D, nbrs + 27 * b, b, rd);
+    tv2_load(inv, nbrs + 27 * b, b, ri);
+    const int ox = __ldg(coord + 3 * b) * 8, oy = __ldg(coord + 3 * b + 1) * 8, oz = __ldg(coord + 3 * b + 2) * 8;
+    __syncthreads();  // the previous brick is done with sd and si
+    tv2_store(sd, rd);
+    tv2_store(si, ri);
+    __syncthreads();
+#pragma unroll 2
+    for (int z = 0; z < 8; ++z) {
+      const int l = (z * 8 + y) * 8 + x;
+      const int X = ox + x, Y = oy + y, Z = oz + z;
+      float nd[6], ni[6];
+      bool ok[6];
+      tv2_nbrs(sd, x, y, z, nd);
+      tv2_nbrs(si, x, y, z, ni);
+      tv2_ingrid(X, Y, Z, G.R, ok);
+      const float d = sd.c[l], own = si.c[l];
+      float g = 0.f;
+#pragma unroll
+      for (int j = 0; j < 6; ++j) {
+        // own != 0 only for T vertices, whose in-grid neighbours are all
+        // stored; ni[j] != 0 only for neighbours in T.
+        if (ok[j]) g = fmaf(d - nd[j], own + ni[j], g);
+      }
+      float gv = (X <= G.R && Y <= G.R && Z <= G.R) ? tv_scale * g : 0.f;
+      const int64_t addr = b * 512 + l;
+      if (DET) {
+        const long long hi = (long long)acc[2 * addr], lo = (long long)acc[2 * addr + 1];
+        acc[2 * addr] = 0ull;
+        acc[2 * addr + 1] = 0ull;
+        const float qv =
+            __fmaf_rn(__ll2float_rn(hi), 9.5367431640625e-07f, __ll2float_rn(lo) * 8.673617379884035e-19f);
+        gv = __fadd_rn(qv, gv);
+      }
+      grad[addr] = gv;
+    }
+  }
+  if (LAST) finish_if_last(partials, fa);
+}
+
 // Adam's hyper-parameters for one step, with the bias corrections.
 struct AdamArgs {
   float lr, b1, b2, eps, ibc1, ibc2;  // ibc = 1 / (1 - beta^t)
@@ -526,6 +633,12 @@ unsigned q_grid(const gp_ctx* ctx, int64_t B) {
   return gp_blocks(B, Q_THREADS, cap);
 }
 
+unsigned tv2_grid(const gp_ctx* ctx, int64_t n_bricks) {
+  int64_t cap = (int64_t)ctx->num_sms * TV2_BLOCKS_PER_SM;
+  if (cap > GP_MAX_PARTIAL_BLOCKS) cap = GP_MAX_PARTIAL_BLOCKS;
+  return gp_blocks(n_bricks, 1, cap);
+}
+
 unsigned tv_grid(const gp_ctx* ctx, int64_t n_bricks) {
   int64_t cap = (int64_t)ctx->num_sms * TV_BLOCKS_PER_SM;  // persistent: one wave
   if (cap > GP_MAX_PARTIAL_BLOCKS) cap = GP_MAX_PARTIAL_BLOCKS;
@@ -588,9 +701,27 @@ extern "C" gp_status gp_step(gp_band* b, const float* rec_dev, int64_t B, const 
   // it; in deterministic mode the query pass fills the fixed-point sums first
   // and the sweep folds them in.  Whichever runs second writes the loss.
   const bool tv_last = det && grad_on;
+  const unsigned tb2 = b->n_bricks ? tv2_grid(ctx, b->n_bricks) : 1;
+  if (tv_on) fa.tv_blocks = (int)tb2;
   auto launch_tv = [&]() -> gp_status {
     if (b->n_bricks == 0) {
       GP_CUDA(ctx, cudaMemsetAsync(b->partials + 3, 0, sizeof(double), s));
+      return GP_OK;
+    }
+    if (tv_on) {
+      // Two passes: 1/TV of the T vertices, then the gradient of every slot.
+      GP_KERNEL(ctx, "k_tv_inv",
+                k_tv_inv<<<tb2, TV2_THREADS, 0, s>>>(G, b->brick_coord, b->brick_nbr, b->n_bricks, b->tv_inv,
+                                                      b->partials));
+      if (!grad_on) return GP_OK;
+#define GP_TV2(D_, L_)                                                                                          \
+  k_tv_grad<D_, L_><<<tb2, TV2_THREADS, 0, s>>>(G, b->brick_coord, b->brick_nbr, b->n_bricks, b->tv_inv, tv_scale, \
+                                                grad_dev, b->acc, b->partials, fa)
+      if (tv_last)
+        GP_KERNEL(ctx, "k_tv_grad", GP_TV2(true, true));
+      else
+        GP_KERNEL(ctx, "k_tv_grad", GP_TV2(false, false));
+#undef GP_TV2
       return GP_OK;
     }
 #define GP_TV(D_, G_, T_, L_)                                                                                  \

@@ -1,0 +1,91 @@
+// L_TV (Eq. 5) and its gradient in two passes over the bricks, for gp_step:
+//   pass 1: inv_i = 1 / TV_i for i in T (0 elsewhere, and where TV_i = 0),
+//           TV_i = sqrt(sum over in-grid axis neighbours n of (d_i - d_n)^2),
+//           written to a per-slot array; the block sums of TV_i;
+//   pass 2: dTV/dd_j = sum over in-grid axis neighbours n of
+//           (d_j - d_n) (inv_j + inv_n), which is the gathered form
+//           [j in T] sum_n (d_j - d_n)/TV_j + sum_{n in T} (d_j - d_n)/TV_n.
+// Each pass needs a brick's values (and, in pass 2, its inverses) and the
+// face of each of its 6 axis-neighbour bricks that touches it: a radius-1
+// stencil, with no halo ring to recompute (the single-sweep form stages a
+// 12^3 halo from 27 bricks and computes 1/TV on the 10^3 inner region).
+// One block of 64 threads per brick at a time, thread (x, y) walking its
+// column z = 0..7.
+#pragma once
+
+#include "gp_step_device.cuh"
+
+constexpr int TV2_THREADS = 64;
+// Face order: -x, +x, -y, +y, -z, +z; their rows of the 27-neighbour table
+// ((dx + 1) + 3 (dy + 1) + 9 (dz + 1)).
+__device__ __forceinline__ int tv2_face_nbr(int f) {
+  return f == 0 ? 12 : f == 1 ? 14 : f == 2 ? 10 : f == 3 ? 16 : f == 4 ? 4 : 22;
+}
+// In-brick slot of the face value thread t holds for face f: the layer of
+// the neighbour brick that touches this one (x = 7 of the -x brick, ...).
+// Face arrays are indexed (z, y) for the x faces, (z, x) for the y faces,
+// (y, x) for the z faces, 8 x 8 each: index t = 8 * first + second.
+__device__ __forceinline__ int tv2_face_local(int f, int t) {
+  const int a = t >> 3, b = t & 7;
+  switch (f) {
+    case 0: return (a * 8 + b) * 8 + 7;  // (z, y) of the -x brick at x = 7
+    case 1: return (a * 8 + b) * 8 + 0;
+    case 2: return (a * 8 + 7) * 8 + b;  // (z, x) of the -y brick at y = 7
+    case 3: return (a * 8 + 0) * 8 + b;
+    case 4: return (7 * 8 + a) * 8 + b;  // (y, x) of the -z brick at z = 7
+    default: return (0 * 8 + a) * 8 + b;
+  }
+}
+
+// A staged brick: its 512 values and the 6 faces (0 where a neighbour brick
+// is absent: only frozen vertices, outside T, can sit next to one).
+struct Tv2Stage {
+  float c[512];
+  float f[6][64];
+};
+
+// This thread's share of brick `slot`'s loads (8 centre values, one per
+// face), issued together.
+struct Tv2Regs {
+  float c[8];
+  float f[6];
+};
+__device__ __forceinline__ void tv2_load(const float* __restrict__ src, const int32_t* __restrict__ nbr_row,
+                                         int64_t slot, Tv2Regs& r) {
+  const int t = threadIdx.x;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) r.c[k] = __ldg(src + slot * 512 + t + 64 * k);
+#pragma unroll
+  for (int f = 0; f < 6; ++f) {
+    const int ns = __ldg(nbr_row + tv2_face_nbr(f));
+    r.f[f] = ns >= 0 ? __ldg(src + (int64_t)ns * 512 + tv2_face_local(f, t)) : 0.f;
+  }
+}
+__device__ __forceinline__ void tv2_store(Tv2Stage& s, const Tv2Regs& r) {
+  const int t = threadIdx.x;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) s.c[t + 64 * k] = r.c[k];
+#pragma unroll
+  for (int f = 0; f < 6; ++f) s.f[f][t] = r.f[f];
+}
+
+// The 6 axis neighbours of (x, y, z) in the staged brick (-x, +x, -y, +y, -z, +z).
+__device__ __forceinline__ void tv2_nbrs(const Tv2Stage& s, int x, int y, int z, float n[6]) {
+  const int l = (z * 8 + y) * 8 + x;
+  n[0] = x > 0 ? s.c[l - 1] : s.f[0][z * 8 + y];
+  n[1] = x < 7 ? s.c[l + 1] : s.f[1][z * 8 + y];
+  n[2] = y > 0 ? s.c[l - 8] : s.f[2][z * 8 + x];
+  n[3] = y < 7 ? s.c[l + 8] : s.f[3][z * 8 + x];
+  n[4] = z > 0 ? s.c[l - 64] : s.f[4][y * 8 + x];
+  n[5] = z < 7 ? s.c[l + 64] : s.f[5][y * 8 + x];
+}
+
+// Which of the 6 neighbours of vertex (X, Y, Z) lie inside [0, R]^3.
+__device__ __forceinline__ void tv2_ingrid(int X, int Y, int Z, int R, bool ok[6]) {
+  ok[0] = X > 0;
+  ok[1] = X < R;
+  ok[2] = Y > 0;
+  ok[3] = Y < R;
+  ok[4] = Z > 0;
+  ok[5] = Z < R;
+}

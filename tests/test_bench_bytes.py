@@ -12,7 +12,7 @@ CSRC = os.path.join(ROOT, "paper_2308_13175_gb300", "csrc")
 # Launched by a step of FitStep: sampling (once-per-epoch kernels move no
 # per-step data the roofline counts), NN, the step and the update.
 STEP_KERNELS = {"k_sample", "k_perm", "k_order_count", "k_order_emit", "k_nn", "k_nn_sorted", "k_count_valid",
-                "k_tv", "k_query", "k_adam", "k_tv_adam"}
+                "k_tv", "k_tv_inv", "k_tv_grad", "k_query", "k_adam", "k_tv_adam"}
 UNCOUNTED = {"k_order_tiles", "k_emit_slots"}  # a scan of tile counts; a per-epoch gather
 
 
@@ -42,6 +42,8 @@ def test_byte_counts_are_the_arrays_touched_once():
     assert bench.alg_bytes("k_query", n, J, Vs, Vt) == 24 * n + 8 * Vt      # records; D read, grad written
     assert bench.alg_bytes("k_adam", n, J, Vs, Vt) == 28 * Vt               # D, g, m, v read; D, m, v written
     assert bench.alg_bytes("k_tv", n, J, Vs, Vt) == 8 * Vs                  # D read, grad written
+    assert bench.alg_bytes("k_tv_inv", n, J, Vs, Vt) == 8 * Vs              # D read, 1/TV written
+    assert bench.alg_bytes("k_tv_grad", n, J, Vs, Vt) == 12 * Vs            # D, 1/TV read, grad written
     assert bench.alg_bytes("k_tv_adam", n, J, Vs, Vt) == 4 * Vs + 28 * Vt   # D read; query part, m, v, D
     assert bench.alg_bytes("k_unknown", n, J, Vs, Vt) == 0
 
