@@ -411,37 +411,55 @@ __global__ void __launch_bounds__(TV_THREADS, TV_BLOCKS_PER_SM) k_tv(Grid G, con
   (void)err;
 }
 
-// The two-pass L_TV of gp_step (gp_tv2.cuh).  Pass 1: 1/TV_i of every T
-// vertex into inv (0 at every other slot), the block's sum of TV_i into
-// partials[block*8 + 3].  The 6 squared differences are summed in the order
-// of the single-sweep form (-x, +x, -y, +y, -z, +z), so inv is the same.
-constexpr int TV2_BLOCKS_PER_SM = 16;
-__global__ void __launch_bounds__(TV2_THREADS, TV2_BLOCKS_PER_SM)
+// The two-pass L_TV of gp_step (gp_tv2.cuh).  Each block walks bricks
+// blockIdx.x, + gridDim.x, ...: the next brick's copies are issued into the
+// other of two stage buffers (cp.async) before the current one is computed,
+// and the brick after that has its neighbour slots read meanwhile.
+//
+// Pass 1: 1/TV_i of every T vertex into inv (0 at every other slot), the
+// block's sum of TV_i into partials[block*8 + 3].  The 6 squared differences
+// are summed in the order of the single-sweep form (-x, +x, -y, +y, -z, +z),
+// so inv is the same.
+constexpr int TV2_INV_BLOCKS_PER_SM = 16;
+constexpr int TV2_GRAD_BLOCKS_PER_SM = 12;
+__global__ void __launch_bounds__(TV2_THREADS, TV2_INV_BLOCKS_PER_SM)
     k_tv_inv(Grid G, const int32_t* __restrict__ coord, const int32_t* __restrict__ nbrs, int64_t n_bricks,
              float* __restrict__ inv, double* __restrict__ partials) {
-  __shared__ Tv2Stage s;
-  __shared__ uint32_t Tw[16];
+  __shared__ Tv2Stage s[2];
+  __shared__ __align__(16) uint32_t Tw[2][16];
   const int t = threadIdx.x, x = t & 7, y = t >> 3;
   float tsum = 0.f;
-  for (int64_t b = blockIdx.x; b < n_bricks; b += gridDim.x) {
-    Tv2Regs r;
-    tv2_load(G.D, nbrs + 27 * b, b, r);
-    const uint32_t tw = t < 16 ? __ldg(G.masks + b * 48 + t) : 0u;
-    const int ox = __ldg(coord + 3 * b) * 8, oy = __ldg(coord + 3 * b + 1) * 8, oz = __ldg(coord + 3 * b + 2) * 8;
-    __syncthreads();  // the previous brick is done with s and Tw
-    tv2_store(s, r);
-    if (t < 16) Tw[t] = tw;
-    __syncthreads();
+  const int64_t first = blockIdx.x, stride = gridDim.x;
+  auto issue = [&](int p, const Tv2Brick& k) {
+    tv2_issue(s[p], G.D, k);
+    if (t < 4) cp_async_cg16(&Tw[p][4 * t], G.masks + k.slot * 48 + 4 * t, 16);
+  };
+  Tv2Brick cur, nxt;
+  if (first < n_bricks) {
+    cur = tv2_brick(coord, nbrs, first);
+    issue(0, cur);
+  }
+  cp_async_commit();
+  if (first + stride < n_bricks) nxt = tv2_brick(coord, nbrs, first + stride);
+  int p = 0;
+  for (int64_t b = first; b < n_bricks; b += stride) {
+    if (b + stride < n_bricks) issue(p ^ 1, nxt);
+    cp_async_commit();
+    Tv2Brick after;
+    if (b + 2 * stride < n_bricks) after = tv2_brick(coord, nbrs, b + 2 * stride);
+    cp_async_wait1();  // this thread's copies of brick b have landed
+    __syncthreads();   // ... and everyone's
+    const Tv2Stage& S = s[p];
 #pragma unroll 2
     for (int z = 0; z < 8; ++z) {
       const int l = (z * 8 + y) * 8 + x;
       float iv = 0.f;
-      if ((Tw[z * 2 + (y >> 2)] >> ((y & 3) * 8 + x)) & 1u) {
+      if ((Tw[p][z * 2 + (y >> 2)] >> ((y & 3) * 8 + x)) & 1u) {
         float n[6];
         bool ok[6];
-        tv2_nbrs(s, x, y, z, n);
-        tv2_ingrid(ox + x, oy + y, oz + z, G.R, ok);
-        const float d = s.c[l];
+        tv2_nbrs(S, x, y, z, n);
+        tv2_ingrid(cur.ox + x, cur.oy + y, cur.oz + z, G.R, ok);
+        const float d = S.c[l];
         float s2 = 0.f;
 #pragma unroll
         for (int j = 0; j < 6; ++j) {
@@ -453,7 +471,12 @@ __global__ void __launch_bounds__(TV2_THREADS, TV2_BLOCKS_PER_SM)
       }
       inv[b * 512 + l] = iv;
     }
+    __syncthreads();  // buffer p is free for the copies of brick b + 2 stride
+    cur = nxt;
+    nxt = after;
+    p ^= 1;
   }
+  cp_async_wait0();
   __shared__ float red[TV2_THREADS / 32];
   const float w = gp_warp_sum(tsum);
   if ((t & 31) == 0) red[t >> 5] = w;
@@ -469,31 +492,44 @@ __global__ void __launch_bounds__(TV2_THREADS, TV2_BLOCKS_PER_SM)
 // grid), plus, DET, the fixed-point query sums (folded and cleared), in the
 // single-sweep form's order of terms.  LAST: this kernel writes the loss slots.
 template <bool DET, bool LAST>
-__global__ void __launch_bounds__(TV2_THREADS, TV2_BLOCKS_PER_SM)
+__global__ void __launch_bounds__(TV2_THREADS, TV2_GRAD_BLOCKS_PER_SM)
     k_tv_grad(Grid G, const int32_t* __restrict__ coord, const int32_t* __restrict__ nbrs, int64_t n_bricks,
               const float* __restrict__ inv, float tv_scale, float* __restrict__ grad,
               unsigned long long* __restrict__ acc, double* __restrict__ partials, FinalArgs fa) {
-  __shared__ Tv2Stage sd, si;
+  __shared__ Tv2Stage sd[2], si[2];
   const int t = threadIdx.x, x = t & 7, y = t >> 3;
-  for (int64_t b = blockIdx.x; b < n_bricks; b += gridDim.x) {
-    Tv2Regs rd, ri;
-    tv2_load(G.D, nbrs + 27 * b, b, rd);
-    tv2_load(inv, nbrs + 27 * b, b, ri);
-    const int ox = __ldg(coord + 3 * b) * 8, oy = __ldg(coord + 3 * b + 1) * 8, oz = __ldg(coord + 3 * b + 2) * 8;
-    __syncthreads();  // the previous brick is done with sd and si
-    tv2_store(sd, rd);
-    tv2_store(si, ri);
+  const int64_t first = blockIdx.x, stride = gridDim.x;
+  auto issue = [&](int p, const Tv2Brick& k) {
+    tv2_issue(sd[p], G.D, k);
+    tv2_issue(si[p], inv, k);
+  };
+  Tv2Brick cur, nxt;
+  if (first < n_bricks) {
+    cur = tv2_brick(coord, nbrs, first);
+    issue(0, cur);
+  }
+  cp_async_commit();
+  if (first + stride < n_bricks) nxt = tv2_brick(coord, nbrs, first + stride);
+  int p = 0;
+  for (int64_t b = first; b < n_bricks; b += stride) {
+    if (b + stride < n_bricks) issue(p ^ 1, nxt);
+    cp_async_commit();
+    Tv2Brick after;
+    if (b + 2 * stride < n_bricks) after = tv2_brick(coord, nbrs, b + 2 * stride);
+    cp_async_wait1();
     __syncthreads();
+    const Tv2Stage& SD = sd[p];
+    const Tv2Stage& SI = si[p];
 #pragma unroll 2
     for (int z = 0; z < 8; ++z) {
       const int l = (z * 8 + y) * 8 + x;
-      const int X = ox + x, Y = oy + y, Z = oz + z;
+      const int X = cur.ox + x, Y = cur.oy + y, Z = cur.oz + z;
       float nd[6], ni[6];
       bool ok[6];
-      tv2_nbrs(sd, x, y, z, nd);
-      tv2_nbrs(si, x, y, z, ni);
+      tv2_nbrs(SD, x, y, z, nd);
+      tv2_nbrs(SI, x, y, z, ni);
       tv2_ingrid(X, Y, Z, G.R, ok);
-      const float d = sd.c[l], own = si.c[l];
+      const float d = SD.c[l], own = SI.c[l];
       float g = 0.f;
 #pragma unroll
       for (int j = 0; j < 6; ++j) {
@@ -513,7 +549,12 @@ __global__ void __launch_bounds__(TV2_THREADS, TV2_BLOCKS_PER_SM)
       }
       grad[addr] = gv;
     }
+    __syncthreads();
+    cur = nxt;
+    nxt = after;
+    p ^= 1;
   }
+  cp_async_wait0();
   if (LAST) finish_if_last(partials, fa);
 }
 
@@ -633,8 +674,8 @@ unsigned q_grid(const gp_ctx* ctx, int64_t B) {
   return gp_blocks(B, Q_THREADS, cap);
 }
 
-unsigned tv2_grid(const gp_ctx* ctx, int64_t n_bricks) {
-  int64_t cap = (int64_t)ctx->num_sms * TV2_BLOCKS_PER_SM;
+unsigned tv2_grid(const gp_ctx* ctx, int64_t n_bricks, int per_sm) {
+  int64_t cap = (int64_t)ctx->num_sms * per_sm;
   if (cap > GP_MAX_PARTIAL_BLOCKS) cap = GP_MAX_PARTIAL_BLOCKS;
   return gp_blocks(n_bricks, 1, cap);
 }
@@ -701,7 +742,8 @@ extern "C" gp_status gp_step(gp_band* b, const float* rec_dev, int64_t B, const 
   // it; in deterministic mode the query pass fills the fixed-point sums first
   // and the sweep folds them in.  Whichever runs second writes the loss.
   const bool tv_last = det && grad_on;
-  const unsigned tb2 = b->n_bricks ? tv2_grid(ctx, b->n_bricks) : 1;
+  const unsigned tb2 = b->n_bricks ? tv2_grid(ctx, b->n_bricks, TV2_INV_BLOCKS_PER_SM) : 1;
+  const unsigned tg2 = b->n_bricks ? tv2_grid(ctx, b->n_bricks, TV2_GRAD_BLOCKS_PER_SM) : 1;
   if (tv_on) fa.tv_blocks = (int)tb2;
   auto launch_tv = [&]() -> gp_status {
     if (b->n_bricks == 0) {
@@ -715,7 +757,7 @@ extern "C" gp_status gp_step(gp_band* b, const float* rec_dev, int64_t B, const 
                                                       b->partials));
       if (!grad_on) return GP_OK;
 #define GP_TV2(D_, L_)                                                                                          \
-  k_tv_grad<D_, L_><<<tb2, TV2_THREADS, 0, s>>>(G, b->brick_coord, b->brick_nbr, b->n_bricks, b->tv_inv, tv_scale, \
+  k_tv_grad<D_, L_><<<tg2, TV2_THREADS, 0, s>>>(G, b->brick_coord, b->brick_nbr, b->n_bricks, b->tv_inv, tv_scale, \
                                                 grad_dev, b->acc, b->partials, fa)
       if (tv_last)
         GP_KERNEL(ctx, "k_tv_grad", GP_TV2(true, true));

@@ -39,34 +39,64 @@ __device__ __forceinline__ int tv2_face_local(int f, int t) {
 
 // A staged brick: its 512 values and the 6 faces (0 where a neighbour brick
 // is absent: only frozen vertices, outside T, can sit next to one).
-struct Tv2Stage {
+struct __align__(16) Tv2Stage {
   float c[512];
   float f[6][64];
 };
 
-// This thread's share of brick `slot`'s loads (8 centre values, one per
-// face), issued together.
-struct Tv2Regs {
-  float c[8];
-  float f[6];
+// The slots a brick's copies read: its own and its 6 face neighbours' (-1
+// absent), and its origin vertex.
+struct Tv2Brick {
+  int64_t slot;
+  int nb[6];
+  int ox, oy, oz;
 };
-__device__ __forceinline__ void tv2_load(const float* __restrict__ src, const int32_t* __restrict__ nbr_row,
-                                         int64_t slot, Tv2Regs& r) {
-  const int t = threadIdx.x;
+__device__ __forceinline__ Tv2Brick tv2_brick(const int32_t* __restrict__ coord, const int32_t* __restrict__ nbrs,
+                                             int64_t b) {
+  Tv2Brick k;
+  k.slot = b;
 #pragma unroll
-  for (int k = 0; k < 8; ++k) r.c[k] = __ldg(src + slot * 512 + t + 64 * k);
-#pragma unroll
-  for (int f = 0; f < 6; ++f) {
-    const int ns = __ldg(nbr_row + tv2_face_nbr(f));
-    r.f[f] = ns >= 0 ? __ldg(src + (int64_t)ns * 512 + tv2_face_local(f, t)) : 0.f;
-  }
+  for (int f = 0; f < 6; ++f) k.nb[f] = __ldg(nbrs + 27 * b + tv2_face_nbr(f));
+  k.ox = __ldg(coord + 3 * b) * 8;
+  k.oy = __ldg(coord + 3 * b + 1) * 8;
+  k.oz = __ldg(coord + 3 * b + 2) * 8;
+  return k;
 }
-__device__ __forceinline__ void tv2_store(Tv2Stage& s, const Tv2Regs& r) {
+
+__device__ __forceinline__ void tv2_cp4(void* smem, const void* gmem, int src_bytes) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(gmem), "r"(src_bytes) : "memory");
+}
+
+// This thread's asynchronous copies of brick k of array src into s (64
+// threads): two 16-byte pieces of the centre; one 16-byte piece of a z face
+// (threads 0-31) or of a y face (threads 32-63); one value of each x face.
+// An absent neighbour's pieces are zero-filled (no bytes read).
+__device__ __forceinline__ void tv2_issue(Tv2Stage& s, const float* __restrict__ src, const Tv2Brick& k) {
   const int t = threadIdx.x;
+  const float* c = src + k.slot * 512;
+  cp_async_cg16(&s.c[4 * t], c + 4 * t, 16);
+  cp_async_cg16(&s.c[4 * (t + 64)], c + 4 * (t + 64), 16);
+  {
+    // z faces (t < 32): plane z = 7 of the -z brick, z = 0 of the +z brick,
+    // face index 8 y + x; y faces: row y = 7 (0) at each z, index 8 z + x.
+    const int f = t < 16 ? 4 : t < 32 ? 5 : t < 48 ? 2 : 3;
+    const int piece = t & 15;  // 16 pieces of 4 floats per face
+    const int ns = f == 2 ? k.nb[2] : f == 3 ? k.nb[3] : f == 4 ? k.nb[4] : k.nb[5];  // no indexed registers
+    int local;
+    if (f >= 4)
+      local = (f == 4 ? 7 * 64 : 0) + 4 * piece;
+    else
+      local = (piece >> 1) * 64 + (f == 2 ? 56 : 0) + 4 * (piece & 1);
+    const float* g = ns >= 0 ? src + (int64_t)ns * 512 + local : src;
+    cp_async_cg16(&s.f[f][4 * piece], g, ns >= 0 ? 16 : 0);
+  }
 #pragma unroll
-  for (int k = 0; k < 8; ++k) s.c[t + 64 * k] = r.c[k];
-#pragma unroll
-  for (int f = 0; f < 6; ++f) s.f[f][t] = r.f[f];
+  for (int f = 0; f < 2; ++f) {
+    const int ns = k.nb[f];
+    const float* g = ns >= 0 ? src + (int64_t)ns * 512 + tv2_face_local(f, t) : src;
+    tv2_cp4(&s.f[f][t], g, ns >= 0 ? 4 : 0);
+  }
 }
 
 // The 6 axis neighbours of (x, y, z) in the staged brick (-x, +x, -y, +y, -z, +z).

@@ -96,10 +96,17 @@ class FitStep:
 
     def run_pipelined(self, t0: int, K: int):
         """Steps t0 .. t0 + K - 1, the same as run(t0), ..., run(t0 + K - 1),
-        with the next batch's sampling and nearest points on a second stream
-        while the current batch's step and update run on a third: the draw
-        does not read the grid values, so only the record buffers need
-        ordering (two of them, alternating).  The calling stream waits for
+        with each next batch's sampling and nearest points on a second stream
+        overlapping part of the current step on a third: the draw does not read
+        the grid values, so only the record buffers need ordering (two of
+        them, alternating).  With the separate descent (gp_step, then
+        gp_update) the next draw starts once the current gp_step is done and
+        overlaps its Adam update: measured on the 10M-point scene, letting it
+        overlap gp_step's L_TV passes and query pass too made the step slower
+        than running everything in turn (the search and those passes contend
+        for L2), while overlapping Adam only made it faster.  With the fused
+        descent (gp_step_update, whose sweep holds every SM) the draw is
+        issued beside the whole descent.  The calling stream waits for
         everything before this returns (asynchronously, as every call here).
         Returns the loss buffer of the last step."""
         if K <= 0:
@@ -107,31 +114,48 @@ class FitStep:
         if self._streams is None:
             lo, hi = torch.cuda.Stream.priority_range()
             self._streams = (torch.cuda.Stream(self.device), torch.cuda.Stream(self.device, priority=hi))
-            self._events = [[torch.cuda.Event() for _ in range(2)] for _ in range(2)]
+            self._events = [[torch.cuda.Event() for _ in range(2)] for _ in range(3)]
         sa, sb = self._streams
-        drawn, stepped = self._events
+        drawn, stepped, queried = self._events
         cur = torch.cuda.current_stream(self.device)
         sa.wait_stream(cur)
         sb.wait_stream(cur)
         counts = {}
 
-        def draw(t):
+        def draw(t, after=None):
             p = t % 2
             with torch.cuda.stream(sa):
-                if t - 2 >= t0:
+                if after is not None:
+                    sa.wait_event(after)
+                elif t - 2 >= t0:
                     sa.wait_event(stepped[p])  # step t - 2 has read buffer p
                 counts[t] = self._draw(t, self.bufs[p])
                 drawn[p].record(sa)
 
-        draw(t0)
-        for t in range(t0, t0 + K):
-            if t + 1 < t0 + K:
-                draw(t + 1)
+        def descend(t):
             p = t % 2
+            buf = self.bufs[p]
             with torch.cuda.stream(sb):
                 sb.wait_event(drawn[p])
-                self._descend(t, self.bufs[p], counts[t])
+                if self.fused:
+                    self._descend(t, buf, counts[t])
+                else:
+                    gb.gp_step(self.band, buf["rec"], counts[t], self.grad, self.loss, self.weights,
+                               nvalid=buf["nvalid"], flags=self.flags)
+                    queried[p].record(sb)  # buffer p's records are read; step t - 1 is done
+                    gb.gp_update(self.band, self.grad, self.lr_at(t), t + 1)
                 stepped[p].record(sb)
+
+        draw(t0)
+        for t in range(t0, t0 + K):
+            if self.fused:
+                if t + 1 < t0 + K:
+                    draw(t + 1)
+                descend(t)
+            else:
+                descend(t)
+                if t + 1 < t0 + K:
+                    draw(t + 1, after=queried[t % 2])
         cur.wait_stream(sa)
         cur.wait_stream(sb)
         return self.loss

@@ -710,10 +710,12 @@ def test_fit_steps_reduce_the_loss(gb, ctx, sphere5k):
     gb.gp_band_check(band)
 
 
-def test_pipelined_steps_equal_sequential_steps(gb, ctx, sphere5k):
+@pytest.mark.parametrize("fused", [True, False])
+def test_pipelined_steps_equal_sequential_steps(gb, ctx, sphere5k, fused):
     """FitStep.run_pipelined overlaps each next batch's sampling and nearest
-    points with the current step; with the deterministic sums it must give
-    the same values, moments and loss, bit for bit, as running the steps one
+    points with the current step (beside the whole fused descent, or beside
+    gp_update after gp_step); with the deterministic sums it must give the
+    same values, moments and loss, bit for bit, as running the steps one
     after the other - across epoch boundaries and a short last batch."""
     import torch
     from paper_2308_13175_gb300.fit import FitStep
@@ -723,7 +725,7 @@ def test_pipelined_steps_equal_sequential_steps(gb, ctx, sphere5k):
         band = _band(gb, ctx, sphere5k, R, 2, 2, knn_k=50, deterministic=True)
         gb.gp_band_init_sphere(band, (0.0, 0.0, 0.0), 0.45, 0.01, seed=5)
         bands.append(band)
-        fits.append(FitStep(band, Q=40_000, B=15_000, seed=3, lr=1e-3, deterministic=True, fused=True))
+        fits.append(FitStep(band, Q=40_000, B=15_000, seed=3, lr=1e-3, deterministic=True, fused=fused))
     K = 7
     for t in range(K):
         fits[0].run(t)
