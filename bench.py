@@ -739,6 +739,7 @@ def run_ours(args, world, rank, local):
     copied = [torch.cuda.Event() for _ in range(2)]
     searched = [torch.cuda.Event() for _ in range(2)]
     stepped = [torch.cuda.Event() for _ in range(2)]
+    queried = [torch.cuda.Event() for _ in range(2)]
 
     def e2e_copy(k):
         b = k % 2
@@ -749,11 +750,13 @@ def run_ours(args, world, rank, local):
             dsrc[b].copy_(hsrc[k % NH], non_blocking=True)
             copied[b].record(copy_stream)
 
-    def e2e_search(k):
+    def e2e_search(k, after=None):
         b, n = k % 2, counts_h[k % NH]
         with torch.cuda.stream(search_stream):
             search_stream.wait_event(copied[b])
-            if k >= 2:
+            if after is not None:
+                search_stream.wait_event(after)  # the previous step's gp_step is done (so is step k - 2)
+            elif k >= 2:
                 search_stream.wait_event(stepped[b])  # step k - 2 has read buffer b's records
             gb.gp_nn(band, dq[b][:n], None, fit.bufs[b]["rec"], hint=dsrc[b][:n], nvalid_out=fit.bufs[b]["nvalid"])
             searched[b].record(search_stream)
@@ -771,10 +774,14 @@ def run_ours(args, world, rank, local):
         e2e_copy(1)
     if pipelined_headline:
         e2e_search(0)
+    # As FitStep.run_pipelined: with the separate descent the next search
+    # waits for the current gp_step and overlaps its Adam update; with the
+    # fused one it is issued beside the whole descent.
+    overlap_all = fit.fused
     for k in range(K):
         b, n = k % 2, counts_h[k % NH]
         if pipelined_headline:
-            if k + 1 < K:
+            if overlap_all and k + 1 < K:
                 e2e_search(k + 1)
         else:
             flush.fill_(float(k))
@@ -783,9 +790,17 @@ def run_ours(args, world, rank, local):
             e2e_copy(k + 2)
         with torch.cuda.stream(step_stream):
             step_stream.wait_event(searched[b])
-            fit._descend(t_e2e + k, fit.bufs[b], n)
+            if fit.fused:
+                fit._descend(t_e2e + k, fit.bufs[b], n)
+            else:
+                buf = fit.bufs[b]
+                gb.gp_step(band, buf["rec"], n, fit.grad, fit.loss, fit.weights, nvalid=buf["nvalid"], flags=fit.flags)
+                queried[b].record(step_stream)
+                gb.gp_update(band, fit.grad, fit.lr_at(t_e2e + k), t_e2e + k + 1)
             hloss[k].copy_(fit.loss, non_blocking=True)
             stepped[b].record(step_stream)
+        if pipelined_headline and not overlap_all and k + 1 < K:
+            e2e_search(k + 1, after=queried[b])
         e2e_q += n
     for st_ in side_streams:
         stream.wait_stream(st_)
@@ -862,8 +877,10 @@ def run_ours(args, world, rank, local):
                                 "source points, drawn before timing) -> H2D copy -> gp_nn (seeded) -> " +
                                 ("gp_step_update" if fit.fused else "gp_step + gp_update") +
                                 " -> loss to host; " +
-                                ("copy of step k + 2 and search of step k + 1 on two more streams while step k "
-                                 "descends" if pipelined_headline else
+                                (("copy of step k + 2 and search of step k + 1 on two more streams while step k "
+                                  "descends" if fit.fused else
+                                  "copy of step k + 2 on a second stream; search of step k + 1 on a third once step "
+                                  "k's gp_step is done, beside its gp_update") if pipelined_headline else
                                  "steps in turn, L2 flush before each, next copy on a second stream") +
                                 "; K steps timed as one region")},
                "gpu_launches": int(launches), "clocks": clk, "kernels": per_kernel, "fwd_bwd_adam": fba,
