@@ -202,7 +202,7 @@ __device__ __forceinline__ int gp_brick_slot(const int32_t* __restrict__ table, 
   return __ldg(table + ((int64_t)bz * nb + by) * nb + bx);
 }
 
-__device__ __forceinline__ int gp_local(int i, int j, int k) {
+__host__ __device__ __forceinline__ int gp_local(int i, int j, int k) {
   return (((k & 7) << 3) | (j & 7)) << 3 | (i & 7);
 }
 

@@ -43,8 +43,9 @@ struct Win {
 };
 
 // Window brick (0..26) of the lowest corner of cell c when all 8 corners lie
-// in stored bricks of the window, else -1.
-__device__ __forceinline__ int win_cell(const Win& W, const int c[3]) {
+// in stored bricks of the window, else -1.  Integer arithmetic only: a host
+// build of it and win_corner is checked on the CPU against the definition.
+__host__ __device__ __forceinline__ int win_cell(const Win& W, const int c[3]) {
   const int rx = c[0] - W.lo[0], ry = c[1] - W.lo[1], rz = c[2] - W.lo[2];
   if ((unsigned)rx > 22u || (unsigned)ry > 22u || (unsigned)rz > 22u) return -1;
   const int b0 = (rx >> 3) + 3 * (ry >> 3) + 9 * (rz >> 3);
@@ -58,7 +59,8 @@ __device__ __forceinline__ int win_cell(const Win& W, const int c[3]) {
 }
 
 // Window brick and in-brick slot of corner (dx, dy, dz) of an in-window cell c.
-__device__ __forceinline__ int win_corner(const Win& W, const int c[3], int dx, int dy, int dz, int& local) {
+__host__ __device__ __forceinline__ int win_corner(const Win& W, const int c[3], int dx, int dy, int dz,
+                                                   int& local) {
   const int x = c[0] + dx, y = c[1] + dy, z = c[2] + dz;
   local = gp_local(x, y, z);
   return ((x - W.lo[0]) >> 3) + 3 * ((y - W.lo[1]) >> 3) + 9 * ((z - W.lo[2]) >> 3);
