@@ -47,7 +47,7 @@ def assert_rel(got, want, tol=REL_TOL, what="value"):
     assert abs(got - want) <= tol * abs(want) + 1e-30, f"{what}: got {got!r}, want {want!r}"
 
 
-def survey_failures(g, ref, tol=REL_TOL):
+def strict_bound_failures(g, ref, tol=REL_TOL):
     """Vertices outside the stricter per-vertex bound
     |g_i - ref_i| <= tol * max(|ref_i|, 1e-3 max|ref|), reported beside the
     contract (it ignores cancellation inside a vertex's sum)."""
@@ -72,7 +72,7 @@ def assert_grad_close(g, ref, scale=None, tol=REL_TOL, what="grad", kappa_max=No
     ref = np.asarray(ref, np.float64)
     nrm = np.linalg.norm(ref)
     err = np.linalg.norm(g - ref)
-    nfail, worst_rel = survey_failures(g, ref, tol)
+    nfail, worst_rel = strict_bound_failures(g, ref, tol)
     print(f"[{what}] norm err {err / max(nrm, 1e-300):.3e}; vertices over tol*max(|g*|, 1e-3 |g*|_inf): "
           f"{nfail} of {ref.size} (worst {worst_rel:.3e})"
           + (f"; kappa max {kappa_max:.3g}" if kappa_max is not None else ""))
