@@ -302,16 +302,6 @@ __device__ __forceinline__ float block_sum(float v, float* red) {
 // units of 2^-24 (integer additions do not depend on their order).
 __device__ __forceinline__ long long loss_fixed(float x) { return __double2ll_rn((double)x * 16777216.0); }
 
-// g + (hi 2^-20 + lo 2^-60) * scale from a two-word fixed-point sum, which is
-// cleared (the fold of gp_step's deterministic mode).
-__device__ __forceinline__ float fold_fixed(unsigned long long* a, float scale, float g) {
-  const long long hi = (long long)a[0], lo = (long long)a[1];
-  a[0] = 0ull;
-  a[1] = 0ull;
-  const float qv = __fmaf_rn(__ll2float_rn(hi), 9.5367431640625e-07f, __ll2float_rn(lo) * 8.673617379884035e-19f);
-  return __fmaf_rn(qv, scale, g);
-}
-
 struct MultiTvSrc {
   const MShape* shapes;
   const MTile* tiles;
@@ -335,8 +325,7 @@ template <bool DET>
 __global__ void __launch_bounds__(TV_SWEEP_THREADS, TV_BLOCKS_PER_SM) k_m_tv(const MShape* __restrict__ shapes,
                                                            const MTile* __restrict__ tiles, int64_t ntiles,
                                                            float alpha, double* __restrict__ sums,
-                                                           long long* __restrict__ isums,
-                                                           const int32_t* __restrict__ nvalid) {
+                                                           long long* __restrict__ isums) {
   __shared__ TvShared sh;
   __shared__ float red[32];
   int cur = -1;
@@ -597,11 +586,11 @@ gp_status launch_tv(gp_multi* m, const gp_loss_w* w) {
   if (m->acc)
     GP_KERNEL(ctx, "k_m_tv",
               k_m_tv<true><<<grid, TV_SWEEP_THREADS, 0, ctx->stream>>>(m->shapes, m->brick_tiles, m->n_brick_tiles,
-                                                                       w->alpha, m->sums, m->isums, m->nvalid));
+                                                                       w->alpha, m->sums, m->isums));
   else
     GP_KERNEL(ctx, "k_m_tv",
               k_m_tv<false><<<grid, TV_SWEEP_THREADS, 0, ctx->stream>>>(m->shapes, m->brick_tiles, m->n_brick_tiles,
-                                                                        w->alpha, m->sums, m->isums, m->nvalid));
+                                                                        w->alpha, m->sums, m->isums));
   return GP_OK;
 }
 

@@ -365,8 +365,8 @@ __global__ void __launch_bounds__(TV_THREADS, TV_BLOCKS_PER_SM) k_tv(Grid G, con
                                                    const int32_t* __restrict__ nbrs, int64_t n_bricks,
                                                    float tv_scale, float* __restrict__ grad,
                                                    unsigned long long* __restrict__ acc,
-                                                   const int32_t* __restrict__ bv, double* __restrict__ partials,
-                                                   int32_t* __restrict__ err, FinalArgs fa) {
+                                                   double* __restrict__ partials, int32_t* __restrict__ err,
+                                                   FinalArgs fa) {
   __shared__ TvShared sh;
   float tsum = 0.f;
   const int l = threadIdx.x;
@@ -574,8 +574,7 @@ struct AdamArgs {
 template <bool DET, bool TV>
 __global__ void __launch_bounds__(TV_THREADS, TV_BLOCKS_PER_SM) k_tv_adam(
     Grid G, const int32_t* __restrict__ coord, const int32_t* __restrict__ nbrs, int64_t n_bricks, float tv_scale,
-    float* __restrict__ qgrad, unsigned long long* __restrict__ acc, const int32_t* __restrict__ bv,
-    float* __restrict__ Dnext, float* __restrict__ m, float* __restrict__ v, AdamArgs ad,
+    float* __restrict__ qgrad, unsigned long long* __restrict__ acc, float* __restrict__ Dnext, float* __restrict__ m, float* __restrict__ v, AdamArgs ad,
     double* __restrict__ partials, int32_t* __restrict__ err, FinalArgs fa) {
   __shared__ TvShared sh;
   float tsum = 0.f;
@@ -768,8 +767,7 @@ extern "C" gp_status gp_step(gp_band* b, const float* rec_dev, int64_t B, const 
     }
 #define GP_TV(D_, G_, T_, L_)                                                                                  \
   k_tv<D_, G_, T_, L_><<<tb, TV_THREADS, 0, s>>>(G, b->brick_coord, b->brick_nbr, b->n_bricks, tv_scale, grad_dev, \
-                                                 b->acc, bv, \
-                                                 b->partials, err, fa)
+                                                 b->acc, b->partials, err, fa)
     gp_prof_pre(ctx);
     if (tv_last) {
       if (tv_on) GP_TV(true, true, true, true); else GP_TV(true, true, false, true);
@@ -1058,7 +1056,7 @@ extern "C" gp_status gp_step_update(gp_band* b, const float* rec_dev, int64_t B,
   gp_prof_pre(ctx);
 #define GP_TVA(D_, T_)                                                                                             \
   k_tv_adam<D_, T_><<<tb, TV_THREADS, 0, s>>>(G, b->brick_coord, b->brick_nbr, b->n_bricks, tv_scale, b->qgrad,  \
-                                              b->acc, bv, b->D_alt, b->m, b->v, ad, b->partials, err, fa)
+                                              b->acc, b->D_alt, b->m, b->v, ad, b->partials, err, fa)
   if (det) {
     if (tv_on) GP_TVA(true, true); else GP_TVA(true, false);
   } else {
